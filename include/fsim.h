@@ -1,0 +1,261 @@
+/*
+ * fsim.h -- C ABI of the GB300 actuated-face PD + IPC solver.
+ *
+ * The library solves the quasi-static problem of "Efficient Incremental
+ * Potential Contact for Actuated Face Simulation" (Li, Yang, Solenthaler,
+ * SIGGRAPH Asia 2023 Technical Communications): minimise
+ *     E-hat(x) = E(x) + B(x),
+ * E the shape-targeting elastic energy of Eq. 1-2 and B the IPC barrier of
+ * Eq. 3, by the loop of Algorithm 1.  Every iteration runs on the GPU:
+ * the per-tet local step (Sec. 2.1), the constraint set, barrier gradient and
+ * PSD Hessian (Sec. 2.2), the global step of Eq. 4 through the prefactored
+ * PD matrix, the Schur complement of Eq. 8-9 and the low-rank update of
+ * Eq. 10-11 (Sec. 3.1-3.2), the CCD step bound and the backtracking line
+ * search.
+ *
+ * Conventions
+ * -----------
+ * - All pointers in this header are HOST pointers unless the name ends in
+ *   "_dev" (device pointers, on the context's device).  The library copies
+ *   every input it keeps; output buffers are owned by the caller.
+ * - Positions are AoS float64 arrays "xyz" of length 3*n (x0,y0,z0,x1,...).
+ * - Index arrays are int32 (vertex/triangle ids) or int64 (row pointers).
+ * - Every entry point returns an fsim_status: 0 on success, a negative code
+ *   on failure.  No entry point traps, asserts or throws; a failed call
+ *   leaves the context usable unless it returns FSIM_ECUDA.
+ * - Calls on one context are serialised on the context's CUDA stream and
+ *   return when their result is on the host (solve_frame is synchronous).
+ *   A context must not be used from two host threads at once.
+ */
+#ifndef FSIM_H
+#define FSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsim_ctx_s* fsim_ctx_t;
+typedef int fsim_status;
+
+enum {
+  FSIM_OK = 0,
+  FSIM_EINVAL = -1,            /* bad argument (null pointer, size, id)        */
+  FSIM_ENOMEM = -2,            /* device allocation failed                      */
+  FSIM_ECUDA = -3,             /* CUDA runtime error; context state undefined   */
+  FSIM_ENOT_SPD = -4,          /* PD matrix or Schur complement not SPD         */
+  FSIM_ENOT_CONVERGED = -5,    /* iteration cap hit; positions still readable   */
+  FSIM_ELS_FAIL = -6,          /* line search made no acceptable step           */
+  FSIM_ECONTACT_OVERFLOW = -7, /* more contact/CCD pairs than the capacity      */
+  FSIM_ENONFINITE = -8,        /* NaN/Inf in inputs or iterates                 */
+  FSIM_EINTERSECTING = -9,     /* proxy primitives touch (d <= 0) at the start  */
+  FSIM_ENOT_READY = -10        /* mesh not prefactored / no actuation set       */
+};
+
+/* Arithmetic of solve_frame (Sec. 3 global step and the local step). */
+enum {
+  FSIM_FP64 = 0,   /* every per-iteration quantity in float64                  */
+  FSIM_MIXED = 1   /* float32 SVD, triangular panels and reduced system; the
+                      gradient, energies, distances and CCD stay float64       */
+};
+
+/* Solver constants (Sec. 2.1-2.2, Algorithm 1). */
+typedef struct {
+  double weight_scale;    /* w_i = weight_scale * rest volume of tet i (Eq. 2)  */
+  double dhat;            /* barrier activation distance d0 (Sec. 2.2)          */
+  double kappa;           /* barrier stiffness of Eq. 3; <= 0 selects the mean
+                             diagonal entry of H over the free DOFs             */
+  double tol_abs;         /* stop when ||g-hat_free||_2 <= max(tol_abs,         */
+  double tol_rel;         /*   tol_rel * ||g-hat_free(x_t)||_2)  (Algorithm 1)  */
+  int32_t max_iters;      /* iteration cap (FSIM_ENOT_CONVERGED beyond)         */
+  int32_t max_ls;         /* line-search halvings before FSIM_ELS_FAIL          */
+  double ccd_s;           /* additive-CCD gap ratio s (pairs keep >= s*d0)      */
+  int32_t accd_max_iters; /* additive-CCD advancement cap per pair              */
+  int32_t reserved0;
+  int64_t contact_capacity; /* max candidate/active pairs per detection; <= 0
+                               selects 64 * (number of proxy triangles)        */
+} fsim_params;
+
+/* Per-frame statistics filled by fsim_solve_frame. */
+typedef struct {
+  int32_t status;         /* same code as the return value                       */
+  int32_t iterations;     /* accepted Newton-like iterations of Algorithm 1      */
+  int32_t ls_trials;      /* energy evaluations spent in line searches           */
+  int32_t n_c;            /* contact-affected vertices at the last iteration     */
+  int32_t n_c_max;        /* largest n_c over the frame                          */
+  int32_t reserved0;
+  int64_t contacts;       /* |C| at the returned positions                       */
+  double grad_norm;       /* ||g-hat_free||_2 at the returned positions           */
+  double grad_norm0;      /* ||g-hat_free||_2 at x_t                              */
+  double energy;          /* E-hat at the returned positions                      */
+  double alpha_min;       /* smallest accepted step of the frame                  */
+} fsim_frame_stats;
+
+/* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
+ * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
+ * contact_capacity auto.  dhat must still be set by the caller. */
+fsim_status fsim_default_params(fsim_params* p);
+
+/* Create a context on CUDA device `device`; it owns one CUDA stream and all
+ * device memory of the meshes uploaded to it. */
+fsim_status fsim_create(fsim_ctx_t* out, int device);
+
+/* Release the context and every device buffer it owns. */
+fsim_status fsim_destroy(fsim_ctx_t ctx);
+
+/* Number of kernel launches this context issued so far (instrumentation). */
+fsim_status fsim_launch_count(fsim_ctx_t ctx, int64_t* count);
+
+/*
+ * Upload one simulation mesh and its collision proxy (Sec. 2.1, Sec. 3.1).
+ *   rest_xyz   [3n]    rest positions (also the initial state)
+ *   tets       [4T]    vertex ids per tetrahedron
+ *   pinned     [n]     1 = Dirichlet vertex kept at its rest position
+ *   proxy_tris [3Nt]   proxy triangles, ids into the Ns proxy vertices
+ *   W_rowptr [Ns+1], W_col [nnz], W_val [nnz]:  CSR rows of the embedding
+ *              s = W x (Sec. 3.1, Fig. 2a); at most 4 entries per row
+ *   region     [n] or NULL: 1 marks the collision-aware set x2 (Sec. 3.1);
+ *              NULL selects the free vertices in the support of W
+ * Writes the new mesh id to *mesh_id.  Proxy edges are derived from the
+ * triangles.  Errors: FSIM_EINVAL for ids out of range or empty sizes.
+ */
+fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id,
+                             const double* rest_xyz, int64_t n,
+                             const int32_t* tets, int64_t T,
+                             const uint8_t* pinned,
+                             const int32_t* proxy_tris, int64_t Nt,
+                             const int64_t* W_rowptr, const int32_t* W_col,
+                             const double* W_val, int64_t Ns,
+                             const uint8_t* region);
+
+/*
+ * One-time precomputation of the PD global step (Eq. 2 and Sec. 3.1-3.2):
+ * w_i and shape gradients; the scalar PD matrix K (H = K (x) I_3 over the
+ * free DOFs); a nested-dissection ordering of x1; the supernodal Cholesky
+ * factor of K11 (H11 = L1 L1^T); the Schur complement Sigma of Eq. 9 and its
+ * explicit inverse (Sec. 3.2).  Errors: FSIM_ENOT_SPD if K11 or Sigma is not
+ * positive definite (a free component without a pinned vertex).
+ */
+fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p);
+
+/*
+ * Per-tet actuation (Sec. 2.1): unit fibre f_i [3T] and stretch a_i [T]
+ * give the symmetric A_i = a f f^T + a^(-1/2) (I - f f^T).  The factor is
+ * untouched (H does not depend on actuation, Sec. 2.1).
+ */
+fsim_status fsim_set_actuation(fsim_ctx_t ctx, int mesh_id,
+                               const double* fiber, const double* stretch);
+
+/*
+ * Solve one frame with Algorithm 1 from x_t = x_init [3n] (NULL: the
+ * positions resident from the previous frame, or the rest state).  Pinned
+ * vertices are reset to rest.  precision is FSIM_FP64 or FSIM_MIXED.  The
+ * result stays resident (read it with fsim_read_positions).  stats may be
+ * NULL.  Returns FSIM_ENOT_CONVERGED / FSIM_ELS_FAIL with the last iterate
+ * resident, FSIM_EINTERSECTING if the proxy touches at x_init.
+ */
+fsim_status fsim_solve_frame(fsim_ctx_t ctx, int mesh_id, const double* x_init,
+                             int precision, fsim_frame_stats* stats);
+
+/* Same as fsim_solve_frame with x_init_dev a DEVICE pointer [3n] (or NULL). */
+fsim_status fsim_solve_frame_dev(fsim_ctx_t ctx, int mesh_id,
+                                 const double* x_init_dev, int precision,
+                                 fsim_frame_stats* stats);
+
+/* Copy the resident positions [3n] to host memory. */
+fsim_status fsim_read_positions(fsim_ctx_t ctx, int mesh_id, double* xyz_out);
+
+/* Device-to-device copy of the resident positions [3n]. */
+fsim_status fsim_read_positions_dev(fsim_ctx_t ctx, int mesh_id, double* xyz_out_dev);
+
+/*
+ * The constraint set C at the resident positions (Sec. 2.2), sorted by
+ * (type, i, j): keys [3*cap] receive triples (type, i, j) with type 0 =
+ * point-triangle (proxy vertex i, proxy triangle j) and type 1 = edge-edge
+ * (proxy edges i < j, edges numbered as the sorted unique (lo, hi) pairs of
+ * the triangles).  *count receives |C|; FSIM_ECONTACT_OVERFLOW if |C| > cap.
+ */
+fsim_status fsim_read_contacts(fsim_ctx_t ctx, int mesh_id, int32_t* keys,
+                               int64_t cap, int64_t* count);
+
+/* ---- step-level entry points (one row of the iteration each) ----------- */
+/* They evaluate one step at the given positions x [3n] (host) with the     */
+/* mesh's current actuation and parameters, without changing the resident   */
+/* state.  Precision follows `precision` where the step has two forms.      */
+
+/* Local step (Eq. 1, Sec. 2.1): elastic energy E and its gradient
+ * sum_i w_i G_i^T (G_i x - p_i) [3n] (zero rows for pinned vertices);
+ * proj_out [9T] (may be NULL) receives p_i = vec(R_i A_i), row-major. */
+fsim_status fsim_eval_elastic(fsim_ctx_t ctx, int mesh_id, const double* x,
+                              int precision, double* energy_out,
+                              double* grad_out, double* proj_out);
+
+/* Proxy positions s = W x [3Ns] (Sec. 3.1). */
+fsim_status fsim_eval_proxy(fsim_ctx_t ctx, int mesh_id, const double* x,
+                            double* s_out);
+
+/* UpdateConstraintSet (Algorithm 1): C at x as in fsim_read_contacts, and
+ * the barrier energy kappa * sum b(d_k) (Eq. 3). */
+fsim_status fsim_eval_contacts(fsim_ctx_t ctx, int mesh_id, const double* x,
+                               int32_t* keys, int64_t cap, int64_t* count,
+                               double* barrier_energy_out);
+
+/* Barrier terms at x (Algorithm 1, Sec. 3.1): grad_out [3n] = W^T grad B(s)
+ * over the free vertices; *n_c and c_out [n2] (may be NULL) the sorted x2
+ * indices of the contact-affected vertices; bcheck_out [(3 n_c)^2] (may be
+ * NULL, row-major) the reduced PSD block B-check of Eq. 10. */
+fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x,
+                              double* grad_out, int32_t* n_c, int32_t* c_out,
+                              double* bcheck_out, int64_t bcheck_cap);
+
+/* Global step (Eq. 4 through Eq. 8-11): dx_out [3n] solves
+ * (H + PositiveDefinite(B)) dx = -g-hat at x (zero on pinned vertices). */
+fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x,
+                                  int precision, double* dx_out);
+
+/* CCD step bound (Algorithm 1): alpha_m = min(1, min TOI) over the pairs
+ * whose swept boxes of s -> s + W dx, inflated by dhat, overlap. */
+fsim_status fsim_eval_ccd(fsim_ctx_t ctx, int mesh_id, const double* x,
+                          const double* dx, double* alpha_out);
+
+/* Line-search objective E-hat(x) = E(x) + B(x) (Sec. 2.2) and the gradient
+ * norm ||g-hat_free||_2 at x (the convergence test of Algorithm 1). */
+fsim_status fsim_eval_energy(fsim_ctx_t ctx, int mesh_id, const double* x,
+                             int precision, double* energy_out,
+                             double* grad_norm_out);
+
+/* Same as fsim_set_actuation with DEVICE pointers fiber_dev [3T] and
+ * stretch_dev [T] (no host copy; the inputs are not validated on the host). */
+fsim_status fsim_set_actuation_dev(fsim_ctx_t ctx, int mesh_id,
+                                   const double* fiber_dev, const double* stretch_dev);
+
+/* The context's CUDA stream (a cudaStream_t) in *stream, so that callers
+ * can order their own work or record timing events on it. */
+fsim_status fsim_get_stream(fsim_ctx_t ctx, void** stream);
+
+/* Kernel timing by CUDA events recorded around every launch of the kernel
+ * classes whose bits are set in class_mask (0 disables): 0 local step,
+ * 1 contact detection, 2 forward and 3 backward supernodal solves, 4 dense
+ * Cholesky, 5 barrier pairs, 6 CCD, 7 Sigma^-1 product, 8 whole reduced
+ * system.  fsim_profile_read synchronises and returns the launch count and
+ * summed milliseconds of one class since the last fsim_profile_reset. */
+fsim_status fsim_profile(fsim_ctx_t ctx, uint32_t class_mask);
+fsim_status fsim_profile_read(fsim_ctx_t ctx, int kernel_class, int64_t* launches,
+                              double* total_ms);
+fsim_status fsim_profile_reset(fsim_ctx_t ctx);
+
+/* Sizes of a mesh (n, T, Ns, Nt, Ne, free / x1 / x2 vertex counts), the
+ * scalar factor's stored entries and supernode / level counts, and the
+ * barrier stiffness kappa in use (after fsim_prefactor). */
+typedef struct {
+  int64_t n, T, Ns, Nt, Ne, n_free, n1, n2, factor_nnz, n_supernodes, n_levels;
+  double kappa;
+} fsim_mesh_info;
+fsim_status fsim_mesh_info_get(fsim_ctx_t ctx, int mesh_id, fsim_mesh_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSIM_H */

@@ -93,13 +93,13 @@ class Problem:
         self.H = H_all[self.free_dofs][:, self.free_dofs].tocsr()
         self.kappa = (float(self.H.diagonal().mean()) if params.kappa is None
                       else float(params.kappa))
-        # collision-aware set x2: marked region, else the support of W
+        # collision-aware set x2 (Sec. 3.1: x2 embeds s): the free support of
+        # W, plus the marked region when one is given
+        x2 = np.zeros(self.n, dtype=bool)
+        x2[np.unique(self.W.indices)] = True
         if region is not None:
-            x2 = np.asarray(region).astype(bool) & ~self.pinned
-        else:
-            x2 = np.zeros(self.n, dtype=bool)
-            x2[np.unique(self.W.indices)] = True
-            x2 &= ~self.pinned
+            x2 |= np.asarray(region).astype(bool)
+        x2 &= ~self.pinned
         self.x2_mask = x2
         self.A = None
 

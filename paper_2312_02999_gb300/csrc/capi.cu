@@ -1,0 +1,876 @@
+// C ABI (include/fsim.h): context, mesh upload, prefactor, actuation, the
+// Algorithm 1 loop and the step-level entry points.
+//
+// The host code here only sequences kernels and reads back the few scalars
+// that steer the loop (gradient norm, n_c, candidate count, trial energy);
+// every arithmetic step of an iteration runs in the CUDA kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "fsim_internal.h"
+#include "kernels.h"
+
+using namespace fsim;
+
+namespace {
+
+struct MeshState {
+  DevMesh d;
+  bool prefactored = false, actuated = false;
+  fsim_params p{};
+  double kappa = 0.0;
+  int64_t factor_nnz = 0;
+  std::vector<void*> allocs;     // device buffers owned by this mesh
+  // host copies kept for the prefactor
+  std::vector<double> rest;
+  std::vector<int32_t> tets;
+  std::vector<uint8_t> pinned;
+  std::vector<uint8_t> x2mask;
+  // scratch for the step entry points
+  double* gtmp = nullptr;
+  double* proj = nullptr;
+  double* dxtmp = nullptr;
+  bool has_x = false;
+};
+
+}  // namespace
+
+struct fsim_ctx_s {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<std::unique_ptr<MeshState>> meshes;
+  // pinned host readback area
+  int* h_counters = nullptr;   // 8 ints
+  double* h_scal = nullptr;    // 8 doubles
+};
+
+namespace {
+
+constexpr int kCounters = 8;
+constexpr int kScal = 8;
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      fprintf(stderr, "fsim: CUDA error %s at %s:%d\n",            \
+              cudaGetErrorString(e_), __FILE__, __LINE__);         \
+      return FSIM_ECUDA;                                           \
+    }                                                              \
+  } while (0)
+
+template <typename T>
+int dalloc(MeshState& ms, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e != cudaSuccess) { cudaGetLastError(); return FSIM_ENOMEM; }
+  ms.allocs.push_back(*p);
+  return FSIM_OK;
+}
+
+#define TRY(x)                    \
+  do {                            \
+    int s_ = (x);                 \
+    if (s_ != FSIM_OK) return s_; \
+  } while (0)
+
+template <typename T>
+int upload(MeshState& ms, cudaStream_t s, T** p, const T* h, size_t count) {
+  TRY(dalloc(ms, p, count));
+  if (count) {
+    cudaError_t e = cudaMemcpyAsync(*p, h, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return FSIM_ECUDA;
+  }
+  return FSIM_OK;
+}
+
+MeshState* get_mesh(fsim_ctx_t ctx, int id) {
+  if (ctx == nullptr || id < 0 || id >= (int)ctx->meshes.size()) return nullptr;
+  return ctx->meshes[id].get();
+}
+
+void free_mesh(MeshState& ms) {
+  for (void* p : ms.allocs) cudaFree(p);
+  ms.allocs.clear();
+  delete[] ms.d.h_level_ptr;
+  delete[] ms.d.h_level_maxns;
+  delete[] ms.d.h_level_maxld;
+  delete[] ms.d.h_fwd_ptr;
+  delete[] ms.d.h_bwd_ptr;
+  ms.d.h_level_ptr = nullptr;
+  ms.d.h_level_maxns = nullptr;
+  ms.d.h_level_maxld = nullptr;
+  ms.d.h_fwd_ptr = nullptr;
+  ms.d.h_bwd_ptr = nullptr;
+}
+
+int sync_read(fsim_ctx_t ctx, const DevMesh& m) {
+  CK(cudaMemcpyAsync(ctx->h_counters, m.counters, sizeof(int) * kCounters, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_scal, m.scal, sizeof(double) * kScal, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSIM_OK;
+}
+
+// Make the reduced-system buffers large enough for nc contact vertices.
+int ensure_reduced(fsim_ctx_t ctx, MeshState& ms, int nc) {
+  DevMesh& m = ms.d;
+  if (nc <= m.nc_cap && m.Bc != nullptr) return FSIM_OK;
+  int cap = std::max(nc, std::max(16, m.nc_cap * 3 / 2));
+  cap = std::min(cap, std::max(m.n2, 1));
+  CK(cudaStreamSynchronize(ctx->stream));
+  auto release = [&](void* p) {
+    if (!p) return;
+    cudaFree(p);
+    ms.allocs.erase(std::remove(ms.allocs.begin(), ms.allocs.end(), p), ms.allocs.end());
+  };
+  release(m.Bc); release(m.bocc); release(m.red); release(m.redf);
+  m.Bc = nullptr; m.bocc = nullptr; m.red = nullptr; m.redf = nullptr;
+  const int64_t n3 = 3 * (int64_t)cap;
+  TRY(dalloc(ms, &m.Bc, (size_t)(n3 * n3)));
+  TRY(dalloc(ms, &m.bocc, (size_t)(2 * (int64_t)cap * cap + cap + 32)));
+  m.red_cap = reduced_workspace_elems(cap);
+  TRY(dalloc(ms, &m.red, (size_t)m.red_cap));
+  TRY(dalloc(ms, &m.redf, (size_t)m.red_cap));
+  m.nc_cap = cap;
+  return FSIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one evaluation at positions xb: local step (energy + per-tet forces into
+// tetf), proxy positions sb and the constraint set with barrier energy.
+// Leaves E in scal[2], B in scal[0], |C| in counters[0].
+// ---------------------------------------------------------------------------
+int evaluate(fsim_ctx_t ctx, MeshState& ms, const double* xb, double* sb, double* tetf,
+             double* proj, int prec) {
+  DevMesh& m = ms.d;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(m.counters, 0, sizeof(int) * 3, s));       // |C|, candidates, overflow
+  CK(cudaMemsetAsync(m.counters + 5, 0, sizeof(int), s));       // touching pair
+  CK(cudaMemsetAsync(m.scal, 0, sizeof(double) * 1, s));
+  launch_elastic(s, m, xb, tetf, proj, m.partials, prec);
+  launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
+  launch_proxy(s, m, xb, sb);
+  launch_detect(s, m, sb, ms.p.dhat, ms.kappa);
+  CK(cudaGetLastError());
+  return FSIM_OK;
+}
+
+// Gradient g-hat (elastic from tetf + barrier over the pairs in m.pairs at
+// sb) into gout, the contact-affected set, B-check (if hess) and ||g||^2.
+// Requires counters[0] (|C|) already on the host in npairs.
+int gradient_and_hessian(fsim_ctx_t ctx, MeshState& ms, const double* sb, const double* tetf,
+                         double* gout, int64_t npairs, bool hess, int* nc_out, double* gn2_out) {
+  DevMesh& m = ms.d;
+  cudaStream_t s = ctx->stream;
+  launch_gather_forces(s, m, tetf, gout);
+  CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
+  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, ms.kappa);
+  if (m.n2 > 0) launch_mark_scan(s, m);
+  else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
+  TRY(sync_read(ctx, m));
+  int nc = ctx->h_counters[3];
+  TRY(ensure_reduced(ctx, ms, std::max(nc, 1)));
+  if (nc > 0) {
+    CK(cudaMemsetAsync(m.Bc, 0, sizeof(double) * 9 * (size_t)nc * nc, s));
+    CK(cudaMemsetAsync(m.bocc, 0, sizeof(int) * (size_t)nc * nc, s));
+  }
+  launch_barrier_scatter(s, m, npairs, nc, gout);   // gradient always, blocks for hess
+  (void)hess;
+  const int nb = gnorm_blocks(m.n);
+  launch_gnorm2(s, m, gout, m.partials, nb);
+  launch_sum_partials(s, m.partials, nb, m.scal + 3);
+  TRY(sync_read(ctx, m));
+  *nc_out = nc;
+  *gn2_out = ctx->h_scal[3];
+  return FSIM_OK;
+}
+
+int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool init_is_dev,
+                     int prec, fsim_frame_stats* stats) {
+  DevMesh& m = ms.d;
+  cudaStream_t s = ctx->stream;
+  const fsim_params& p = ms.p;
+  fsim_frame_stats st{};
+  st.alpha_min = 1.0;
+  if (x_init != nullptr) {
+    CK(cudaMemcpyAsync(m.x, x_init, sizeof(double) * 3 * (size_t)m.n,
+                       init_is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  }
+  launch_reset_pinned(s, m, m.x);
+  CK(cudaMemsetAsync(m.counters + 4, 0, sizeof(int), s));
+  launch_check_finite(s, 3 * m.n, m.x, m.counters + 4);
+  TRY(evaluate(ctx, ms, m.x, m.s, m.tetf, nullptr, prec));
+  TRY(sync_read(ctx, m));
+  int rc = FSIM_OK;
+  if (ctx->h_counters[4]) rc = FSIM_ENONFINITE;
+  else if (ctx->h_counters[5]) rc = FSIM_EINTERSECTING;
+  else if (ctx->h_counters[2]) rc = FSIM_ECONTACT_OVERFLOW;
+  int64_t npairs = ctx->h_counters[0];
+  double E = ctx->h_scal[2] + ctx->h_scal[0];
+  double gn = 0.0, tol = 0.0;
+  int nc = 0;
+  if (rc == FSIM_OK) {
+    double gn2;
+    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, true, &nc, &gn2));
+    gn = std::sqrt(gn2);
+    st.grad_norm0 = gn;
+    tol = std::max(p.tol_abs, p.tol_rel * gn);
+    if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
+  }
+  while (rc == FSIM_OK) {
+    st.n_c = nc;
+    st.n_c_max = std::max(st.n_c_max, nc);
+    if (gn <= tol) break;
+    if (st.iterations >= p.max_iters) { rc = FSIM_ENOT_CONVERGED; break; }
+    // global step (Eq. 4 via Eq. 8-11)
+    CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
+    global_step(s, m, m.g, m.dx, nc, prec, m.counters + 6, ctx->num_sms);
+    CK(cudaGetLastError());
+    // CCD step bound
+    launch_proxy(s, m, m.dx, m.ds);
+    CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int) * 2, s));
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_ccd_candidates(s, m, m.s, m.ds, p.dhat);
+    TRY(sync_read(ctx, m));
+    if (ctx->h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
+    if (ctx->h_counters[2]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
+    launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters, ctx->h_counters[1]);
+    // backtracking line search from alpha_m on E-hat = E + B
+    bool accepted = false;
+    double scale = 1.0, Et = 0.0;
+    int64_t np_t = 0;
+    for (int k = 0; k <= p.max_ls; ++k) {
+      launch_axpy_positions(s, 3 * m.n, m.x, m.dx, m.scal + 1, scale, m.xt);
+      TRY(evaluate(ctx, ms, m.xt, m.st, m.tetf_t, nullptr, prec));
+      TRY(sync_read(ctx, m));
+      st.ls_trials++;
+      Et = ctx->h_scal[2] + ctx->h_scal[0];
+      np_t = ctx->h_counters[0];
+      if (ctx->h_counters[2]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
+      if (!ctx->h_counters[5] && std::isfinite(Et) && Et <= E + 1e-12 * std::fabs(E)) {
+        accepted = true;
+        break;
+      }
+      scale *= 0.5;
+    }
+    if (rc != FSIM_OK) break;
+    if (!accepted) { rc = FSIM_ELS_FAIL; break; }
+    st.alpha_min = std::min(st.alpha_min, ctx->h_scal[1] * scale);
+    std::swap(m.x, m.xt);
+    std::swap(m.s, m.st);
+    std::swap(m.tetf, m.tetf_t);
+    E = Et;
+    npairs = np_t;
+    st.iterations++;
+    double gn2;
+    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, true, &nc, &gn2));
+    gn = std::sqrt(gn2);
+    if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
+  }
+  ms.has_x = true;
+  st.status = rc;
+  st.grad_norm = gn;
+  st.energy = E;
+  st.contacts = npairs;
+  if (stats) *stats = st;
+  return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+fsim_status fsim_default_params(fsim_params* p) {
+  if (!p) return FSIM_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->weight_scale = 1e3;
+  p->dhat = 0.0;
+  p->kappa = 0.0;
+  p->tol_abs = 1e-8;
+  p->tol_rel = 0.0;
+  p->max_iters = 500;
+  p->max_ls = 40;
+  p->ccd_s = 0.1;
+  p->accd_max_iters = 2000;
+  p->contact_capacity = 0;
+  return FSIM_OK;
+}
+
+fsim_status fsim_create(fsim_ctx_t* out, int device) {
+  if (!out) return FSIM_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return FSIM_EINVAL;
+  }
+  auto* c = new (std::nothrow) fsim_ctx_s();
+  if (!c) return FSIM_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return FSIM_ECUDA; }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return FSIM_ECUDA;
+  }
+  if (cudaHostAlloc((void**)&c->h_counters, sizeof(int) * kCounters, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&c->h_scal, sizeof(double) * kScal, cudaHostAllocDefault) != cudaSuccess) {
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return FSIM_ENOMEM;
+  }
+  set_solver_smem_limits(200 * 1024);
+  *out = c;
+  return FSIM_OK;
+}
+
+fsim_status fsim_destroy(fsim_ctx_t ctx) {
+  if (!ctx) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& m : ctx->meshes)
+    if (m) free_mesh(*m);
+  cudaFreeHost(ctx->h_counters);
+  cudaFreeHost(ctx->h_scal);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return FSIM_OK;
+}
+
+fsim_status fsim_launch_count(fsim_ctx_t ctx, int64_t* count) {
+  if (!ctx || !count) return FSIM_EINVAL;
+  *count = launch_counter();
+  return FSIM_OK;
+}
+
+fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xyz, int64_t n,
+                             const int32_t* tets, int64_t T, const uint8_t* pinned,
+                             const int32_t* proxy_tris, int64_t Nt, const int64_t* W_rowptr,
+                             const int32_t* W_col, const double* W_val, int64_t Ns,
+                             const uint8_t* region) {
+  if (!ctx || !mesh_id || !rest_xyz || !tets || !pinned || n <= 0 || T <= 0 || n >= (1LL << 30) ||
+      T >= (1LL << 30) || Ns < 0 || Nt < 0 || (Ns > 0 && (!W_rowptr || !W_col || !W_val)) ||
+      (Nt > 0 && !proxy_tris))
+    return FSIM_EINVAL;
+  for (int64_t k = 0; k < 4 * T; ++k)
+    if (tets[k] < 0 || tets[k] >= n) return FSIM_EINVAL;
+  for (int64_t k = 0; k < 3 * Nt; ++k)
+    if (proxy_tris[k] < 0 || proxy_tris[k] >= Ns) return FSIM_EINVAL;
+  if (Ns > 0) {
+    if (W_rowptr[0] != 0) return FSIM_EINVAL;
+    for (int64_t r = 0; r < Ns; ++r) {
+      if (W_rowptr[r + 1] < W_rowptr[r] || W_rowptr[r + 1] - W_rowptr[r] > 4) return FSIM_EINVAL;
+    }
+    for (int64_t e = 0; e < W_rowptr[Ns]; ++e)
+      if (W_col[e] < 0 || W_col[e] >= n) return FSIM_EINVAL;
+  }
+  cudaSetDevice(ctx->device);
+  auto msp = std::make_unique<MeshState>();
+  MeshState& ms = *msp;
+  DevMesh& m = ms.d;
+  cudaStream_t s = ctx->stream;
+  m.n = (int)n; m.T = (int)T; m.Ns = (int)Ns; m.Nt = (int)Nt;
+  ms.rest.assign(rest_xyz, rest_xyz + 3 * n);
+  ms.tets.assign(tets, tets + 4 * T);
+  ms.pinned.assign(pinned, pinned + n);
+  // collision-aware set x2: region (if given) plus the free support of W
+  ms.x2mask.assign(n, 0);
+  if (region)
+    for (int64_t v = 0; v < n; ++v) ms.x2mask[v] = region[v] ? 1 : 0;
+  if (Ns > 0)
+    for (int64_t e = 0; e < W_rowptr[Ns]; ++e) ms.x2mask[W_col[e]] = 1;
+  for (int64_t v = 0; v < n; ++v)
+    if (pinned[v]) ms.x2mask[v] = 0;
+  // proxy edges: sorted unique (lo, hi)
+  std::vector<std::pair<int, int>> ed;
+  ed.reserve(3 * Nt);
+  for (int64_t t = 0; t < Nt; ++t)
+    for (int k = 0; k < 3; ++k) {
+      int a = proxy_tris[3 * t + k], b = proxy_tris[3 * t + (k + 1) % 3];
+      ed.push_back({std::min(a, b), std::max(a, b)});
+    }
+  std::sort(ed.begin(), ed.end());
+  ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+  m.Ne = (int)ed.size();
+  std::vector<int> edges(2 * ed.size());
+  for (size_t k = 0; k < ed.size(); ++k) { edges[2 * k] = ed[k].first; edges[2 * k + 1] = ed[k].second; }
+  // vertex -> incident (t, a) slots
+  std::vector<int> vptr(n + 1, 0), vslot(4 * T);
+  for (int64_t k = 0; k < 4 * T; ++k) vptr[tets[k] + 1]++;
+  for (int64_t v = 0; v < n; ++v) vptr[v + 1] += vptr[v];
+  {
+    std::vector<int> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t t = 0; t < T; ++t)
+      for (int a = 0; a < 4; ++a) vslot[fill[tets[4 * t + a]]++] = (int)(t * 4 + a);
+  }
+  std::vector<int> tets_i(tets, tets + 4 * T);
+  TRY(upload(ms, s, &m.rest, rest_xyz, 3 * n));
+  TRY(upload(ms, s, &m.x, rest_xyz, 3 * n));
+  TRY(dalloc(ms, &m.xt, 3 * n));
+  TRY(dalloc(ms, &m.dx, 3 * n));
+  TRY(dalloc(ms, &m.g, 3 * n));
+  TRY(dalloc(ms, &ms.gtmp, 3 * n));
+  TRY(dalloc(ms, &ms.dxtmp, 3 * n));
+  TRY(upload(ms, s, &m.pinned, pinned, n));
+  TRY(upload(ms, s, (int**)&m.tets, tets_i.data(), 4 * T));
+  TRY(dalloc(ms, &m.tetf, 12 * T));
+  TRY(dalloc(ms, &m.tetf_t, 12 * T));
+  TRY(upload(ms, s, &m.vinc_ptr, vptr.data(), n + 1));
+  TRY(upload(ms, s, &m.vinc_slot, vslot.data(), 4 * T));
+  TRY(dalloc(ms, &m.act, 6 * T));
+  if (Ns > 0) {
+    TRY(upload(ms, s, &m.Wptr, W_rowptr, Ns + 1));
+    TRY(upload(ms, s, &m.Wcol, W_col, W_rowptr[Ns]));
+    TRY(upload(ms, s, &m.Wval, W_val, W_rowptr[Ns]));
+  } else {
+    int64_t z = 0;
+    TRY(upload(ms, s, &m.Wptr, &z, 1));
+    TRY(dalloc(ms, &m.Wcol, 1));
+    TRY(dalloc(ms, &m.Wval, 1));
+  }
+  TRY(upload(ms, s, &m.tris, proxy_tris, 3 * Nt));
+  TRY(upload(ms, s, &m.edges, edges.data(), edges.size()));
+  TRY(dalloc(ms, &m.s, 3 * Ns));
+  TRY(dalloc(ms, &m.st, 3 * Ns));
+  TRY(dalloc(ms, &m.ds, 3 * Ns));
+  TRY(dalloc(ms, &m.counters, kCounters));
+  TRY(dalloc(ms, &m.scal, kScal));
+  m.n_partials = std::max(elastic_blocks(m.T), gnorm_blocks(m.n)) + 16;
+  TRY(dalloc(ms, &m.partials, m.n_partials));
+  CK(cudaStreamSynchronize(s));
+  ctx->meshes.push_back(std::move(msp));
+  *mesh_id = (int)ctx->meshes.size() - 1;
+  return FSIM_OK;
+}
+
+fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
+  MeshState* msp = get_mesh(ctx, mesh_id);
+  if (!msp || !p || !(p->dhat > 0.0) || !(p->weight_scale > 0.0) || p->max_iters < 0 ||
+      p->max_ls < 0 || !(p->ccd_s > 0.0 && p->ccd_s < 1.0) || p->accd_max_iters <= 0)
+    return FSIM_EINVAL;
+  if (msp->prefactored) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  MeshState& ms = *msp;
+  DevMesh& m = ms.d;
+  cudaStream_t s = ctx->stream;
+  ms.p = *p;
+  std::vector<double> dminv, w;
+  tet_rest_data(ms.rest.data(), ms.tets.data(), m.T, p->weight_scale, dminv, w);
+  for (double wt : w)
+    if (!(wt > 0.0) || !std::isfinite(wt)) return FSIM_EINVAL;   // degenerate tet
+  HostFactor f;
+  int rc = build_factor(m.n, ms.rest.data(), ms.tets.data(), m.T, dminv, w, ms.pinned.data(),
+                        ms.x2mask, f);
+  if (rc != FSIM_OK) return rc;
+  ms.kappa = p->kappa > 0.0 ? p->kappa : f.kappa_auto;
+  ms.factor_nnz = f.factor_nnz;
+  m.nf = f.n_free; m.n1 = f.n1; m.n2 = f.n2;
+  TRY(upload(ms, s, &m.dminv, dminv.data(), dminv.size()));
+  TRY(upload(ms, s, &m.w, w.data(), w.size()));
+  TRY(upload(ms, s, &m.perm, f.perm.data(), f.perm.size()));
+  TRY(upload(ms, s, &m.pos, f.pos.data(), f.pos.size()));
+  std::vector<int> x2of(m.n, -1);
+  for (int q = 0; q < m.n2; ++q) x2of[f.perm[m.n1 + q]] = q;
+  TRY(upload(ms, s, &m.x2of, x2of.data(), x2of.size()));
+  // supernodes
+  const int nsn = (int)f.sn.size();
+  m.n_sn = nsn;
+  m.n_levels = f.n_levels;
+  std::vector<int> c0(nsn), ns(nsn), nr1(nsn);
+  std::vector<int64_t> roff(nsn), zoff(nsn);
+  m.max_ns = 1; m.max_ld = 1;
+  for (int j = 0; j < nsn; ++j) {
+    c0[j] = f.sn[j].c0; ns[j] = f.sn[j].ns; nr1[j] = f.sn[j].nr1;
+    roff[j] = f.sn[j].rows_off; zoff[j] = f.sn[j].z_off;
+    m.max_ns = std::max(m.max_ns, ns[j]);
+    m.max_ld = std::max(m.max_ld, ns[j] + nr1[j]);
+  }
+  if (3 * (size_t)m.max_ld * sizeof(double) > 200 * 1024) return FSIM_EINVAL;
+  TRY(upload(ms, s, &m.sn_c0, c0.data(), nsn));
+  TRY(upload(ms, s, &m.sn_ns, ns.data(), nsn));
+  TRY(upload(ms, s, &m.sn_nr1, nr1.data(), nsn));
+  TRY(upload(ms, s, &m.sn_roff, roff.data(), nsn));
+  TRY(upload(ms, s, &m.sn_zoff, zoff.data(), nsn));
+  TRY(upload(ms, s, &m.sn_rows, f.rows.data(), f.rows.size()));
+  TRY(upload(ms, s, &m.Z, f.Z.data(), f.Z.size()));
+  {
+    std::vector<float> zf(f.Z.begin(), f.Z.end());
+    TRY(upload(ms, s, &m.Zf, zf.data(), zf.size()));
+    CK(cudaStreamSynchronize(s));
+  }
+  TRY(upload(ms, s, &m.level_sn, f.level_sn.data(), f.level_sn.size()));
+  m.h_level_ptr = new int[f.n_levels + 1];
+  m.h_level_maxns = new int[std::max(f.n_levels, 1)];
+  m.h_level_maxld = new int[std::max(f.n_levels, 1)];
+  m.h_fwd_ptr = new int[f.n_levels + 1];
+  m.h_bwd_ptr = new int[f.n_levels + 1];
+  // work items: forward = 32-row chunks of Z_J, backward = 16-column chunks
+  std::vector<int4> fwd, bwd;
+  m.h_fwd_ptr[0] = 0;
+  m.h_bwd_ptr[0] = 0;
+  for (int l = 0; l <= f.n_levels; ++l) m.h_level_ptr[l] = f.level_ptr[l];
+  for (int l = 0; l < f.n_levels; ++l) {
+    int mx = 1, mxld = 1;
+    for (int k = f.level_ptr[l]; k < f.level_ptr[l + 1]; ++k) {
+      const int J = f.level_sn[k];
+      const int ldj = ns[J] + nr1[J];
+      mx = std::max(mx, ns[J]);
+      mxld = std::max(mxld, ldj);
+      for (int r0 = 0; r0 < ldj; r0 += 32) fwd.push_back(make_int4(J, r0, std::min(32, ldj - r0), 0));
+      for (int k0 = 0; k0 < ns[J]; k0 += 16) bwd.push_back(make_int4(J, k0, std::min(16, ns[J] - k0), 0));
+    }
+    m.h_level_maxns[l] = mx;
+    m.h_level_maxld[l] = mxld;
+    m.h_fwd_ptr[l + 1] = (int)fwd.size();
+    m.h_bwd_ptr[l + 1] = (int)bwd.size();
+  }
+  TRY(upload(ms, s, &m.fwd_items, fwd.data(), fwd.size()));
+  TRY(upload(ms, s, &m.bwd_items, bwd.data(), bwd.size()));
+  TRY(dalloc(ms, &m.y1, 3 * (size_t)std::max(m.n1, 1)));
+  TRY(dalloc(ms, &m.y1f, 3 * (size_t)std::max(m.n1, 1)));
+  TRY(upload(ms, s, &m.k12_ptr, f.k12_ptr.data(), f.k12_ptr.size()));
+  TRY(upload(ms, s, &m.k12_col, f.k12_col.data(), f.k12_col.size()));
+  TRY(upload(ms, s, &m.k12_val, f.k12_val.data(), f.k12_val.size()));
+  TRY(upload(ms, s, &m.k21_ptr, f.k21_ptr.data(), f.k21_ptr.size()));
+  TRY(upload(ms, s, &m.k21_col, f.k21_col.data(), f.k21_col.size()));
+  TRY(upload(ms, s, &m.k21_val, f.k21_val.data(), f.k21_val.size()));
+  TRY(upload(ms, s, &m.Sinv, f.sigma_inv.data(), f.sigma_inv.size()));
+  {
+    std::vector<float> sf(f.sigma_inv.begin(), f.sigma_inv.end());
+    TRY(upload(ms, s, &m.Sinvf, sf.data(), sf.size()));
+    CK(cudaStreamSynchronize(s));
+  }
+  TRY(dalloc(ms, &m.r, 3 * (size_t)m.nf));
+  TRY(dalloc(ms, &m.t1, 3 * (size_t)std::max(m.n1, 1)));
+  TRY(dalloc(ms, &m.u, 3 * (size_t)std::max(m.n2, 1)));
+  TRY(dalloc(ms, &m.rf, 3 * (size_t)std::max(m.n1, 2 * m.n2) + 8));
+  m.cap = p->contact_capacity > 0 ? p->contact_capacity
+                                  : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
+  if (m.cap >= (1LL << 31)) return FSIM_EINVAL;
+  TRY(dalloc(ms, &m.pairs, m.cap));
+  TRY(dalloc(ms, &m.cand, m.cap));
+  TRY(dalloc(ms, &m.pair_grad, 12 * (size_t)m.cap));
+  TRY(dalloc(ms, &m.pair_hess, 144 * (size_t)m.cap));
+  TRY(dalloc(ms, &m.x2mark, std::max(m.n2, 1)));
+  TRY(dalloc(ms, &m.clist, std::max(m.n2, 1)));
+  TRY(ensure_reduced(ctx, ms, std::min(std::max(m.n2, 1), 64)));
+  CK(cudaStreamSynchronize(s));
+  ms.prefactored = true;
+  return FSIM_OK;
+}
+
+fsim_status fsim_set_actuation(fsim_ctx_t ctx, int mesh_id, const double* fiber, const double* stretch) {
+  MeshState* msp = get_mesh(ctx, mesh_id);
+  if (!msp || !fiber || !stretch) return FSIM_EINVAL;
+  const int T = msp->d.T;
+  for (int t = 0; t < T; ++t) {
+    const double a = stretch[t];
+    const double f2 = fiber[3 * t] * fiber[3 * t] + fiber[3 * t + 1] * fiber[3 * t + 1] +
+                      fiber[3 * t + 2] * fiber[3 * t + 2];
+    if (!(a > 0.0) || !std::isfinite(a) || !(f2 > 0.0) || !std::isfinite(f2)) return FSIM_ENONFINITE;
+  }
+  cudaSetDevice(ctx->device);
+  DevMesh& m = msp->d;
+  cudaStream_t s = ctx->stream;
+  // staging: fiber into tetf (>= 3T doubles), stretch into tetf_t
+  CK(cudaMemcpyAsync(m.tetf, fiber, sizeof(double) * 3 * (size_t)T, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(m.tetf_t, stretch, sizeof(double) * (size_t)T, cudaMemcpyHostToDevice, s));
+  launch_actuation(s, T, m.tetf, m.tetf_t, m.act);
+  CK(cudaStreamSynchronize(s));
+  msp->actuated = true;
+  return FSIM_OK;
+}
+
+fsim_status fsim_set_actuation_dev(fsim_ctx_t ctx, int mesh_id, const double* fiber_dev,
+                                   const double* stretch_dev) {
+  MeshState* msp = get_mesh(ctx, mesh_id);
+  if (!msp || !fiber_dev || !stretch_dev) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  launch_actuation(ctx->stream, msp->d.T, fiber_dev, stretch_dev, msp->d.act);
+  CK(cudaGetLastError());
+  msp->actuated = true;
+  return FSIM_OK;
+}
+
+fsim_status fsim_get_stream(fsim_ctx_t ctx, void** stream) {
+  if (!ctx || !stream) return FSIM_EINVAL;
+  *stream = (void*)ctx->stream;
+  return FSIM_OK;
+}
+
+fsim_status fsim_profile(fsim_ctx_t ctx, uint32_t class_mask) {
+  if (!ctx) return FSIM_EINVAL;
+  prof_set_mask(class_mask);
+  return FSIM_OK;
+}
+
+fsim_status fsim_profile_read(fsim_ctx_t ctx, int kernel_class, int64_t* launches, double* total_ms) {
+  if (!ctx || !launches || !total_ms) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return prof_read(kernel_class, launches, total_ms) == 0 ? FSIM_OK : FSIM_EINVAL;
+}
+
+fsim_status fsim_profile_reset(fsim_ctx_t ctx) {
+  if (!ctx) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_reset();
+  return FSIM_OK;
+}
+
+static int ready(MeshState* ms) {
+  if (!ms) return FSIM_EINVAL;
+  if (!ms->prefactored || !ms->actuated) return FSIM_ENOT_READY;
+  return FSIM_OK;
+}
+
+fsim_status fsim_solve_frame(fsim_ctx_t ctx, int mesh_id, const double* x_init, int precision,
+                             fsim_frame_stats* stats) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (precision != FSIM_FP64 && precision != FSIM_MIXED) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  return solve_frame_impl(ctx, *ms, x_init, false, precision, stats);
+}
+
+fsim_status fsim_solve_frame_dev(fsim_ctx_t ctx, int mesh_id, const double* x_init_dev,
+                                 int precision, fsim_frame_stats* stats) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (precision != FSIM_FP64 && precision != FSIM_MIXED) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  return solve_frame_impl(ctx, *ms, x_init_dev, true, precision, stats);
+}
+
+fsim_status fsim_read_positions(fsim_ctx_t ctx, int mesh_id, double* xyz_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  if (!ms || !xyz_out) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  CK(cudaMemcpyAsync(xyz_out, ms->d.x, sizeof(double) * 3 * (size_t)ms->d.n, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSIM_OK;
+}
+
+fsim_status fsim_read_positions_dev(fsim_ctx_t ctx, int mesh_id, double* xyz_out_dev) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  if (!ms || !xyz_out_dev) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  CK(cudaMemcpyAsync(xyz_out_dev, ms->d.x, sizeof(double) * 3 * (size_t)ms->d.n,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSIM_OK;
+}
+
+static int copy_keys(fsim_ctx_t ctx, MeshState& ms, int64_t np, int32_t* keys, int64_t cap,
+                     int64_t* count) {
+  std::vector<unsigned long long> k(np);
+  if (np > 0) {
+    CK(cudaMemcpyAsync(k.data(), ms.d.pairs, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  std::sort(k.begin(), k.end());
+  *count = np;
+  if (np > cap) return FSIM_ECONTACT_OVERFLOW;
+  for (int64_t q = 0; q < np; ++q) {
+    keys[3 * q] = (int32_t)(k[q] >> 62);
+    keys[3 * q + 1] = (int32_t)((k[q] >> 31) & 0x7fffffffULL);
+    keys[3 * q + 2] = (int32_t)(k[q] & 0x7fffffffULL);
+  }
+  return FSIM_OK;
+}
+
+fsim_status fsim_read_contacts(fsim_ctx_t ctx, int mesh_id, int32_t* keys, int64_t cap, int64_t* count) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!count || (cap > 0 && !keys)) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  TRY(evaluate(ctx, *ms, m.x, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  return copy_keys(ctx, *ms, ctx->h_counters[0], keys, cap, count);
+}
+
+// ---- step-level entry points ------------------------------------------------
+static int stage_x(fsim_ctx_t ctx, MeshState& ms, const double* x) {
+  DevMesh& m = ms.d;
+  CK(cudaMemcpyAsync(m.xt, x, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyHostToDevice, ctx->stream));
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_elastic(fsim_ctx_t ctx, int mesh_id, const double* x, int precision,
+                              double* energy_out, double* grad_out, double* proj_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x || (precision != 0 && precision != 1)) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  cudaStream_t s = ctx->stream;
+  TRY(stage_x(ctx, *ms, x));
+  if (proj_out && !ms->proj) TRY(dalloc(*ms, &ms->proj, 9 * (size_t)m.T));
+  launch_elastic(s, m, m.xt, m.tetf_t, proj_out ? ms->proj : nullptr, m.partials, precision);
+  launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
+  launch_gather_forces(s, m, m.tetf_t, ms->gtmp);
+  TRY(sync_read(ctx, m));
+  if (energy_out) *energy_out = ctx->h_scal[2];
+  if (grad_out)
+    CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
+  if (proj_out)
+    CK(cudaMemcpy(proj_out, ms->proj, sizeof(double) * 9 * (size_t)m.T, cudaMemcpyDeviceToHost));
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_proxy(fsim_ctx_t ctx, int mesh_id, const double* x, double* s_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  if (!ms || !x || !s_out) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  TRY(stage_x(ctx, *ms, x));
+  launch_proxy(ctx->stream, m, m.xt, m.st);
+  CK(cudaMemcpyAsync(s_out, m.st, sizeof(double) * 3 * (size_t)m.Ns, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_contacts(fsim_ctx_t ctx, int mesh_id, const double* x, int32_t* keys,
+                               int64_t cap, int64_t* count, double* barrier_energy_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x || !count || (cap > 0 && !keys)) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  TRY(stage_x(ctx, *ms, x));
+  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  if (barrier_energy_out) *barrier_energy_out = ctx->h_scal[0];
+  return copy_keys(ctx, *ms, ctx->h_counters[0], keys, cap, count);
+}
+
+fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, double* grad_out,
+                              int32_t* n_c, int32_t* c_out, double* bcheck_out, int64_t bcheck_cap) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  cudaStream_t s = ctx->stream;
+  TRY(stage_x(ctx, *ms, x));
+  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  const int64_t np = ctx->h_counters[0];
+  // barrier gradient only: zero elastic forces by gathering a zero tetf
+  CK(cudaMemsetAsync(m.tetf_t, 0, sizeof(double) * 12 * (size_t)m.T, s));
+  int nc = 0;
+  double gn2 = 0.0;
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, true, &nc, &gn2));
+  if (n_c) *n_c = nc;
+  if (grad_out)
+    CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
+  if (c_out && nc > 0) CK(cudaMemcpy(c_out, m.clist, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+  if (bcheck_out) {
+    if ((int64_t)9 * nc * nc > bcheck_cap) return FSIM_EINVAL;
+    if (nc > 0)
+      CK(cudaMemcpy(bcheck_out, m.Bc, sizeof(double) * 9 * (size_t)nc * nc, cudaMemcpyDeviceToHost));
+  }
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, int precision,
+                                  double* dx_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x || !dx_out || (precision != 0 && precision != 1)) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  cudaStream_t s = ctx->stream;
+  TRY(stage_x(ctx, *ms, x));
+  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  const int64_t np = ctx->h_counters[0];
+  int nc = 0;
+  double gn2 = 0.0;
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, true, &nc, &gn2));
+  CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
+  global_step(s, m, ms->gtmp, ms->dxtmp, nc, precision, m.counters + 6, ctx->num_sms);
+  CK(cudaGetLastError());
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
+  CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_ccd(fsim_ctx_t ctx, int mesh_id, const double* x, const double* dx,
+                          double* alpha_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x || !dx || !alpha_out) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  cudaStream_t s = ctx->stream;
+  TRY(stage_x(ctx, *ms, x));
+  CK(cudaMemcpyAsync(ms->dxtmp, dx, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyHostToDevice, s));
+  launch_proxy(s, m, m.xt, m.st);
+  launch_proxy(s, m, ms->dxtmp, m.ds);
+  CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int) * 2, s));
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_ccd_candidates(s, m, m.st, m.ds, ms->p.dhat);
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  launch_ccd(s, m, m.st, m.ds, ms->p.dhat, ms->p.ccd_s, ms->p.accd_max_iters, ctx->h_counters[1]);
+  TRY(sync_read(ctx, m));
+  *alpha_out = ctx->h_scal[1];
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_energy(fsim_ctx_t ctx, int mesh_id, const double* x, int precision,
+                             double* energy_out, double* grad_norm_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  TRY(ready(ms));
+  if (!x || (precision != 0 && precision != 1)) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevMesh& m = ms->d;
+  TRY(stage_x(ctx, *ms, x));
+  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
+  const double E = ctx->h_scal[2] + ctx->h_scal[0];
+  const int64_t np = ctx->h_counters[0];
+  int nc = 0;
+  double gn2 = 0.0;
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, false, &nc, &gn2));
+  if (energy_out) *energy_out = E;
+  if (grad_norm_out) *grad_norm_out = std::sqrt(gn2);
+  return FSIM_OK;
+}
+
+fsim_status fsim_mesh_info_get(fsim_ctx_t ctx, int mesh_id, fsim_mesh_info* info) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  if (!ms || !info) return FSIM_EINVAL;
+  const DevMesh& m = ms->d;
+  info->n = m.n; info->T = m.T; info->Ns = m.Ns; info->Nt = m.Nt; info->Ne = m.Ne;
+  info->n_free = m.nf; info->n1 = m.n1; info->n2 = m.n2;
+  info->factor_nnz = ms->factor_nnz;
+  info->n_supernodes = m.n_sn;
+  info->n_levels = m.n_levels;
+  info->kappa = ms->kappa;
+  return FSIM_OK;
+}
+
+}  // extern "C"

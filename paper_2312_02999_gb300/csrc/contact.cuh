@@ -1,0 +1,419 @@
+// Point-triangle / edge-edge distance, closest-feature classification and the
+// PSD-projected IPC barrier Hessian of one pair (device, float64).
+//
+// Sec. 2.2: every vertex-triangle and edge-edge pair k of the proxy with
+// unsigned distance d_k < d0 contributes kappa * b(d_k) (Eq. 3).  Reading of
+// the unprinted barrier: b(d) = -(d - dhat)^2 ln(d / dhat).
+//
+// Distance structure used here: the closest points are an affine combination
+// v = sum_i c_i(beta) X_i of the pair's four vertices, with beta the k <= 2
+// free parameters of the closest-feature case (face interior: k = 2, edge
+// interior: k = 1, vertex: k = 0; edge-edge interior: k = 2 ...).  With
+// f(x, beta) = |v|^2 minimised over beta, the envelope theorem and implicit
+// differentiation give
+//   grad d^2 = 2 c (x) v,
+//   hess d^2 = 2 (c c^T) (x) I_3 - F (2 E^T E)^-1 F^T,
+//   F_k = 2 (c'_k (x) v + c (x) E_k),  E_k = sum_i c'_k[i] X_i = dv/dbeta_k.
+// Both live in the (3 + k)-dimensional span of {c^ (x) e_a} u {q_m (x) v^}
+// where (c^, q_1.. q_k) orthonormalises (c, c'_1.. c'_k) in R^4, so the 12x12
+// pair Hessian kappa (b'' grad d grad d^T + b' hess d) is formed, projected
+// onto the PSD cone (PositiveDefinite of Algorithm 1) and lifted back exactly
+// in that small basis.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace fsim {
+
+// Classification threshold for nearly parallel edges (no mollifier: those
+// pairs take the closest of the four endpoint-to-segment distances).
+#define FSIM_PARALLEL_EPS 1e-10
+
+struct PairGeom {
+  double c[4];      // affine coefficients, v = sum_i c_i X_i
+  double cp[2][4];  // d c / d beta_k
+  int k;            // number of free parameters (0..2)
+  double v[3];      // difference vector of the closest points
+  double d2;        // |v|^2
+};
+
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Closest point of segment [A, B] to P: clamped parameter and squared distance.
+__device__ __forceinline__ void seg_closest(const double* P, const double* A, const double* B,
+                                            double& t, double& d2) {
+  double e[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+  double r[3] = {P[0] - A[0], P[1] - A[1], P[2] - A[2]};
+  t = dot3(r, e) / dot3(e, e);
+  t = fmin(fmax(t, 0.0), 1.0);
+  double q[3] = {P[0] - (A[0] + t * e[0]), P[1] - (A[1] + t * e[1]), P[2] - (A[2] + t * e[2])};
+  d2 = dot3(q, q);
+}
+
+__device__ __forceinline__ void geom_finish(PairGeom& g, const double X[4][3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    g.v[d] = g.c[0] * X[0][d] + g.c[1] * X[1][d] + g.c[2] * X[2][d] + g.c[3] * X[3][d];
+  g.d2 = dot3(g.v, g.v);
+}
+
+// point X[0] vs triangle X[1..3]
+__device__ void pt_geometry(const double X[4][3], PairGeom& g) {
+  const double* p = X[0];
+  const double* a = X[1];
+  const double* b = X[2];
+  const double* c = X[3];
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double r[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double a11 = dot3(e1, e1), a12 = dot3(e1, e2), a22 = dot3(e2, e2);
+  double r1 = dot3(e1, r), r2 = dot3(e2, r);
+  double det = a11 * a22 - a12 * a12;
+  double u = (a22 * r1 - a12 * r2) / det;
+  double w = (a11 * r2 - a12 * r1) / det;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { g.c[i] = 0.0; g.cp[0][i] = 0.0; g.cp[1][i] = 0.0; }
+  if (u >= 0.0 && w >= 0.0 && u + w <= 1.0) {
+    g.k = 2;
+    g.c[0] = 1.0; g.c[1] = -(1.0 - u - w); g.c[2] = -u; g.c[3] = -w;
+    g.cp[0][1] = 1.0; g.cp[0][2] = -1.0;   // d/du
+    g.cp[1][1] = 1.0; g.cp[1][3] = -1.0;   // d/dw
+  } else {
+    double t0, d0, t1, d1, t2, d2;
+    seg_closest(p, a, b, t0, d0);
+    seg_closest(p, b, c, t1, d1);
+    seg_closest(p, c, a, t2, d2);
+    int k = 0; double t = t0, dm = d0;
+    if (d1 < dm) { k = 1; t = t1; dm = d1; }
+    if (d2 < dm) { k = 2; t = t2; dm = d2; }
+    const int ia = 1 + k, ib = 1 + (k + 1) % 3;   // pair-local ids of the edge
+    g.c[0] = 1.0;
+    if (t > 0.0 && t < 1.0) {
+      g.k = 1;
+      g.c[ia] = -(1.0 - t); g.c[ib] = -t;
+      g.cp[0][ia] = 1.0; g.cp[0][ib] = -1.0;
+    } else {
+      g.k = 0;
+      g.c[t <= 0.0 ? ia : ib] = -1.0;
+    }
+  }
+  geom_finish(g, X);
+}
+
+// edge X[0]X[1] vs edge X[2]X[3]
+__device__ void ee_geometry(const double X[4][3], PairGeom& g) {
+  const double* a0 = X[0];
+  const double* a1 = X[1];
+  const double* b0 = X[2];
+  const double* b1 = X[3];
+  double u[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+  double v[3] = {b1[0] - b0[0], b1[1] - b0[1], b1[2] - b0[2]};
+  double w0[3] = {a0[0] - b0[0], a0[1] - b0[1], a0[2] - b0[2]};
+  double A = dot3(u, u), B = dot3(u, v), C = dot3(v, v), D = dot3(u, w0), E = dot3(v, w0);
+  double den = A * C - B * B;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { g.c[i] = 0.0; g.cp[0][i] = 0.0; g.cp[1][i] = 0.0; }
+  bool interior = false;
+  if (den > FSIM_PARALLEL_EPS * A * C) {
+    double s = (B * E - C * D) / den;
+    double t = (A * E - B * D) / den;
+    if (s > 0.0 && s < 1.0 && t > 0.0 && t < 1.0) {
+      interior = true;
+      g.k = 2;
+      g.c[0] = 1.0 - s; g.c[1] = s; g.c[2] = -(1.0 - t); g.c[3] = -t;
+      g.cp[0][0] = -1.0; g.cp[0][1] = 1.0;
+      g.cp[1][2] = 1.0; g.cp[1][3] = -1.0;
+    }
+  }
+  if (!interior) {
+    double ta0, da0, ta1, da1, tb0, db0, tb1, db1;
+    seg_closest(a0, b0, b1, ta0, da0);
+    seg_closest(a1, b0, b1, ta1, da1);
+    seg_closest(b0, a0, a1, tb0, db0);
+    seg_closest(b1, a0, a1, tb1, db1);
+    int k = 0; double t = ta0, dm = da0;
+    if (da1 < dm) { k = 1; t = ta1; dm = da1; }
+    if (db0 < dm) { k = 2; t = tb0; dm = db0; }
+    if (db1 < dm) { k = 3; t = tb1; dm = db1; }
+    const bool mid = t > 0.0 && t < 1.0;
+    if (k < 2) {            // point a_k vs segment b: v = a_k - (b0 + t (b1 - b0))
+      g.c[k] = 1.0;
+      if (mid) {
+        g.k = 1; g.c[2] = -(1.0 - t); g.c[3] = -t;
+        g.cp[0][2] = 1.0; g.cp[0][3] = -1.0;
+      } else {
+        g.k = 0; g.c[t <= 0.0 ? 2 : 3] = -1.0;
+      }
+    } else {                // point b_(k-2) vs segment a: v = (a0 + t (a1 - a0)) - b
+      g.c[k] = -1.0;
+      if (mid) {
+        g.k = 1; g.c[0] = 1.0 - t; g.c[1] = t;
+        g.cp[0][0] = -1.0; g.cp[0][1] = 1.0;
+      } else {
+        g.k = 0; g.c[t <= 0.0 ? 0 : 1] = 1.0;
+      }
+    }
+  }
+  geom_finish(g, X);
+}
+
+__device__ __forceinline__ void pair_geometry(int type, const double X[4][3], PairGeom& g) {
+  if (type == 0) pt_geometry(X, g);
+  else ee_geometry(X, g);
+}
+
+__device__ __forceinline__ double pair_distance(int type, const double X[4][3]) {
+  PairGeom g;
+  pair_geometry(type, X, g);
+  return sqrt(g.d2);
+}
+
+// float32 distance of a pair given in coordinates relative to its first
+// vertex (rounding error ~1e-7 of the pair's own extent).  Used only as a
+// conservative filter: callers act on it only when it is far (>= 2x) from
+// the threshold they test, so the float64 decision is never changed.
+__device__ __forceinline__ float seg_d2f(const float* P, const float* A, const float* B) {
+  const float e0 = B[0] - A[0], e1 = B[1] - A[1], e2 = B[2] - A[2];
+  const float r0 = P[0] - A[0], r1 = P[1] - A[1], r2 = P[2] - A[2];
+  const float ee = e0 * e0 + e1 * e1 + e2 * e2;
+  float t = ee > 0.f ? (r0 * e0 + r1 * e1 + r2 * e2) / ee : 0.f;
+  t = fminf(fmaxf(t, 0.f), 1.f);
+  const float q0 = r0 - t * e0, q1 = r1 - t * e1, q2 = r2 - t * e2;
+  return q0 * q0 + q1 * q1 + q2 * q2;
+}
+
+__device__ float pair_distance_f(int type, const float X[4][3]) {
+  if (type == 0) {
+    const float* p = X[0]; const float* a = X[1]; const float* b = X[2]; const float* c = X[3];
+    const float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const float e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const float r[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    const float a11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    const float a12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    const float a22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    const float r1 = e1[0] * r[0] + e1[1] * r[1] + e1[2] * r[2];
+    const float r2 = e2[0] * r[0] + e2[1] * r[1] + e2[2] * r[2];
+    const float det = a11 * a22 - a12 * a12;
+    if (det > 0.f) {
+      const float u = (a22 * r1 - a12 * r2) / det, w = (a11 * r2 - a12 * r1) / det;
+      if (u >= 0.f && w >= 0.f && u + w <= 1.f) {
+        const float q0 = r[0] - u * e1[0] - w * e2[0], q1 = r[1] - u * e1[1] - w * e2[1],
+                    q2 = r[2] - u * e1[2] - w * e2[2];
+        return sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+      }
+    }
+    return sqrtf(fminf(fminf(seg_d2f(p, a, b), seg_d2f(p, b, c)), seg_d2f(p, c, a)));
+  }
+  const float* a0 = X[0]; const float* a1 = X[1]; const float* b0 = X[2]; const float* b1 = X[3];
+  const float u[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+  const float v[3] = {b1[0] - b0[0], b1[1] - b0[1], b1[2] - b0[2]};
+  const float w0[3] = {a0[0] - b0[0], a0[1] - b0[1], a0[2] - b0[2]};
+  const float A = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float B = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  const float C = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const float D = u[0] * w0[0] + u[1] * w0[1] + u[2] * w0[2];
+  const float E = v[0] * w0[0] + v[1] * w0[1] + v[2] * w0[2];
+  const float den = A * C - B * B;
+  if (den > 1e-6f * A * C) {
+    const float s = (B * E - C * D) / den, t = (A * E - B * D) / den;
+    if (s > 0.f && s < 1.f && t > 0.f && t < 1.f) {
+      const float q0 = w0[0] + s * u[0] - t * v[0], q1 = w0[1] + s * u[1] - t * v[1],
+                  q2 = w0[2] + s * u[2] - t * v[2];
+      return sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+    }
+  }
+  return sqrtf(fminf(fminf(seg_d2f(a0, b0, b1), seg_d2f(a1, b0, b1)),
+                     fminf(seg_d2f(b0, a0, a1), seg_d2f(b1, a0, a1))));
+}
+
+// X relative to its first vertex, in float32
+__device__ __forceinline__ void to_rel_f(const double X[4][3], float Y[4][3]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Y[k][d] = (float)(X[k][d] - X[0][d]);
+}
+
+// IPC barrier and its first two derivatives (reading of Eq. 3's b).
+__device__ __forceinline__ void barrier3(double d, double dhat, double& b, double& b1, double& b2) {
+  const double u = d - dhat;
+  const double L = log(d / dhat);
+  b = -u * u * L;
+  b1 = -2.0 * u * L - u * u / d;
+  b2 = -2.0 * L - 4.0 * u / d + u * u / (d * d);
+}
+
+__device__ __forceinline__ double barrier_value(double d, double dhat) {
+  if (!(d < dhat)) return 0.0;
+  const double u = d - dhat;
+  return -u * u * log(d / dhat);
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n (n <= 5) matrix A;
+// on return A holds the eigenvalues on its diagonal, Q the eigenvectors.
+__device__ void jacobi_sym(double A[5][5], double Q[5][5], int n) {
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) Q[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dia += A[i][i] * A[i][i];
+      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
+    }
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p][q];
+        if (fabs(apq) <= 1e-300) continue;
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        A[p][q] = 0.0; A[q][p] = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double qkp = Q[k][p], qkq = Q[k][q];
+          Q[k][p] = c * qkp - s * qkq;
+          Q[k][q] = s * qkp + c * qkq;
+        }
+      }
+  }
+}
+
+// Barrier gradient (per pair vertex, 4 x 3) and the 16 PSD Hessian blocks
+// H[i][j] (3x3, row-major) of kappa * b(d(X)) for a pair with d < dhat.
+// Returns d.
+__device__ double pair_barrier_psd(int type, const double X[4][3], double dhat, double kappa,
+                                   double grad[4][3], double H[4][4][9]) {
+  PairGeom g;
+  pair_geometry(type, X, g);
+  const double d = sqrt(g.d2);
+  double b, b1, b2;
+  barrier3(d, dhat, b, b1, b2);
+  const int k = g.k, n = 3 + k;
+  // orthonormal (c^, q_1 .. q_k) in R^4
+  double cn = sqrt(g.c[0] * g.c[0] + g.c[1] * g.c[1] + g.c[2] * g.c[2] + g.c[3] * g.c[3]);
+  double ch[4], q[2][4];
+  for (int i = 0; i < 4; ++i) ch[i] = g.c[i] / cn;
+  double qc[2][2] = {{0, 0}, {0, 0}};   // q_m . c'_k
+  double chc[2] = {0, 0};                // c^ . c'_k
+  for (int m = 0; m < k; ++m) {
+    double r[4];
+    for (int i = 0; i < 4; ++i) r[i] = g.cp[m][i];
+    double a = 0;
+    for (int i = 0; i < 4; ++i) a += ch[i] * r[i];
+    for (int i = 0; i < 4; ++i) r[i] -= a * ch[i];
+    for (int l = 0; l < m; ++l) {
+      double bq = 0;
+      for (int i = 0; i < 4; ++i) bq += q[l][i] * r[i];
+      for (int i = 0; i < 4; ++i) r[i] -= bq * q[l][i];
+    }
+    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    for (int i = 0; i < 4; ++i) q[m][i] = r[i] / rn;
+  }
+  for (int kk = 0; kk < k; ++kk) {
+    double s = 0;
+    for (int i = 0; i < 4; ++i) s += ch[i] * g.cp[kk][i];
+    chc[kk] = s;
+    for (int m = 0; m < k; ++m) {
+      double t = 0;
+      for (int i = 0; i < 4; ++i) t += q[m][i] * g.cp[kk][i];
+      qc[m][kk] = t;
+    }
+  }
+  double E[2][3];
+  for (int kk = 0; kk < k; ++kk)
+    for (int dd = 0; dd < 3; ++dd)
+      E[kk][dd] = g.cp[kk][0] * X[0][dd] + g.cp[kk][1] * X[1][dd] + g.cp[kk][2] * X[2][dd] +
+                  g.cp[kk][3] * X[3][dd];
+  // reduced hess d^2: diag(2|c|^2 I3, 0) - F (2 E^T E)^-1 F^T
+  double Hd2[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) Hd2[i][j] = 0.0;
+  for (int a = 0; a < 3; ++a) Hd2[a][a] = 2.0 * cn * cn;
+  if (k > 0) {
+    const double vn = sqrt(g.d2);
+    double Fr[5][2];
+    for (int kk = 0; kk < k; ++kk) {
+      for (int a = 0; a < 3; ++a) Fr[a][kk] = 2.0 * (chc[kk] * g.v[a] + cn * E[kk][a]);
+      for (int m = 0; m < k; ++m) Fr[3 + m][kk] = 2.0 * qc[m][kk] * vn;
+    }
+    double G[2][2], Gi[2][2];
+    for (int a = 0; a < k; ++a)
+      for (int bb = 0; bb < k; ++bb) G[a][bb] = 2.0 * dot3(E[a], E[bb]);
+    if (k == 1) {
+      Gi[0][0] = 1.0 / G[0][0];
+    } else {
+      const double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+      Gi[0][0] = G[1][1] / det; Gi[1][1] = G[0][0] / det;
+      Gi[0][1] = -G[0][1] / det; Gi[1][0] = -G[1][0] / det;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < k; ++a)
+          for (int bb = 0; bb < k; ++bb) s += Fr[i][a] * Gi[a][bb] * Fr[j][bb];
+        Hd2[i][j] -= s;
+      }
+  }
+  // grad d = (|c| v^, 0); hess d = hess d^2/(2d) - (|c|^2 v^ v^T (+) 0)/d
+  double vh[3] = {g.v[0] / d, g.v[1] / d, g.v[2] / d};
+  double gr[5] = {cn * vh[0], cn * vh[1], cn * vh[2], 0.0, 0.0};
+  double A[5][5], Q[5][5];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double hdd = Hd2[i][j] / (2.0 * d) - (i < 3 && j < 3 ? cn * cn * vh[i] * vh[j] / d : 0.0);
+      A[i][j] = kappa * (b2 * gr[i] * gr[j] + b1 * hdd);
+    }
+  for (int i = n; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) { A[i][j] = 0.0; A[j][i] = 0.0; }
+  jacobi_sym(A, Q, n);
+  double Hp[5][5];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < n; ++l) {
+        const double lam = A[l][l];
+        if (lam > 0.0) s += Q[i][l] * lam * Q[j][l];
+      }
+      Hp[i][j] = s;
+    }
+  // gradient per vertex: kappa b' c_i v^
+  for (int i = 0; i < 4; ++i)
+    for (int dd = 0; dd < 3; ++dd) grad[i][dd] = kappa * b1 * g.c[i] * vh[dd];
+  // lift: block(i,j) = c^_i c^_j Hcc + c^_i h_j v^T + c^_j v^ h_i^T + s_ij v^ v^T
+  double hv[4][3], sq[4][4];
+  for (int i = 0; i < 4; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int m = 0; m < k; ++m) s += q[m][i] * Hp[a][3 + m];
+      hv[i][a] = s;
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < k; ++m)
+        for (int l = 0; l < k; ++l) s += q[m][i] * q[l][j] * Hp[3 + m][3 + l];
+      sq[i][j] = s;
+    }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int a = 0; a < 3; ++a)
+        for (int bb = 0; bb < 3; ++bb)
+          H[i][j][3 * a + bb] = ch[i] * ch[j] * Hp[a][bb] + ch[i] * hv[j][a] * vh[bb] +
+                                ch[j] * vh[a] * hv[i][bb] + sq[i][j] * vh[a] * vh[bb];
+  return d;
+}
+
+}  // namespace fsim

@@ -1,0 +1,325 @@
+// Local step of Algorithm 1 (GetProjection, Eq. 1 and Sec. 2.1) fused with
+// the elastic energy and the per-tet elastic forces of Eq. 4.
+//
+// Per tet i: F = Ds Dm^-1, M = F A (A symmetric), R = polar rotation of M,
+// p = vec(R A), D = F - R A, energy 1/2 w |D|_F^2 and the gradient
+// contribution w D gradN_a of each of its four vertices (the row form of
+// w_i G_i^T (G_i x - p_i)).  Forces are written per tet and gathered per
+// vertex in a fixed order (deterministic sums, no atomics).
+#include <cstdio>
+#include <vector>
+
+#include "kernels.h"
+#include "mat3.cuh"
+
+namespace fsim {
+
+namespace {
+std::int64_t g_launches = 0;
+
+// event-pair pool for ProfScope; resolved (summed per class) in prof_read
+struct Prof {
+  unsigned mask = 0;
+  std::vector<cudaEvent_t> ev0, ev1;
+  std::vector<int> cls;
+  std::vector<int> free_slots, pending;
+  int64_t launches[PROF_NCLASS] = {0};
+  double ms[PROF_NCLASS] = {0};
+} g_prof;
+
+void prof_resolve() {
+  for (int slot : g_prof.pending) {
+    cudaEventSynchronize(g_prof.ev1[slot]);
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_prof.ev0[slot], g_prof.ev1[slot]) == cudaSuccess) {
+      g_prof.ms[g_prof.cls[slot]] += t;
+      g_prof.launches[g_prof.cls[slot]] += 1;
+    }
+    g_prof.free_slots.push_back(slot);
+  }
+  g_prof.pending.clear();
+}
+}  // namespace
+
+int64_t launch_counter() { return g_launches; }
+void count_launch(int k) { g_launches += k; }
+
+ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
+  if (!(g_prof.mask & (1u << c))) return;
+  if (g_prof.pending.size() >= 4096) prof_resolve();
+  if (g_prof.free_slots.empty()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    g_prof.ev0.push_back(a); g_prof.ev1.push_back(b); g_prof.cls.push_back(c);
+    g_prof.free_slots.push_back((int)g_prof.ev0.size() - 1);
+  }
+  slot = g_prof.free_slots.back();
+  g_prof.free_slots.pop_back();
+  g_prof.cls[slot] = c;
+  cudaEventRecord(g_prof.ev0[slot], s);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  cudaEventRecord(g_prof.ev1[slot], stream);
+  g_prof.pending.push_back(slot);
+}
+
+void prof_set_mask(unsigned mask) { g_prof.mask = mask; }
+
+int prof_read(int c, int64_t* launches, double* total_ms) {
+  if (c < 0 || c >= PROF_NCLASS) return -1;
+  prof_resolve();
+  *launches = g_prof.launches[c];
+  *total_ms = g_prof.ms[c];
+  return 0;
+}
+
+void prof_reset() {
+  prof_resolve();
+  for (int c = 0; c < PROF_NCLASS; ++c) { g_prof.launches[c] = 0; g_prof.ms[c] = 0.0; }
+}
+
+constexpr int kElasticThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;   // valid in thread 0
+}
+
+__global__ void k_actuation(int T, const double* __restrict__ fiber,
+                            const double* __restrict__ stretch, double* __restrict__ act) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double f0 = fiber[3 * t], f1 = fiber[3 * t + 1], f2 = fiber[3 * t + 2];
+  const double nn = sqrt(f0 * f0 + f1 * f1 + f2 * f2);
+  f0 /= nn; f1 /= nn; f2 /= nn;
+  const double a = stretch[t];
+  const double b = 1.0 / sqrt(a);          // transverse stretch a^(-1/2)
+  const double k = a - b;
+  act[0 * T + t] = b + k * f0 * f0;
+  act[1 * T + t] = k * f0 * f1;
+  act[2 * T + t] = k * f0 * f2;
+  act[3 * T + t] = b + k * f1 * f1;
+  act[4 * T + t] = k * f1 * f2;
+  act[5 * T + t] = b + k * f2 * f2;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kElasticThreads)
+k_elastic(int T, const int4* __restrict__ tets, const double* __restrict__ dminv,
+          const double* __restrict__ w, const double* __restrict__ act,
+          const double* __restrict__ x, double* __restrict__ tetf,
+          double* __restrict__ proj, double* __restrict__ partials) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (t < T) {
+    const int4 tv = tets[t];
+    const double* x0 = x + 3 * (size_t)tv.x;
+    const double* x1 = x + 3 * (size_t)tv.y;
+    const double* x2 = x + 3 * (size_t)tv.z;
+    const double* x3 = x + 3 * (size_t)tv.w;
+    double Ds[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double o = x0[d];
+      Ds[d][0] = x1[d] - o;
+      Ds[d][1] = x2[d] - o;
+      Ds[d][2] = x3[d] - o;
+    }
+    double Di[3][3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Di[k / 3][k % 3] = dminv[(size_t)k * T + t];
+    double F[3][3];
+    matmul(Ds, Di, F);
+    double A[3][3];
+    A[0][0] = act[0 * (size_t)T + t];
+    A[0][1] = A[1][0] = act[1 * (size_t)T + t];
+    A[0][2] = A[2][0] = act[2 * (size_t)T + t];
+    A[1][1] = act[3 * (size_t)T + t];
+    A[1][2] = A[2][1] = act[4 * (size_t)T + t];
+    A[2][2] = act[5 * (size_t)T + t];
+    double M[3][3], R[3][3];
+    matmul(F, A, M);
+    if (PREC == 0) {
+      polar_rotation<double, 10>(M, R);
+    } else {
+      float Mf[3][3], Rf[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mf[i][j] = (float)M[i][j];
+      polar_rotation<float, 6>(Mf, Rf);
+      double R0[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) R0[i][j] = (double)Rf[i][j];
+      polar_refine(M, R0, R);
+    }
+    double P[3][3];
+    matmul(R, A, P);
+    const double wt = w[t];
+    double Dd[3][3];
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Dd[i][j] = F[i][j] - P[i][j];
+        s += Dd[i][j] * Dd[i][j];
+      }
+    e = 0.5 * wt * s;
+    // f_a = w D gradN_a, gradN_a = row a-1 of Dm^-1 (a = 1..3), f_0 = -sum
+    double f0[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double fa = wt * (Dd[d][0] * Di[a - 1][0] + Dd[d][1] * Di[a - 1][1] + Dd[d][2] * Di[a - 1][2]);
+        tetf[(size_t)(a * 3 + d) * T + t] = fa;
+        f0[d] -= fa;
+      }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) tetf[(size_t)d * T + t] = f0[d];
+    if (proj != nullptr) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) proj[(size_t)9 * t + k] = P[k / 3][k % 3];
+    }
+  }
+  const double bs = block_sum(e);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+__global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
+                                const int* __restrict__ vslot, const double* __restrict__ tetf,
+                                const uint8_t* __restrict__ pinned, double* __restrict__ g) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  if (!pinned[v]) {
+    for (int e = vptr[v]; e < vptr[v + 1]; ++e) {
+      const int slot = vslot[e];
+      const int t = slot >> 2, a = slot & 3;
+      s0 += tetf[(size_t)(a * 3 + 0) * T + t];
+      s1 += tetf[(size_t)(a * 3 + 1) * T + t];
+      s2 += tetf[(size_t)(a * 3 + 2) * T + t];
+    }
+  }
+  g[3 * (size_t)v + 0] = s0;
+  g[3 * (size_t)v + 1] = s1;
+  g[3 * (size_t)v + 2] = s2;
+}
+
+// Fixed-order sum of n partials by one block (deterministic).
+__global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_axpy(int n3, const double* __restrict__ x, const double* __restrict__ dx,
+                       const double* __restrict__ alpha, double scale, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const double a = alpha[0] * scale;
+  out[i] = x[i] + a * dx[i];
+}
+
+__global__ void k_gnorm2(int n, const double* __restrict__ g, const uint8_t* __restrict__ pinned,
+                         double* __restrict__ partials) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (v < n && !pinned[v]) {
+    const double a = g[3 * (size_t)v], b = g[3 * (size_t)v + 1], c = g[3 * (size_t)v + 2];
+    s = a * a + b * b + c * c;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_reset_pinned(int n, const uint8_t* __restrict__ pinned,
+                               const double* __restrict__ rest, double* __restrict__ x) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n || !pinned[v]) return;
+  x[3 * (size_t)v] = rest[3 * (size_t)v];
+  x[3 * (size_t)v + 1] = rest[3 * (size_t)v + 1];
+  x[3 * (size_t)v + 2] = rest[3 * (size_t)v + 2];
+}
+
+__global__ void k_check_finite(int n, const double* __restrict__ v, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(v[i])) atomicOr(flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act) {
+  k_actuation<<<(T + 255) / 256, 256, 0, s>>>(T, fiber, stretch, act);
+  count_launch();
+}
+
+int elastic_blocks(int T) { return (T + kElasticThreads - 1) / kElasticThreads; }
+
+void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* tetf,
+                    double* proj, double* partials, int precision) {
+  const int nb = elastic_blocks(m.T);
+  ProfScope ps(PROF_ELASTIC, s);
+  if (precision == 0)
+    k_elastic<0><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
+  else
+    k_elastic<1><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
+  count_launch();
+}
+
+void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g) {
+  k_gather_forces<<<(m.n + 255) / 256, 256, 0, s>>>(m.n, m.T, m.vinc_ptr, m.vinc_slot, tetf,
+                                                    m.pinned, g);
+  count_launch();
+}
+
+void launch_sum_partials(cudaStream_t s, const double* partials, int n, double* out) {
+  k_sum_partials<<<1, 1024, 0, s>>>(partials, n, out);
+  count_launch();
+}
+
+void launch_axpy_positions(cudaStream_t s, int n3, const double* x, const double* dx,
+                           const double* alpha_dev, double alpha_scale, double* out) {
+  k_axpy<<<(n3 + 255) / 256, 256, 0, s>>>(n3, x, dx, alpha_dev, alpha_scale, out);
+  count_launch();
+}
+
+int gnorm_blocks(int n) { return (n + 255) / 256; }
+
+void launch_gnorm2(cudaStream_t s, const DevMesh& m, const double* g, double* partials, int nblk) {
+  k_gnorm2<<<nblk, 256, 0, s>>>(m.n, g, m.pinned, partials);
+  count_launch();
+}
+
+void launch_reset_pinned(cudaStream_t s, const DevMesh& m, double* x) {
+  k_reset_pinned<<<(m.n + 255) / 256, 256, 0, s>>>(m.n, m.pinned, m.rest, x);
+  count_launch();
+}
+
+void launch_check_finite(cudaStream_t s, int n, const double* v, int* flag) {
+  if (n <= 0) return;
+  k_check_finite<<<(n + 255) / 256, 256, 0, s>>>(n, v, flag);
+  count_launch();
+}
+
+}  // namespace fsim

@@ -1,0 +1,151 @@
+// Device-side mesh state and the host-callable kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsim {
+
+// All device pointers of one mesh (owned by the context, see capi.cu).
+struct DevMesh {
+  int n = 0, T = 0, Ns = 0, Nt = 0, Ne = 0;
+  int nf = 0, n1 = 0, n2 = 0;
+  // vertices (AoS xyz)
+  double* rest = nullptr;
+  double* x = nullptr;        // current iterate
+  double* xt = nullptr;       // line-search trial
+  double* dx = nullptr;       // search direction
+  double* g = nullptr;        // gradient g-hat (by vertex)
+  uint8_t* pinned = nullptr;
+  // tets
+  int4* tets = nullptr;
+  double* dminv = nullptr;    // 9T SoA: Dm^-1 (row-major entry k at k*T + t)
+  double* w = nullptr;        // T
+  double* act = nullptr;      // 6T SoA: A00 A01 A02 A11 A12 A22
+  double* tetf = nullptr;     // 12T SoA per-tet vertex forces ((a*3+d)*T + t)
+  double* tetf_t = nullptr;   // same at the trial point
+  int* vinc_ptr = nullptr;    // vertex -> incident (t*4 + a) slots
+  int* vinc_slot = nullptr;
+  // proxy
+  int64_t* Wptr = nullptr;
+  int* Wcol = nullptr;
+  double* Wval = nullptr;
+  int* tris = nullptr;        // 3 Nt
+  int* edges = nullptr;       // 2 Ne (lo, hi), sorted unique
+  double* s = nullptr;        // 3 Ns proxy positions at x
+  double* st = nullptr;       // 3 Ns proxy positions at the trial point
+  double* ds = nullptr;       // 3 Ns proxy step
+  float* box = nullptr;       // scratch boxes (6 floats per primitive)
+  // solver ordering
+  int* perm = nullptr;        // nf: position -> vertex
+  int* pos = nullptr;         // n: vertex -> position or -1
+  int* x2of = nullptr;        // n: vertex -> x2 index or -1
+  // factor of K11
+  int n_sn = 0, n_levels = 0, max_ns = 0, max_ld = 0;
+  int* sn_c0 = nullptr; int* sn_ns = nullptr; int* sn_nr1 = nullptr;
+  int64_t* sn_roff = nullptr; int64_t* sn_zoff = nullptr;
+  int* sn_rows = nullptr;
+  double* Z = nullptr;
+  float* Zf = nullptr;
+  int* level_sn = nullptr;    // supernodes grouped by level
+  int* h_level_ptr = nullptr; // HOST array (n_levels + 1)
+  int* h_level_maxns = nullptr;  // HOST: largest ns per level
+  int* h_level_maxld = nullptr;  // HOST: largest ns + nr1 per level
+  int4* fwd_items = nullptr;  // (J, first row, rows, 0) work items, grouped by level
+  int4* bwd_items = nullptr;  // (J, first column, columns, 0)
+  int* h_fwd_ptr = nullptr;   // HOST (n_levels + 1)
+  int* h_bwd_ptr = nullptr;   // HOST (n_levels + 1)
+  double* y1 = nullptr;       // n1*3 forward-solve scratch
+  float* y1f = nullptr;
+  // couplings
+  int* k12_ptr = nullptr; int* k12_col = nullptr; double* k12_val = nullptr;
+  int* k21_ptr = nullptr; int* k21_col = nullptr; double* k21_val = nullptr;
+  double* Sinv = nullptr;     // n2 x n2
+  float* Sinvf = nullptr;
+  // global-step work (solver positions, AoS 3)
+  double* r = nullptr;        // nf*3
+  double* t1 = nullptr;       // n1*3
+  double* u = nullptr;        // n2*3
+  float* rf = nullptr;        // nf*3 (mixed)
+  // contact work
+  int64_t cap = 0;            // pair capacity
+  unsigned long long* pairs = nullptr;    // keys (type<<62 | i<<31 | j)
+  unsigned long long* cand = nullptr;     // CCD candidates
+  int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite
+  double* scal = nullptr;     // [0] barrier energy [1] alpha [2] elastic energy [3] gnorm2 ...
+  double* partials = nullptr; // block partial sums
+  int n_partials = 0;
+  double* pair_grad = nullptr;   // cap * 12
+  double* pair_hess = nullptr;   // cap * 144
+  int* x2mark = nullptr;      // n2 (touched flags -> c positions)
+  int* clist = nullptr;       // n2 (contact-affected x2 indices)
+  // reduced system (capacity n2)
+  double* Bc = nullptr;       // (3 n2)^2 dense B-check
+  int* bocc = nullptr;        // n2*n2 block occupancy
+  double* red = nullptr;      // work for the reduced system
+  float* redf = nullptr;
+  int64_t red_cap = 0;        // elements of red / redf
+  int nc_cap = 0;             // n_c the reduced buffers are sized for
+};
+
+// ---- local step (k_local.cu) ---------------------------------------------
+void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act);
+// precision 0: float64 SVD; 1: float32 SVD + float64 polar refinement.
+void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* tetf,
+                    double* proj, double* partials, int precision);
+int elastic_blocks(int T);
+void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g);
+void launch_sum_partials(cudaStream_t s, const double* partials, int n, double* out);
+
+// ---- contact (k_contact.cu) -----------------------------------------------
+void launch_proxy(cudaStream_t s, const DevMesh& m, const double* x, double* sp);
+// Constraint set at proxy positions sp; appends keys to m.pairs and adds the
+// barrier energy to m.scal[0].
+void launch_detect(cudaStream_t s, const DevMesh& m, const double* sp, double dhat, double kappa);
+// Candidate pairs of the swept boxes sp -> sp + dsp (inflated by dhat) and
+// the ACCD time of impact (min into m.scal[1] as ordered bits).
+void launch_ccd(cudaStream_t s, const DevMesh& m, const double* sp, const double* dsp,
+                double dhat, double ccd_s, int accd_max_iters, int64_t ncand_host);
+void launch_ccd_candidates(cudaStream_t s, const DevMesh& m, const double* sp, const double* dsp,
+                           double dhat);
+// Per-pair barrier gradient and PSD Hessian blocks (pass A) and x2 marks.
+void launch_barrier_pairs(cudaStream_t s, const DevMesh& m, int64_t npairs, const double* sp,
+                          double dhat, double kappa);
+void launch_mark_scan(cudaStream_t s, const DevMesh& m);
+// Scatter pair gradients into g and Hessian blocks into the dense B-check (3nc)^2.
+void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, int nc, double* g);
+
+// ---- global step (k_solve.cu) ----------------------------------------------
+// dx (by vertex) solving (H + B) dx = -g, with B-check already assembled for nc.
+void global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
+                 int precision, int* info_dev, int num_sms);
+int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
+void set_solver_smem_limits(int max_bytes);
+
+// ---- misc ------------------------------------------------------------------
+void launch_axpy_positions(cudaStream_t s, int n3, const double* x, const double* dx,
+                           const double* alpha_dev, double alpha_scale, double* out);
+void launch_gnorm2(cudaStream_t s, const DevMesh& m, const double* g, double* partials, int nblk);
+int gnorm_blocks(int n);
+void launch_reset_pinned(cudaStream_t s, const DevMesh& m, double* x);
+void launch_check_finite(cudaStream_t s, int n, const double* v, int* flag);
+
+// number of kernel launches issued through these launchers (per process)
+int64_t launch_counter();
+void count_launch(int k = 1);
+
+// Optional CUDA-event timing of kernel classes (see fsim_profile in fsim.h).
+enum ProfClass {
+  PROF_ELASTIC = 0, PROF_DETECT = 1, PROF_TRSV_FWD = 2, PROF_TRSV_BWD = 3, PROF_CHOL = 4,
+  PROF_BARRIER = 5, PROF_CCD = 6, PROF_GEMV = 7, PROF_REDUCED = 8, PROF_NCLASS = 9
+};
+struct ProfScope {
+  ProfScope(int cls, cudaStream_t s);
+  ~ProfScope();
+  int slot;
+  cudaStream_t stream;
+};
+void prof_set_mask(unsigned mask);
+int prof_read(int cls, int64_t* launches, double* total_ms);
+void prof_reset();
+
+}  // namespace fsim

@@ -1,0 +1,345 @@
+"""Thin ctypes binding of the fsim C ABI (include/fsim.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library
+``libfsim.so`` (built in-tree by ``paper_2312_02999_gb300.build``).  There is
+no CPU fallback: importing this module without the library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsim.so")
+
+FSIM_OK = 0
+FSIM_EINVAL = -1
+FSIM_ENOMEM = -2
+FSIM_ECUDA = -3
+FSIM_ENOT_SPD = -4
+FSIM_ENOT_CONVERGED = -5
+FSIM_ELS_FAIL = -6
+FSIM_ECONTACT_OVERFLOW = -7
+FSIM_ENONFINITE = -8
+FSIM_EINTERSECTING = -9
+FSIM_ENOT_READY = -10
+FP64 = 0
+MIXED = 1
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOT_SPD",
+                -5: "ENOT_CONVERGED", -6: "ELS_FAIL", -7: "ECONTACT_OVERFLOW",
+                -8: "ENONFINITE", -9: "EINTERSECTING", -10: "ENOT_READY"}
+
+
+class FsimError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what} failed: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("weight_scale", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
+                ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int32),
+                ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
+                ("reserved0", C.c_int32), ("contact_capacity", C.c_int64)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("ls_trials", C.c_int32),
+                ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("reserved0", C.c_int32),
+                ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
+                ("energy", C.c_double), ("alpha_min", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("n", "T", "Ns", "Nt", "Ne", "n_free", "n1", "n2",
+                                         "factor_nnz", "n_supernodes", "n_levels")] + \
+               [("kappa", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_U8 = C.POINTER(C.c_uint8)
+
+_SIGS = {
+    "fsim_default_params": [C.POINTER(Params)],
+    "fsim_create": [C.POINTER(_P), C.c_int],
+    "fsim_destroy": [_P],
+    "fsim_launch_count": [_P, _I64],
+    "fsim_mesh_upload": [_P, C.POINTER(C.c_int), _D, C.c_int64, _I32, C.c_int64, _U8, _I32,
+                         C.c_int64, _I64, _I32, _D, C.c_int64, _U8],
+    "fsim_prefactor": [_P, C.c_int, C.POINTER(Params)],
+    "fsim_set_actuation": [_P, C.c_int, _D, _D],
+    "fsim_solve_frame": [_P, C.c_int, _D, C.c_int, C.POINTER(FrameStats)],
+    "fsim_solve_frame_dev": [_P, C.c_int, C.c_void_p, C.c_int, C.POINTER(FrameStats)],
+    "fsim_read_positions": [_P, C.c_int, _D],
+    "fsim_read_positions_dev": [_P, C.c_int, C.c_void_p],
+    "fsim_read_contacts": [_P, C.c_int, _I32, C.c_int64, _I64],
+    "fsim_eval_elastic": [_P, C.c_int, _D, C.c_int, _D, _D, _D],
+    "fsim_eval_proxy": [_P, C.c_int, _D, _D],
+    "fsim_eval_contacts": [_P, C.c_int, _D, _I32, C.c_int64, _I64, _D],
+    "fsim_eval_barrier": [_P, C.c_int, _D, _D, _I32, _I32, _D, C.c_int64],
+    "fsim_eval_global_step": [_P, C.c_int, _D, C.c_int, _D],
+    "fsim_eval_ccd": [_P, C.c_int, _D, _D, _D],
+    "fsim_eval_energy": [_P, C.c_int, _D, C.c_int, _D, _D],
+    "fsim_mesh_info_get": [_P, C.c_int, C.POINTER(MeshInfo)],
+    "fsim_set_actuation_dev": [_P, C.c_int, C.c_void_p, C.c_void_p],
+    "fsim_get_stream": [_P, C.POINTER(C.c_void_p)],
+    "fsim_profile": [_P, C.c_uint32],
+    "fsim_profile_read": [_P, C.c_int, _I64, _D],
+    "fsim_profile_reset": [_P],
+}
+
+PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
+                "sigma_gemv", "reduced"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfsim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_2312_02999_gb300.build)")
+    lib = C.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _d(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _i32(a):
+    return a.ctypes.data_as(_I32) if a is not None else None
+
+
+def _chk(st, what):
+    if st != FSIM_OK:
+        raise FsimError(st, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _chk(load().fsim_default_params(C.byref(p)), "fsim_default_params")
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One fsim context on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = _P()
+        _chk(self.lib.fsim_create(C.byref(h), int(device)), "fsim_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.fsim_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        v = C.c_int64()
+        _chk(self.lib.fsim_launch_count(self.h, C.byref(v)), "fsim_launch_count")
+        return int(v.value)
+
+    def stream_ptr(self) -> int:
+        v = C.c_void_p()
+        _chk(self.lib.fsim_get_stream(self.h, C.byref(v)), "fsim_get_stream")
+        return int(v.value or 0)
+
+    def profile(self, mask: int):
+        _chk(self.lib.fsim_profile(self.h, int(mask)), "fsim_profile")
+
+    def profile_reset(self):
+        _chk(self.lib.fsim_profile_reset(self.h), "fsim_profile_reset")
+
+    def profile_read(self, cls: int):
+        n = C.c_int64()
+        ms = C.c_double()
+        _chk(self.lib.fsim_profile_read(self.h, int(cls), C.byref(n), C.byref(ms)),
+             "fsim_profile_read")
+        return int(n.value), float(ms.value)
+
+    def upload(self, mesh) -> "Mesh":
+        rest = np.ascontiguousarray(mesh.rest, dtype=np.float64)
+        tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+        pinned = np.ascontiguousarray(mesh.pinned, dtype=np.uint8)
+        tris = np.ascontiguousarray(mesh.proxy_tris, dtype=np.int32)
+        rp = np.ascontiguousarray(mesh.W_rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(mesh.W_col, dtype=np.int32)
+        val = np.ascontiguousarray(mesh.W_val, dtype=np.float64)
+        region = None if mesh.region is None else np.ascontiguousarray(mesh.region, dtype=np.uint8)
+        mid = C.c_int()
+        st = self.lib.fsim_mesh_upload(
+            self.h, C.byref(mid), _d(rest), rest.shape[0], _i32(tets), tets.shape[0],
+            pinned.ctypes.data_as(_U8), _i32(tris), tris.shape[0], rp.ctypes.data_as(_I64),
+            _i32(col), _d(val), rp.shape[0] - 1,
+            region.ctypes.data_as(_U8) if region is not None else None)
+        _chk(st, "fsim_mesh_upload")
+        return Mesh(self, mid.value, rest.shape[0], tets.shape[0], rp.shape[0] - 1)
+
+
+class Mesh:
+    """A mesh resident in a Context (thin wrapper over the mesh id)."""
+
+    def __init__(self, ctx: Context, mid: int, n: int, T: int, Ns: int):
+        self.ctx, self.id, self.n, self.T, self.Ns = ctx, mid, n, T, Ns
+        self.lib = ctx.lib
+
+    def prefactor(self, params: Params):
+        _chk(self.lib.fsim_prefactor(self.ctx.h, self.id, C.byref(params)), "fsim_prefactor")
+
+    def set_actuation(self, fiber, stretch):
+        f = np.ascontiguousarray(fiber, dtype=np.float64)
+        a = np.ascontiguousarray(stretch, dtype=np.float64)
+        _chk(self.lib.fsim_set_actuation(self.ctx.h, self.id, _d(f), _d(a)), "fsim_set_actuation")
+
+    def set_actuation_dev(self, fiber_ptr: int, stretch_ptr: int):
+        _chk(self.lib.fsim_set_actuation_dev(self.ctx.h, self.id, C.c_void_p(fiber_ptr),
+                                             C.c_void_p(stretch_ptr)), "fsim_set_actuation_dev")
+
+    def info(self) -> dict:
+        i = MeshInfo()
+        _chk(self.lib.fsim_mesh_info_get(self.ctx.h, self.id, C.byref(i)), "fsim_mesh_info_get")
+        return i.as_dict()
+
+    def solve_frame(self, x_init=None, precision=FP64, check=True):
+        """Returns (status, stats dict); positions stay resident."""
+        st = FrameStats()
+        x = None if x_init is None else np.ascontiguousarray(x_init, dtype=np.float64).reshape(-1)
+        rc = self.lib.fsim_solve_frame(self.ctx.h, self.id, _d(x), int(precision), C.byref(st))
+        if check and rc not in (FSIM_OK,):
+            raise FsimError(rc, "fsim_solve_frame")
+        return rc, st.as_dict()
+
+    def solve_frame_dev(self, x_init_ptr=None, precision=FP64):
+        st = FrameStats()
+        rc = self.lib.fsim_solve_frame_dev(self.ctx.h, self.id,
+                                           C.c_void_p(x_init_ptr) if x_init_ptr else None,
+                                           int(precision), C.byref(st))
+        return rc, st.as_dict()
+
+    def positions(self) -> np.ndarray:
+        out = np.empty((self.n, 3))
+        _chk(self.lib.fsim_read_positions(self.ctx.h, self.id, _d(out)), "fsim_read_positions")
+        return out
+
+    def read_positions_dev(self, ptr: int):
+        _chk(self.lib.fsim_read_positions_dev(self.ctx.h, self.id, C.c_void_p(ptr)),
+             "fsim_read_positions_dev")
+
+    def contacts(self, cap: int = 1 << 22):
+        keys = np.empty((cap, 3), dtype=np.int32)
+        cnt = C.c_int64()
+        _chk(self.lib.fsim_read_contacts(self.ctx.h, self.id, _i32(keys), cap, C.byref(cnt)),
+             "fsim_read_contacts")
+        return keys[: cnt.value].copy()
+
+    # ---- step-level entry points ------------------------------------------
+    def _x(self, x):
+        return np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+
+    def eval_elastic(self, x, precision=FP64, want_proj=False):
+        xx = self._x(x)
+        E = C.c_double()
+        g = np.empty((self.n, 3))
+        P = np.empty((self.T, 9)) if want_proj else None
+        _chk(self.lib.fsim_eval_elastic(self.ctx.h, self.id, _d(xx), int(precision), C.byref(E),
+                                        _d(g), _d(P)), "fsim_eval_elastic")
+        return (E.value, g, P) if want_proj else (E.value, g)
+
+    def eval_proxy(self, x):
+        xx = self._x(x)
+        s = np.empty((self.Ns, 3))
+        _chk(self.lib.fsim_eval_proxy(self.ctx.h, self.id, _d(xx), _d(s)), "fsim_eval_proxy")
+        return s
+
+    def eval_contacts(self, x, cap: int = 1 << 22):
+        xx = self._x(x)
+        keys = np.empty((cap, 3), dtype=np.int32)
+        cnt = C.c_int64()
+        B = C.c_double()
+        _chk(self.lib.fsim_eval_contacts(self.ctx.h, self.id, _d(xx), _i32(keys), cap,
+                                         C.byref(cnt), C.byref(B)), "fsim_eval_contacts")
+        return keys[: cnt.value].copy(), B.value
+
+    def eval_barrier(self, x, want_bcheck=True):
+        xx = self._x(x)
+        g = np.empty((self.n, 3))
+        nc = C.c_int32()
+        info = self.info()
+        clist = np.empty(max(int(info["n2"]), 1), dtype=np.int32)
+        cap = 9 * int(info["n2"]) ** 2 if want_bcheck else 0
+        B = np.empty(max(cap, 1)) if want_bcheck else None
+        _chk(self.lib.fsim_eval_barrier(self.ctx.h, self.id, _d(xx), _d(g), C.byref(nc),
+                                        _i32(clist), _d(B), cap), "fsim_eval_barrier")
+        k = nc.value
+        Bc = B[: 9 * k * k].reshape(3 * k, 3 * k) if want_bcheck else None
+        return g, clist[:k].copy(), Bc
+
+    def eval_global_step(self, x, precision=FP64):
+        xx = self._x(x)
+        dx = np.empty((self.n, 3))
+        _chk(self.lib.fsim_eval_global_step(self.ctx.h, self.id, _d(xx), int(precision), _d(dx)),
+             "fsim_eval_global_step")
+        return dx
+
+    def eval_ccd(self, x, dx):
+        xx, dd = self._x(x), self._x(dx)
+        a = C.c_double()
+        _chk(self.lib.fsim_eval_ccd(self.ctx.h, self.id, _d(xx), _d(dd), C.byref(a)),
+             "fsim_eval_ccd")
+        return a.value
+
+    def eval_energy(self, x, precision=FP64):
+        xx = self._x(x)
+        E = C.c_double()
+        gn = C.c_double()
+        _chk(self.lib.fsim_eval_energy(self.ctx.h, self.id, _d(xx), int(precision), C.byref(E),
+                                       C.byref(gn)), "fsim_eval_energy")
+        return E.value, gn.value
+
+
+def params_for(mesh, **kw) -> Params:
+    """Default parameters with the workload's dhat / weight / tolerances."""
+    p = default_params(dhat=mesh.dhat, weight_scale=mesh.weight_scale, tol_abs=mesh.tol_abs,
+                       tol_rel=mesh.tol_rel)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p

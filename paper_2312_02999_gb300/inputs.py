@@ -197,7 +197,7 @@ def face_shell(n_target: int = 30000, nr: int = 7, thickness: float = 0.03,
                theta_range=(-55.0, 65.0), phi_range=(-80.0, 80.0),
                theta_mouth: float = -20.0, proxy_phi: float = 60.0,
                proxy_theta: float = 22.0, dhat_rel: float = 1e-4,
-               weight_scale: float = 1e3, tol_abs: float = 0.0,
+               weight_scale: float = 1e3, tol_abs: float = 1e-10,
                tol_rel: float = 1e-7) -> MeshInput:
     """Front half of an ellipsoidal head, ``thickness`` thick, nr vertex layers.
 

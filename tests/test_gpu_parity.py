@@ -1,0 +1,307 @@
+"""GPU parity: every step of the iteration through the C ABI against the oracle.
+
+Tolerances (float64 path): the local-step energy, gradient and projections,
+barrier gradient and B-check, global step and energies agree with the oracle
+to 1e-9 relative (float64 rounding amplified by at most the conditioning of
+the 3x3 SVDs and of the global system); proxy positions are bit-exact
+(selection embedding); the contact set is bit-exact except for pairs whose
+distance is within 1e-9 d0 of the threshold (either answer is correct there);
+CCD step bounds agree to 1e-12; final positions of a frame agree within 1e-9
+of the bounding-box diagonal (float64) and 1e-6 (mixed).
+"""
+import numpy as np
+import pytest
+
+from oracle import contact as OC
+from oracle import fem as OF
+from oracle import solver as S
+from paper_2312_02999_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsim():
+    from paper_2312_02999_gb300 import build
+    build.build()
+    from paper_2312_02999_gb300 import fsim as f
+    return f
+
+
+@pytest.fixture(scope="module")
+def ctx(fsim):
+    c = fsim.Context(0)
+    yield c
+    c.close()
+
+
+def _pair(fsim, ctx, mesh, act, kappa=None, **kw):
+    m = ctx.upload(mesh)
+    p = fsim.params_for(mesh, **kw)
+    if kappa is not None:
+        p.kappa = kappa
+    m.prefactor(p)
+    m.set_actuation(act.fiber, act.stretch)
+    k = m.info()["kappa"]
+    op = S.Params(dhat=mesh.dhat, tol_abs=p.tol_abs, tol_rel=p.tol_rel, kappa=k,
+                  max_iters=p.max_iters, weight_scale=mesh.weight_scale)
+    pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr, mesh.W_col,
+                   mesh.W_val, op, region=mesh.region)
+    pr.set_actuation(act.fiber, act.stretch)
+    return m, pr
+
+
+def _contact_x(mesh, scale=2e-4, seed=3, gap_shift=0.0):
+    rng = np.random.default_rng(seed)
+    x = mesh.rest.copy()
+    free = mesh.pinned == 0
+    x[free] += scale * rng.standard_normal((int(free.sum()), 3))
+    if gap_shift:
+        top = mesh.rest[:, 2] > mesh.rest[:, 2].mean()
+        x[top & free, 2] -= gap_shift
+    return x
+
+
+@pytest.fixture(scope="module")
+def slab_small(fsim, ctx):
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    return (mesh, act) + _pair(fsim, ctx, mesh, act)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_local_step_energy_gradient_projection(fsim, slab_small, prec):
+    mesh, act, m, pr = slab_small
+    x = _contact_x(mesh, 3e-3, seed=5)
+    E, g, P = m.eval_elastic(x, precision=prec, want_proj=True)
+    F = OF.deformation_gradients(x, pr.tets, pr.G)
+    _, Po = OF.local_step(F, pr.A)
+    Eo = OF.elastic_energy(F, Po, pr.w)
+    go = OF.elastic_gradient(x, pr.tets, pr.G, Po, pr.w)
+    go[mesh.pinned == 1] = 0.0
+    assert abs(E - Eo) <= 1e-10 * abs(Eo)
+    assert _rel(g, go) <= 1e-9
+    assert _rel(P, Po.reshape(-1, 9)) <= 1e-10
+
+
+def test_proxy_map_is_exact(fsim, slab_small):
+    mesh, act, m, pr = slab_small
+    x = _contact_x(mesh)
+    s = m.eval_proxy(x)
+    assert np.array_equal(s, pr.W @ x)
+
+
+def _check_contact_sets(gpu_keys, ora, s, pr, dhat):
+    typ, i, j, d = ora
+    a = set(map(tuple, gpu_keys.tolist()))
+    b = set(zip(typ.tolist(), i.tolist(), j.tolist()))
+    diff = a ^ b
+    for (t, ii, jj) in diff:   # only threshold ties may differ
+        V = OC.pair_vertices(np.array([t]), np.array([ii]), np.array([jj]), pr.tris, pr.edges)
+        dd = OC.distance(s[V], np.array([t == 1]))[0]
+        assert abs(dd - dhat) <= 1e-9 * dhat, (t, ii, jj, dd)
+    return len(a), len(diff)
+
+
+def test_constraint_set_and_barrier_energy(fsim, slab_small):
+    mesh, act, m, pr = slab_small
+    for seed in (3, 4, 5):
+        x = _contact_x(mesh, 3e-4, seed=seed, gap_shift=0.0035)
+        keys, B = m.eval_contacts(x)
+        s = pr.W @ x
+        ora = OC.constraint_set(s, pr.tris, pr.edges, mesh.dhat)
+        n, nd = _check_contact_sets(keys, ora, s, pr, mesh.dhat)
+        assert n > 0 and nd == 0
+        Bo = pr.kappa * OC.barrier(ora[3], mesh.dhat).sum()
+        assert abs(B - Bo) <= 1e-10 * abs(Bo)
+        # keys are sorted canonically
+        assert keys.tolist() == sorted(keys.tolist())
+
+
+def test_barrier_gradient_and_reduced_block(fsim, slab_small):
+    mesh, act, m, pr = slab_small
+    x = _contact_x(mesh, 3e-4, seed=7, gap_shift=0.0035)
+    g, clist, Bc = m.eval_barrier(x)
+    ev = pr.evaluate(x)
+    V, gp, _ = pr._pair_terms(ev, project=False)
+    gs = np.zeros((pr.W.shape[0], 3))
+    np.add.at(gs, V.ravel(), gp.reshape(-1, 3))
+    go = pr.W.T @ gs
+    assert _rel(g, go) <= 1e-9
+    Bfull = pr.barrier_hessian(ev, project=True).toarray()
+    x2v = np.nonzero(pr.x2_mask)[0]                 # x2 in vertex order
+    cv = x2v[clist]
+    touched = np.unique(np.nonzero(np.abs(Bfull).sum(1) > 0)[0] // 3)
+    assert set(touched.tolist()) <= set(cv.tolist())
+    idx = (3 * cv[:, None] + np.arange(3)).ravel()
+    Bo = Bfull[np.ix_(idx, idx)]
+    assert _rel(Bc, Bo) <= 1e-8
+    assert np.allclose(Bc, Bc.T, atol=1e-9 * np.abs(Bc).max())
+
+
+@pytest.mark.parametrize("prec,state,res_tol,fwd_tol", [
+    (0, "mild", 1e-9, 1e-9), (0, "stiff", 1e-6, 1e-5),
+    (1, "mild", 1e-4, 1e-3), (1, "stiff", 1e-4, 1e-2)])
+def test_global_step_matches_direct_solve(fsim, slab_small, prec, state, res_tol, fwd_tol):
+    # Pairs close to contact make H-hat ill-conditioned (kappa b'' ~ (dhat/d)^2):
+    # "mild" has min d ~ 0.5 dhat (cond(H-hat) ~ 1.6e4), "stiff" a pair at
+    # 0.003 dhat (cond ~ 4.8e6).  The explicit Sigma^-1 / low-rank route is
+    # not backward stable, so its residual grows like cond * eps; the float64
+    # bounds below are 1e3 * eps * cond.  Mixed precision solves the K11 and
+    # Sigma parts in float32 (cond(H) ~ 40) and the reduced system in float64.
+    mesh, act, m, pr = slab_small
+    if state == "mild":
+        x = _contact_x(mesh, 1e-4, seed=9, gap_shift=0.0033)
+    else:
+        x = _contact_x(mesh, 3e-4, seed=9, gap_shift=0.0035)
+    dx = m.eval_global_step(x, precision=prec)
+    ev = pr.evaluate(x)
+    g = pr.gradient(x, ev).ravel()[pr.free_dofs]
+    Bf = pr.free_part(pr.barrier_hessian(ev))
+    assert ev["C"][0].size > 0
+    Hh = pr.H + Bf
+    res = np.linalg.norm(Hh @ dx.ravel()[pr.free_dofs] + g) / np.linalg.norm(g)
+    assert res <= res_tol, res
+    dxo = np.zeros_like(x)
+    dxo.reshape(-1)[pr.free_dofs] = pr.global_step_direct(g, Bf)
+    assert _rel(dx, dxo) <= fwd_tol
+    assert np.all(dx[mesh.pinned == 1] == 0.0)
+
+
+def test_global_step_without_contact(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2, gap=0.3)
+    act = I.slab_actuation(mesh, seed=2)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    x = _contact_x(mesh, 1e-3, seed=1)
+    dx = m.eval_global_step(x)
+    ev = pr.evaluate(x)
+    assert ev["C"][0].size == 0
+    g = pr.gradient(x, ev).ravel()[pr.free_dofs]
+    dxo = np.zeros_like(x)
+    dxo.reshape(-1)[pr.free_dofs] = pr.global_step_direct(g, pr.free_part(pr.barrier_hessian(ev)))
+    assert _rel(dx, dxo) <= 1e-10
+
+
+def test_ccd_step_bound(fsim, slab_small):
+    mesh, act, m, pr = slab_small
+    x = _contact_x(mesh, 2e-4, seed=2, gap_shift=0.003)
+    rng = np.random.default_rng(8)
+    dx = np.zeros_like(x)
+    free = mesh.pinned == 0
+    top = mesh.rest[:, 2] > mesh.rest[:, 2].mean()
+    dx[free & top, 2] = -0.004
+    dx[free] += 3e-4 * rng.standard_normal((int(free.sum()), 3))
+    a = m.eval_ccd(x, dx)
+    s = pr.W @ x
+    ao = OC.ccd_step_bound(s, pr.W @ dx, pr.tris, pr.edges, mesh.dhat)
+    assert 0 < ao < 1
+    assert abs(a - ao) <= 1e-12 * ao
+
+
+def test_energy_and_gradient_norm(fsim, slab_small):
+    mesh, act, m, pr = slab_small
+    x = _contact_x(mesh, 3e-4, seed=12, gap_shift=0.0035)
+    E, gn = m.eval_energy(x)
+    ev = pr.evaluate(x)
+    Eo = ev["E"] + ev["B"]
+    gno = np.linalg.norm(pr.gradient(x, ev).ravel()[pr.free_dofs])
+    assert abs(E - Eo) <= 1e-10 * abs(Eo)
+    assert abs(gn - gno) <= 1e-9 * gno
+
+
+def _diag(mesh):
+    return float(np.linalg.norm(mesh.rest.max(0) - mesh.rest.min(0)))
+
+
+@pytest.mark.parametrize("nx,nz", [(3, 2), (5, 2)])
+def test_frame_parity_float64(fsim, ctx, nx, nz):
+    mesh = I.two_slabs(nx, nx, nz)
+    act = I.slab_actuation(mesh, seed=5)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    rc, st = m.solve_frame(precision=fsim.FP64)
+    x = m.positions()
+    xo, so = pr.solve_frame(mesh.rest)
+    assert rc == 0 and so.status == 0
+    assert st["contacts"] > 0
+    err = np.abs(x - xo).max() / _diag(mesh)
+    assert err <= 1e-9, (err, st["iterations"], so.iterations)
+    assert abs(st["iterations"] - so.iterations) <= 2
+    keys = m.contacts()
+    ora = OC.constraint_set(pr.W @ x, pr.tris, pr.edges, mesh.dhat)
+    _check_contact_sets(keys, ora, pr.W @ x, pr, mesh.dhat)
+
+
+def test_frame_parity_mixed(fsim, ctx):
+    mesh = I.two_slabs(5, 5, 2)
+    act = I.slab_actuation(mesh, seed=5)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    rc, st = m.solve_frame(precision=fsim.MIXED)
+    x = m.positions()
+    xo, so = pr.solve_frame(mesh.rest)
+    assert rc == 0
+    err = np.abs(x - xo).max() / _diag(mesh)
+    assert err <= 1e-6, err
+
+
+def test_rest_pose_converges_in_zero_iterations(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, lo=1.0, hi=1.0)
+    m, _ = _pair(fsim, ctx, mesh, act)
+    rc, st = m.solve_frame()
+    assert rc == 0 and st["iterations"] == 0
+    assert np.abs(m.positions() - mesh.rest).max() == 0.0
+
+
+def test_error_paths(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, seed=5)
+    m, _ = _pair(fsim, ctx, mesh, act, max_iters=1)
+    rc, st = m.solve_frame(check=False)
+    assert rc == fsim.FSIM_ENOT_CONVERGED and st["iterations"] == 1
+    bad = act.stretch.copy()
+    bad[3] = np.nan
+    with pytest.raises(fsim.FsimError) as e:
+        m.set_actuation(act.fiber, bad)
+    assert e.value.status == fsim.FSIM_ENONFINITE
+    # touching proxy at the start: collapse the gap
+    x = mesh.rest.copy()
+    top = mesh.rest[:, 2] > mesh.rest[:, 2].mean()
+    x[top & (mesh.pinned == 0), 2] -= 0.005
+    rc, _ = m.solve_frame(x_init=x, check=False)
+    assert rc == fsim.FSIM_EINTERSECTING
+    # tiny pair capacity overflows instead of writing out of bounds
+    m2, _ = _pair(fsim, ctx, mesh, act, contact_capacity=4)
+    rc, _ = m2.solve_frame(check=False)
+    assert rc == fsim.FSIM_ECONTACT_OVERFLOW
+    # a context stays usable after the errors
+    rc, st = m2.solve_frame(x_init=mesh.rest, check=False)
+    assert rc == fsim.FSIM_ECONTACT_OVERFLOW
+
+
+def test_kappa_auto_matches_oracle(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, seed=5)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr, mesh.W_col,
+                   mesh.W_val, S.Params(dhat=mesh.dhat))
+    assert abs(m.info()["kappa"] - pr.kappa) <= 1e-12 * pr.kappa
+
+
+@pytest.mark.slow
+def test_config1_two_slabs_frame_parity(fsim, ctx):
+    mesh = I.two_slabs()
+    act = I.slab_actuation(mesh, seed=1)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    for prec, tol in ((fsim.FP64, 1e-9), (fsim.MIXED, 1e-6)):
+        rc, st = m.solve_frame(x_init=mesh.rest, precision=prec)
+        assert rc == 0
+        x = m.positions()
+        if prec == fsim.FP64:
+            xo, so = pr.solve_frame(mesh.rest)
+        err = np.abs(x - xo).max() / _diag(mesh)
+        assert err <= tol, (prec, err)
