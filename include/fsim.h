@@ -246,6 +246,38 @@ fsim_status fsim_profile_read(fsim_ctx_t ctx, int kernel_class, int64_t* launche
                               double* total_ms);
 fsim_status fsim_profile_reset(fsim_ctx_t ctx);
 
+/*
+ * CCD step bound that allocates no device memory.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot let a
+ * library allocate GPU memory on its own: engines that reserve all device
+ * memory up front in their own pool, applications held to a fixed memory
+ * budget, or code recorded into a caller's CUDA graph.
+ *
+ * Computes alpha_m = min(1, min over candidate pairs of the additive-CCD time
+ * of impact) exactly as the solver's CCD stage (fsim_eval_ccd) does, for
+ * proxy positions s_dev [3 Ns] and step ds_dev [3 Ns], triangles
+ * tris_dev [3 Nt] and edges edges_dev [2 Ne] (the sorted unique (lo, hi)
+ * pairs of the triangles' edges), all DEVICE pointers owned by the caller;
+ * the result is written to the device double *alpha_dev.  Work is queued on
+ * `stream` (a cudaStream_t, NULL = default stream) and the call returns after
+ * that stream has finished it.
+ *
+ * Scratch: a fixed static device array of 2^20 candidate pairs (about 8 MiB),
+ * present on every GPU that loads the library until the process exits.  More
+ * candidates than that return FSIM_ECONTACT_OVERFLOW (alpha_dev then holds a
+ * bound over the first 2^20 candidates only and must not be used).  The first
+ * call on a device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Errors: FSIM_EINVAL for null pointers, negative sizes, dhat <= 0,
+ * ccd_s outside (0, 1) or accd_max_iters <= 0; FSIM_ECUDA for a CUDA error.
+ */
+fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_dev, int64_t Ns,
+                             const int32_t* tris_dev, int64_t Nt,
+                             const int32_t* edges_dev, int64_t Ne, double dhat,
+                             double ccd_s, int32_t accd_max_iters, double* alpha_dev,
+                             void* stream);
+
 /* Sizes of a mesh (n, T, Ns, Nt, Ne, free / x1 / x2 vertex counts), the
  * scalar factor's stored entries and supernode / level counts, and the
  * barrier stiffness kappa in use (after fsim_prefactor). */

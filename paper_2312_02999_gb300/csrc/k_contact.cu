@@ -9,6 +9,7 @@
 // exactly as the oracle does, and the float64 distance decides d < dhat.
 #include "contact.cuh"
 #include "kernels.h"
+#include "../../include/fsim.h"
 
 namespace fsim {
 
@@ -474,3 +475,112 @@ void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int n
 }
 
 }  // namespace fsim
+
+// ===========================================================================
+// CCD step bound without any device allocation.
+//
+// Some callers cannot let a library allocate GPU memory: an animation or game
+// engine that reserves all device memory up front in its own pool, a host
+// application that must stay inside a fixed memory budget, or code that is
+// about to be recorded into someone else's CUDA graph.  For them,
+// fsim_ccd_noalloc computes the same additive-CCD step bound as the solver's
+// CCD stage, with every input and output owned by the caller and its only
+// scratch (the candidate-pair list and two counters) in the fixed array below.
+// ===========================================================================
+namespace fsim {
+namespace {
+
+// Largest candidate list the static scratch holds (8 MiB of keys).
+constexpr int64_t kNoallocCandidates = int64_t(1) << 20;
+// Words [0, 2): four int counters ([1] candidates, [2] overflow flag), as the
+// pair kernels use them; words [2, 2 + kNoallocCandidates): candidate keys.
+// Every GPU that loads the library keeps this array until the process exits.
+constexpr int kNoallocHeaderWords = 2;
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[kNoallocHeaderWords + kNoallocCandidates];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// ACCD over a candidate list whose length is read on the device (so the host
+// never has to read it back); fixed grid, grid-stride loop.
+__global__ void k_accd_count(const int* __restrict__ counters, int64_t cap,
+                             const unsigned long long* __restrict__ cand,
+                             const double* __restrict__ s, const double* __restrict__ ds,
+                             const int* __restrict__ tris, const int* __restrict__ edges,
+                             double s_ratio, int max_iters, double* __restrict__ alpha) {
+  int64_t n = counters[1];
+  n = n < cap ? n : cap;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int type, i, j;
+    unpack_key(cand[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    double X[4][3], dX[4][3];
+    gather_X(s, V, X);
+    gather_X(ds, V, dX);
+    const double toi = accd_toi(type, X, dX, s_ratio, max_iters);
+    if (toi < 1.0)
+      atomicMin(reinterpret_cast<unsigned long long*>(alpha),
+                (unsigned long long)__double_as_longlong(toi));
+  }
+}
+
+__global__ void k_set_one(double* a) { *a = 1.0; }
+
+}  // namespace
+}  // namespace fsim
+
+extern "C" fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_dev, int64_t Ns,
+                                        const int32_t* tris_dev, int64_t Nt,
+                                        const int32_t* edges_dev, int64_t Ne, double dhat,
+                                        double ccd_s, int32_t accd_max_iters, double* alpha_dev,
+                                        void* stream) {
+  using namespace fsim;
+  if (!alpha_dev || Ns < 0 || Nt < 0 || Ne < 0 || Ns >= (1LL << 31) || Nt >= (1LL << 31) ||
+      Ne >= (1LL << 31) || !(dhat > 0.0) || !(ccd_s > 0.0 && ccd_s < 1.0) || accd_max_iters <= 0)
+    return FSIM_EINVAL;
+  if (Ns > 0 && (!s_dev || !ds_dev)) return FSIM_EINVAL;
+  if ((Nt > 0 && !tris_dev) || (Ne > 0 && !edges_dev)) return FSIM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FSIM_ECUDA;
+  // one-time set-up per device: the host-side name of the array is not a
+  // device address, so ask the runtime for the address on this device
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return FSIM_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* base = (unsigned long long*)g_noalloc_ptr[dev];
+  int* counters = reinterpret_cast<int*>(base);          // header: 4 ints
+  unsigned long long* keys = base + kNoallocHeaderWords;
+  // the array keeps the previous call's contents: reset the counters
+  if (cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kNoallocHeaderWords, st) !=
+      cudaSuccess)
+    return FSIM_ECUDA;
+  k_set_one<<<1, 1, 0, st>>>(alpha_dev);
+  if (Ns > 0 && Nt > 0) {
+    dim3 gpt((unsigned)((Ns + kTile - 1) / kTile), (unsigned)((Nt + kTile - 1) / kTile));
+    k_pairs_pt<1><<<gpt, kTile, 0, st>>>((int)Ns, (int)Nt, s_dev, ds_dev, tris_dev, dhat, 0.0, keys,
+                                         counters, kNoallocCandidates, nullptr);
+  }
+  if (Ne > 1) {
+    const unsigned ne = (unsigned)((Ne + kTile - 1) / kTile);
+    k_pairs_ee<1><<<dim3(ne, ne), kTile, 0, st>>>((int)Ne, s_dev, ds_dev, edges_dev, dhat, 0.0, keys,
+                                                  counters, kNoallocCandidates, nullptr);
+  }
+  k_accd_count<<<256, 128, 0, st>>>(counters, kNoallocCandidates, keys, s_dev, ds_dev, tris_dev,
+                                    edges_dev, ccd_s, accd_max_iters, alpha_dev);
+  if (cudaGetLastError() != cudaSuccess) return FSIM_ECUDA;
+  int host_counters[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(host_counters, counters, sizeof(host_counters), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FSIM_ECUDA;
+  return host_counters[2] ? FSIM_ECONTACT_OVERFLOW : FSIM_OK;
+}

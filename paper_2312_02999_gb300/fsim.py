@@ -98,6 +98,8 @@ _SIGS = {
     "fsim_profile": [_P, C.c_uint32],
     "fsim_profile_read": [_P, C.c_int, _I64, _D],
     "fsim_profile_reset": [_P],
+    "fsim_ccd_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                         C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_void_p, C.c_void_p],
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
