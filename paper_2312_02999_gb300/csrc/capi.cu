@@ -46,13 +46,13 @@ struct fsim_ctx_s {
   cudaStream_t stream = nullptr;
   std::vector<std::unique_ptr<MeshState>> meshes;
   // pinned host readback area
-  int* h_counters = nullptr;   // 8 ints
+  int* h_counters = nullptr;   // kCounters ints
   double* h_scal = nullptr;    // 8 doubles
 };
 
 namespace {
 
-constexpr int kCounters = 8;
+constexpr int kCounters = 16;
 constexpr int kScal = 8;
 
 #define CK(call)                                                   \
@@ -154,6 +154,7 @@ int evaluate(fsim_ctx_t ctx, MeshState& ms, const double* xb, double* sb, double
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(m.counters, 0, sizeof(int) * 3, s));       // |C|, candidates, overflow
   CK(cudaMemsetAsync(m.counters + 5, 0, sizeof(int), s));       // touching pair
+  CK(cudaMemsetAsync(m.counters + 8, 0, sizeof(int), s));       // near-pair list
   CK(cudaMemsetAsync(m.scal, 0, sizeof(double) * 1, s));
   launch_elastic(s, m, xb, tetf, proj, m.partials, prec);
   launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
@@ -167,12 +168,12 @@ int evaluate(fsim_ctx_t ctx, MeshState& ms, const double* xb, double* sb, double
 // sb) into gout, the contact-affected set, B-check (if hess) and ||g||^2.
 // Requires counters[0] (|C|) already on the host in npairs.
 int gradient_and_hessian(fsim_ctx_t ctx, MeshState& ms, const double* sb, const double* tetf,
-                         double* gout, int64_t npairs, bool hess, int* nc_out, double* gn2_out) {
+                         double* gout, int64_t npairs, int prec, int* nc_out, double* gn2_out) {
   DevMesh& m = ms.d;
   cudaStream_t s = ctx->stream;
   launch_gather_forces(s, m, tetf, gout);
   CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
-  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, ms.kappa);
+  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, ms.kappa, prec);
   if (m.n2 > 0) launch_mark_scan(s, m);
   else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
   TRY(sync_read(ctx, m));
@@ -182,8 +183,7 @@ int gradient_and_hessian(fsim_ctx_t ctx, MeshState& ms, const double* sb, const 
     CK(cudaMemsetAsync(m.Bc, 0, sizeof(double) * 9 * (size_t)nc * nc, s));
     CK(cudaMemsetAsync(m.bocc, 0, sizeof(int) * (size_t)nc * nc, s));
   }
-  launch_barrier_scatter(s, m, npairs, nc, gout);   // gradient always, blocks for hess
-  (void)hess;
+  launch_barrier_scatter(s, m, npairs, nc, gout);
   const int nb = gnorm_blocks(m.n);
   launch_gnorm2(s, m, gout, m.partials, nb);
   launch_sum_partials(s, m.partials, nb, m.scal + 3);
@@ -219,7 +219,7 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
   int nc = 0;
   if (rc == FSIM_OK) {
     double gn2;
-    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, true, &nc, &gn2));
+    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
     gn = std::sqrt(gn2);
     st.grad_norm0 = gn;
     tol = std::max(p.tol_abs, p.tol_rel * gn);
@@ -234,16 +234,14 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
     global_step(s, m, m.g, m.dx, nc, prec, m.counters + 6, ctx->num_sms);
     CK(cudaGetLastError());
-    // CCD step bound
+    // CCD step bound; the ACCD kernel reads the candidate count on the device,
+    // and the overflow / factorisation flags are checked at the next read-back
     launch_proxy(s, m, m.dx, m.ds);
-    CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int) * 2, s));
+    CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(m.counters + 9, 0, sizeof(int), s));
     const double one = 1.0;
     CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_ccd_candidates(s, m, m.s, m.ds, p.dhat);
-    TRY(sync_read(ctx, m));
-    if (ctx->h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
-    if (ctx->h_counters[2]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
-    launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters, ctx->h_counters[1]);
+    launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
     // backtracking line search from alpha_m on E-hat = E + B
     bool accepted = false;
     double scale = 1.0, Et = 0.0;
@@ -252,6 +250,8 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
       launch_axpy_positions(s, 3 * m.n, m.x, m.dx, m.scal + 1, scale, m.xt);
       TRY(evaluate(ctx, ms, m.xt, m.st, m.tetf_t, nullptr, prec));
       TRY(sync_read(ctx, m));
+      if (k == 0 && ctx->h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
+      if (k == 0 && ctx->h_counters[9]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
       st.ls_trials++;
       Et = ctx->h_scal[2] + ctx->h_scal[0];
       np_t = ctx->h_counters[0];
@@ -272,7 +272,7 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     npairs = np_t;
     st.iterations++;
     double gn2;
-    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, true, &nc, &gn2));
+    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
     gn = std::sqrt(gn2);
     if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
   }
@@ -443,6 +443,16 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
   TRY(dalloc(ms, &m.s, 3 * Ns));
   TRY(dalloc(ms, &m.st, 3 * Ns));
   TRY(dalloc(ms, &m.ds, 3 * Ns));
+  {
+    const int64_t np = Ns + Nt + (int64_t)m.Ne;
+    TRY(dalloc(ms, &m.pbox, 12 * (size_t)np));
+    TRY(dalloc(ms, &m.pkey, 12 * (size_t)np));
+    TRY(dalloc(ms, &m.sf, 3 * (size_t)Ns));
+    TRY(dalloc(ms, &m.dsf, 3 * (size_t)Ns));
+    double mx = 0.0;
+    for (int64_t k = 0; k < 3 * n; ++k) mx = std::max(mx, std::fabs(rest_xyz[k]));
+    m.coord_scale = 2.0 * std::max(mx, 1e-30);
+  }
   TRY(dalloc(ms, &m.counters, kCounters));
   TRY(dalloc(ms, &m.scal, kScal));
   m.n_partials = std::max(elastic_blocks(m.T), gnorm_blocks(m.n)) + 16;
@@ -490,7 +500,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   std::vector<int64_t> roff(nsn), zoff(nsn);
   m.max_ns = 1; m.max_ld = 1;
   for (int j = 0; j < nsn; ++j) {
-    c0[j] = f.sn[j].c0; ns[j] = f.sn[j].ns; nr1[j] = f.sn[j].nr1;
+    c0[j] = f.sn[j].c0; ns[j] = f.sn[j].ns; nr1[j] = f.sn[j].nr;   // all rows (x1 and x2)
     roff[j] = f.sn[j].rows_off; zoff[j] = f.sn[j].z_off;
     m.max_ns = std::max(m.max_ns, ns[j]);
     m.max_ld = std::max(m.max_ld, ns[j] + nr1[j]);
@@ -553,12 +563,14 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   TRY(dalloc(ms, &m.r, 3 * (size_t)m.nf));
   TRY(dalloc(ms, &m.t1, 3 * (size_t)std::max(m.n1, 1)));
   TRY(dalloc(ms, &m.u, 3 * (size_t)std::max(m.n2, 1)));
-  TRY(dalloc(ms, &m.rf, 3 * (size_t)std::max(m.n1, 2 * m.n2) + 8));
+  TRY(dalloc(ms, &m.rf, 3 * (size_t)m.nf + 8));
+  TRY(dalloc(ms, &m.uf, 3 * (size_t)std::max(m.n2, 1)));
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
                                   : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
   if (m.cap >= (1LL << 31)) return FSIM_EINVAL;
   TRY(dalloc(ms, &m.pairs, m.cap));
   TRY(dalloc(ms, &m.cand, m.cap));
+  TRY(dalloc(ms, &m.nearl, m.cap));
   TRY(dalloc(ms, &m.pair_grad, 12 * (size_t)m.cap));
   TRY(dalloc(ms, &m.pair_hess, 144 * (size_t)m.cap));
   TRY(dalloc(ms, &m.x2mark, std::max(m.n2, 1)));
@@ -777,7 +789,7 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
   CK(cudaMemsetAsync(m.tetf_t, 0, sizeof(double) * 12 * (size_t)m.T, s));
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, true, &nc, &gn2));
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
   if (n_c) *n_c = nc;
   if (grad_out)
     CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
@@ -805,7 +817,7 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, true, &nc, &gn2));
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
   CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
   global_step(s, m, ms->gtmp, ms->dxtmp, nc, precision, m.counters + 6, ctx->num_sms);
   CK(cudaGetLastError());
@@ -827,14 +839,13 @@ fsim_status fsim_eval_ccd(fsim_ctx_t ctx, int mesh_id, const double* x, const do
   CK(cudaMemcpyAsync(ms->dxtmp, dx, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyHostToDevice, s));
   launch_proxy(s, m, m.xt, m.st);
   launch_proxy(s, m, ms->dxtmp, m.ds);
-  CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int) * 2, s));
+  CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(m.counters + 9, 0, sizeof(int), s));
   const double one = 1.0;
   CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-  launch_ccd_candidates(s, m, m.st, m.ds, ms->p.dhat);
+  launch_ccd(s, m, m.st, m.ds, ms->p.dhat, ms->p.ccd_s, ms->p.accd_max_iters);
   TRY(sync_read(ctx, m));
-  if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
-  launch_ccd(s, m, m.st, m.ds, ms->p.dhat, ms->p.ccd_s, ms->p.accd_max_iters, ctx->h_counters[1]);
-  TRY(sync_read(ctx, m));
+  if (ctx->h_counters[9]) return FSIM_ECONTACT_OVERFLOW;
   *alpha_out = ctx->h_scal[1];
   return FSIM_OK;
 }
@@ -854,7 +865,7 @@ fsim_status fsim_eval_energy(fsim_ctx_t ctx, int mesh_id, const double* x, int p
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, false, &nc, &gn2));
+  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
   if (energy_out) *energy_out = E;
   if (grad_norm_out) *grad_norm_out = std::sqrt(gn2);
   return FSIM_OK;

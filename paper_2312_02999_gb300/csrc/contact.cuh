@@ -251,84 +251,58 @@ __device__ __forceinline__ double barrier_value(double d, double dhat) {
   return -u * u * log(d / dhat);
 }
 
-// Cyclic Jacobi eigen-decomposition of a symmetric n x n (n <= 5) matrix A;
-// on return A holds the eigenvalues on its diagonal, Q the eigenvectors.
-__device__ void jacobi_sym(double A[5][5], double Q[5][5], int n) {
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) Q[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 12; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = 0; i < n; ++i) {
-      dia += A[i][i] * A[i][i];
-      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
-    }
-    if (off <= 1e-30 * dia || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p][q];
-        if (fabs(apq) <= 1e-300) continue;
-        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
-          const double akp = A[k][p], akq = A[k][q];
-          A[k][p] = c * akp - s * akq;
-          A[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
-          const double apk = A[p][k], aqk = A[q][k];
-          A[p][k] = c * apk - s * aqk;
-          A[q][k] = s * apk + c * aqk;
-        }
-        A[p][q] = 0.0; A[q][p] = 0.0;
-        for (int k = 0; k < n; ++k) {
-          const double qkp = Q[k][p], qkq = Q[k][q];
-          Q[k][p] = c * qkp - s * qkq;
-          Q[k][q] = s * qkp + c * qkq;
-        }
-      }
-  }
-}
+// The pair Hessian kappa (b'' grad d grad d^T + b' hess d) in the reduced
+// basis {c^ (x) e_a} u {q_m (x) v^} (n = 3 + k <= 5 coordinates), before the
+// PSD projection, with everything the lift back to the 12x12 blocks needs.
+struct PairReduced {
+  int n, k;
+  double d;            // unsigned distance
+  double gfac;         // kappa b'(d): gradient of vertex i = gfac c_i v^
+  double c[4];         // affine coefficients
+  double ch[4];        // c / |c|
+  double q[2][4];      // orthonormal complement directions in R^4
+  double vh[3];        // v / |v|
+  double A[5][5];      // reduced Hessian (n x n used)
+};
 
-// Barrier gradient (per pair vertex, 4 x 3) and the 16 PSD Hessian blocks
-// H[i][j] (3x3, row-major) of kappa * b(d(X)) for a pair with d < dhat.
-// Returns d.
-__device__ double pair_barrier_psd(int type, const double X[4][3], double dhat, double kappa,
-                                   double grad[4][3], double H[4][4][9]) {
+__device__ void pair_reduced(int type, const double X[4][3], double dhat, double kappa,
+                             PairReduced& r) {
   PairGeom g;
   pair_geometry(type, X, g);
   const double d = sqrt(g.d2);
   double b, b1, b2;
   barrier3(d, dhat, b, b1, b2);
   const int k = g.k, n = 3 + k;
+  r.n = n; r.k = k; r.d = d; r.gfac = kappa * b1;
   // orthonormal (c^, q_1 .. q_k) in R^4
-  double cn = sqrt(g.c[0] * g.c[0] + g.c[1] * g.c[1] + g.c[2] * g.c[2] + g.c[3] * g.c[3]);
-  double ch[4], q[2][4];
-  for (int i = 0; i < 4; ++i) ch[i] = g.c[i] / cn;
+  const double cn = sqrt(g.c[0] * g.c[0] + g.c[1] * g.c[1] + g.c[2] * g.c[2] + g.c[3] * g.c[3]);
+  for (int i = 0; i < 4; ++i) { r.c[i] = g.c[i]; r.ch[i] = g.c[i] / cn; }
   double qc[2][2] = {{0, 0}, {0, 0}};   // q_m . c'_k
   double chc[2] = {0, 0};                // c^ . c'_k
   for (int m = 0; m < k; ++m) {
-    double r[4];
-    for (int i = 0; i < 4; ++i) r[i] = g.cp[m][i];
+    double w[4];
+    for (int i = 0; i < 4; ++i) w[i] = g.cp[m][i];
     double a = 0;
-    for (int i = 0; i < 4; ++i) a += ch[i] * r[i];
-    for (int i = 0; i < 4; ++i) r[i] -= a * ch[i];
+    for (int i = 0; i < 4; ++i) a += r.ch[i] * w[i];
+    for (int i = 0; i < 4; ++i) w[i] -= a * r.ch[i];
     for (int l = 0; l < m; ++l) {
       double bq = 0;
-      for (int i = 0; i < 4; ++i) bq += q[l][i] * r[i];
-      for (int i = 0; i < 4; ++i) r[i] -= bq * q[l][i];
+      for (int i = 0; i < 4; ++i) bq += r.q[l][i] * w[i];
+      for (int i = 0; i < 4; ++i) w[i] -= bq * r.q[l][i];
     }
-    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
-    for (int i = 0; i < 4; ++i) q[m][i] = r[i] / rn;
+    const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+    for (int i = 0; i < 4; ++i) r.q[m][i] = w[i] / wn;
   }
+  for (int m = k; m < 2; ++m)
+    for (int i = 0; i < 4; ++i) r.q[m][i] = 0.0;
   for (int kk = 0; kk < k; ++kk) {
-    double s = 0;
-    for (int i = 0; i < 4; ++i) s += ch[i] * g.cp[kk][i];
-    chc[kk] = s;
+    double t = 0;
+    for (int i = 0; i < 4; ++i) t += r.ch[i] * g.cp[kk][i];
+    chc[kk] = t;
     for (int m = 0; m < k; ++m) {
-      double t = 0;
-      for (int i = 0; i < 4; ++i) t += q[m][i] * g.cp[kk][i];
-      qc[m][kk] = t;
+      double u = 0;
+      for (int i = 0; i < 4; ++i) u += r.q[m][i] * g.cp[kk][i];
+      qc[m][kk] = u;
     }
   }
   double E[2][3];
@@ -342,11 +316,10 @@ __device__ double pair_barrier_psd(int type, const double X[4][3], double dhat, 
     for (int j = 0; j < 5; ++j) Hd2[i][j] = 0.0;
   for (int a = 0; a < 3; ++a) Hd2[a][a] = 2.0 * cn * cn;
   if (k > 0) {
-    const double vn = sqrt(g.d2);
     double Fr[5][2];
     for (int kk = 0; kk < k; ++kk) {
       for (int a = 0; a < 3; ++a) Fr[a][kk] = 2.0 * (chc[kk] * g.v[a] + cn * E[kk][a]);
-      for (int m = 0; m < k; ++m) Fr[3 + m][kk] = 2.0 * qc[m][kk] * vn;
+      for (int m = 0; m < k; ++m) Fr[3 + m][kk] = 2.0 * qc[m][kk] * d;
     }
     double G[2][2], Gi[2][2];
     for (int a = 0; a < k; ++a)
@@ -360,60 +333,25 @@ __device__ double pair_barrier_psd(int type, const double X[4][3], double dhat, 
     }
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double s = 0.0;
+        double t = 0.0;
         for (int a = 0; a < k; ++a)
-          for (int bb = 0; bb < k; ++bb) s += Fr[i][a] * Gi[a][bb] * Fr[j][bb];
-        Hd2[i][j] -= s;
+          for (int bb = 0; bb < k; ++bb) t += Fr[i][a] * Gi[a][bb] * Fr[j][bb];
+        Hd2[i][j] -= t;
       }
   }
   // grad d = (|c| v^, 0); hess d = hess d^2/(2d) - (|c|^2 v^ v^T (+) 0)/d
-  double vh[3] = {g.v[0] / d, g.v[1] / d, g.v[2] / d};
-  double gr[5] = {cn * vh[0], cn * vh[1], cn * vh[2], 0.0, 0.0};
-  double A[5][5], Q[5][5];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      double hdd = Hd2[i][j] / (2.0 * d) - (i < 3 && j < 3 ? cn * cn * vh[i] * vh[j] / d : 0.0);
-      A[i][j] = kappa * (b2 * gr[i] * gr[j] + b1 * hdd);
-    }
-  for (int i = n; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) { A[i][j] = 0.0; A[j][i] = 0.0; }
-  jacobi_sym(A, Q, n);
-  double Hp[5][5];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      double s = 0.0;
-      for (int l = 0; l < n; ++l) {
-        const double lam = A[l][l];
-        if (lam > 0.0) s += Q[i][l] * lam * Q[j][l];
+  for (int a = 0; a < 3; ++a) r.vh[a] = g.v[a] / d;
+  const double gr[5] = {cn * r.vh[0], cn * r.vh[1], cn * r.vh[2], 0.0, 0.0};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      if (i < n && j < n) {
+        const double hdd = Hd2[i][j] / (2.0 * d) -
+                           (i < 3 && j < 3 ? cn * cn * r.vh[i] * r.vh[j] / d : 0.0);
+        r.A[i][j] = kappa * (b2 * gr[i] * gr[j] + b1 * hdd);
+      } else {
+        r.A[i][j] = 0.0;
       }
-      Hp[i][j] = s;
     }
-  // gradient per vertex: kappa b' c_i v^
-  for (int i = 0; i < 4; ++i)
-    for (int dd = 0; dd < 3; ++dd) grad[i][dd] = kappa * b1 * g.c[i] * vh[dd];
-  // lift: block(i,j) = c^_i c^_j Hcc + c^_i h_j v^T + c^_j v^ h_i^T + s_ij v^ v^T
-  double hv[4][3], sq[4][4];
-  for (int i = 0; i < 4; ++i) {
-    for (int a = 0; a < 3; ++a) {
-      double s = 0.0;
-      for (int m = 0; m < k; ++m) s += q[m][i] * Hp[a][3 + m];
-      hv[i][a] = s;
-    }
-  }
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      double s = 0.0;
-      for (int m = 0; m < k; ++m)
-        for (int l = 0; l < k; ++l) s += q[m][i] * q[l][j] * Hp[3 + m][3 + l];
-      sq[i][j] = s;
-    }
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j)
-      for (int a = 0; a < 3; ++a)
-        for (int bb = 0; bb < 3; ++bb)
-          H[i][j][3 * a + bb] = ch[i] * ch[j] * Hp[a][bb] + ch[i] * hv[j][a] * vh[bb] +
-                                ch[j] * vh[a] * hv[i][bb] + sq[i][j] * vh[a] * vh[bb];
-  return d;
 }
 
 }  // namespace fsim

@@ -12,9 +12,10 @@ namespace fsim {
 // ---------------------------------------------------------------------------
 struct Supernode {
   int c0 = 0, ns = 0;           // first solver position and number of columns
-  int nr1 = 0;                  // off-diagonal rows inside x1 (factor rows)
+  int nr1 = 0;                  // off-diagonal rows inside x1
+  int nr = 0;                   // all off-diagonal rows kept (x1 rows, then x2 rows)
   int64_t rows_off = 0;         // offset of its nr1 row positions in rows[]
-  int64_t z_off = 0;            // offset of its Z block ((ns+nr1) x ns, col-major)
+  int64_t z_off = 0;            // offset of its Z block ((ns+nr) x ns, col-major)
   int level = 0;                // 0 = leaf; parents have larger levels
 };
 
@@ -23,7 +24,7 @@ struct HostFactor {
   std::vector<int> perm;        // solver position -> mesh vertex (x1 then x2)
   std::vector<int> pos;         // mesh vertex -> solver position or -1 (pinned)
   std::vector<Supernode> sn;    // post-ordered supernodes of L11
-  std::vector<int> rows;        // off-diagonal row positions (x1) per supernode
+  std::vector<int> rows;        // off-diagonal row positions (x1 and x2) per supernode
   std::vector<double> Z;        // per supernode [L_JJ^-1 ; L_RJ L_JJ^-1]
   std::vector<int> level_ptr;   // supernodes grouped by level (CSR)
   std::vector<int> level_sn;

@@ -225,33 +225,129 @@ k_pairs_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
   if (MODE == 0 && esum != 0.0) atomicAdd(scal + 0, kappa * esum);
 }
 
-// Pass A: per-pair gradient and PSD Hessian blocks; mark touched x2 vertices.
-__global__ void k_barrier_pairs(int64_t np, const unsigned long long* __restrict__ pairs,
-                                const double* __restrict__ s, const int* __restrict__ tris,
-                                const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
-                                const int* __restrict__ Wcol, const int* __restrict__ x2of,
-                                double dhat, double kappa, double* __restrict__ pgrad,
-                                double* __restrict__ phess, int* __restrict__ x2mark) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  int type, i, j;
-  unpack_key(pairs[p], type, i, j);
-  int V[4];
-  load_pair(type, i, j, tris, edges, V);
-  double X[4][3];
-  gather_X(s, V, X);
-  double gr[4][3], H[4][4][9];
-  pair_barrier_psd(type, X, dhat, kappa, gr, H);
-  for (int k = 0; k < 4; ++k)
-    for (int d = 0; d < 3; ++d) pgrad[p * 12 + 3 * k + d] = gr[k][d];
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      for (int e = 0; e < 9; ++e) phess[p * 144 + (a * 4 + b) * 9 + e] = H[a][b][e];
-  for (int k = 0; k < 4; ++k)
-    for (int64_t e = Wptr[V[k]]; e < Wptr[V[k] + 1]; ++e) {
-      const int q = x2of[Wcol[e]];
-      if (q >= 0) x2mark[q] = 1;
+// Pass A: per-pair gradient and PSD Hessian blocks (PositiveDefinite of
+// Algorithm 1); marks the touched x2 vertices.  One warp per pair: the
+// reduced (n <= 5) Hessian is built redundantly by every lane, each cyclic
+// Jacobi rotation updates its rows, columns and eigenvectors lane-parallel,
+// and the 144 block entries of the lift are spread over the lanes.  ET is the
+// type of the small eigen-solve (float64, or float32 in the mixed form).
+constexpr int kPairWarps = 4;
+
+template <typename ET>
+__global__ void __launch_bounds__(32 * kPairWarps)
+k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+                const double* __restrict__ s, const int* __restrict__ tris,
+                const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
+                const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
+                double kappa, double* __restrict__ pgrad, double* __restrict__ phess,
+                int* __restrict__ x2mark) {
+  __shared__ ET As[kPairWarps][5][5];
+  __shared__ ET Qs[kPairWarps][5][5];
+  __shared__ double Hp[kPairWarps][5][5];
+  __shared__ double hv[kPairWarps][4][3];
+  __shared__ double sq[kPairWarps][4][4];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t np = *count;
+  np = np < cap ? np : cap;
+  for (int64_t p = blockIdx.x * (int64_t)kPairWarps + w; p < np;
+       p += (int64_t)gridDim.x * kPairWarps) {
+    int type, i, j;
+    unpack_key(pairs[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    double X[4][3];
+    gather_X(s, V, X);
+    PairReduced r;
+    pair_reduced(type, X, dhat, kappa, r);
+    const int n = r.n;
+    if (lane < 25) {
+      const int a = lane / 5, b = lane % 5;
+      As[w][a][b] = (ET)r.A[a][b];
+      Qs[w][a][b] = a == b ? ET(1) : ET(0);
     }
+    __syncwarp();
+    const ET tiny = sizeof(ET) == 8 ? ET(1e-300) : ET(1e-30);
+    const ET tol = sizeof(ET) == 8 ? ET(1e-30) : ET(1e-13);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      ET off = 0, dia = 0;
+      for (int a = 0; a < n; ++a) {
+        dia += As[w][a][a] * As[w][a][a];
+        for (int b = a + 1; b < n; ++b) off += As[w][a][b] * As[w][a][b];
+      }
+      if (!(off > tol * dia)) break;
+      for (int pp = 0; pp < n - 1; ++pp)
+        for (int qq = pp + 1; qq < n; ++qq) {
+          const ET apq = As[w][pp][qq];
+          if (!(fabs(apq) > tiny)) continue;
+          const ET app = As[w][pp][pp], aqq = As[w][qq][qq];
+          const ET th = (aqq - app) / (ET(2) * apq);
+          const ET t = (th >= ET(0) ? ET(1) : ET(-1)) / (fabs(th) + sqrt(th * th + ET(1)));
+          const ET c = ET(1) / sqrt(t * t + ET(1)), sn = t * c;
+          ET x0 = 0, x1 = 0;
+          const bool rowl = lane < n && lane != pp && lane != qq;
+          const bool qlan = lane >= 8 && lane < 8 + n;
+          if (rowl) { x0 = As[w][lane][pp]; x1 = As[w][lane][qq]; }
+          if (qlan) { x0 = Qs[w][lane - 8][pp]; x1 = Qs[w][lane - 8][qq]; }
+          __syncwarp();
+          if (rowl) {
+            const ET np_ = c * x0 - sn * x1, nq = sn * x0 + c * x1;
+            As[w][lane][pp] = np_; As[w][pp][lane] = np_;
+            As[w][lane][qq] = nq; As[w][qq][lane] = nq;
+          }
+          if (qlan) {
+            Qs[w][lane - 8][pp] = c * x0 - sn * x1;
+            Qs[w][lane - 8][qq] = sn * x0 + c * x1;
+          }
+          if (lane == 16) As[w][pp][pp] = app - t * apq;
+          if (lane == 17) As[w][qq][qq] = aqq + t * apq;
+          if (lane == 18) { As[w][pp][qq] = ET(0); As[w][qq][pp] = ET(0); }
+          __syncwarp();
+        }
+    }
+    // projection: keep eigenvalues above a relative floor (zero in float64;
+    // float32 rounding noise of the largest one in the mixed form)
+    ET lmax = 0;
+    for (int a = 0; a < n; ++a) lmax = fmax(lmax, As[w][a][a]);
+    const ET floor_ = sizeof(ET) == 8 ? ET(0) : ET(1e-6) * lmax;
+    if (lane < 25) {
+      const int a = lane / 5, b = lane % 5;
+      double acc = 0.0;
+      if (a < n && b < n)
+        for (int l = 0; l < n; ++l) {
+          const ET lam = As[w][l][l];
+          if (lam > floor_) acc += (double)Qs[w][a][l] * (double)lam * (double)Qs[w][b][l];
+        }
+      Hp[w][a][b] = acc;
+    }
+    __syncwarp();
+    const int k = r.k;
+    if (lane < 12) {                  // hv[i][a] = sum_m q_m[i] Hp[a][3+m]
+      const int ii = lane / 3, a = lane % 3;
+      double acc = 0.0;
+      for (int m = 0; m < k; ++m) acc += r.q[m][ii] * Hp[w][a][3 + m];
+      hv[w][ii][a] = acc;
+    } else if (lane < 28) {           // sq[i][j] = sum q_m[i] q_l[j] Hp[3+m][3+l]
+      const int ii = (lane - 12) / 4, jj = (lane - 12) % 4;
+      double acc = 0.0;
+      for (int m = 0; m < k; ++m)
+        for (int l = 0; l < k; ++l) acc += r.q[m][ii] * r.q[l][jj] * Hp[w][3 + m][3 + l];
+      sq[w][ii][jj] = acc;
+    }
+    __syncwarp();
+    if (lane < 12) pgrad[p * 12 + lane] = r.gfac * r.c[lane / 3] * r.vh[lane % 3];
+    for (int e = lane; e < 144; e += 32) {
+      const int ab = e / 9, rc = e % 9;
+      const int ii = ab / 4, jj = ab % 4, a = rc / 3, b = rc % 3;
+      phess[p * 144 + e] = r.ch[ii] * r.ch[jj] * Hp[w][a][b] + r.ch[ii] * hv[w][jj][a] * r.vh[b] +
+                           r.ch[jj] * r.vh[a] * hv[w][ii][b] + sq[w][ii][jj] * r.vh[a] * r.vh[b];
+    }
+    if (lane < 4)
+      for (int64_t e = Wptr[V[lane]]; e < Wptr[V[lane] + 1]; ++e) {
+        const int q = x2of[Wcol[e]];
+        if (q >= 0) x2mark[q] = 1;
+      }
+    __syncwarp();
+  }
 }
 
 // x2mark (0/1 flags) -> x2mark[q] = c position + 1 (0 if untouched); clist; nc.
@@ -397,65 +493,348 @@ __global__ void k_accd(int64_t nc, const unsigned long long* __restrict__ cand,
 }
 
 // ---------------------------------------------------------------------------
+// Broad phase with per-primitive data prepared once per call.  Primitive
+// index space: vertices [0, Ns), triangles [Ns, Ns+Nt), edges [Ns+Nt, ..).
+// Per primitive: float32 boxes rounded outward (inflated by pad, and plain)
+// and the exact float64 bounds as order-preserving 64-bit keys, so that the
+// inner loops are float32 and integer only.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  // +0.0 for -0.0, then flip so that unsigned order equals float64 order
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v + 0.0);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+
+__global__ void k_prim_prep(int Ns, int Nt, int Ne, const double* __restrict__ s,
+                            const double* __restrict__ ds, const int* __restrict__ tris,
+                            const int* __restrict__ edges, double pad, float* __restrict__ box,
+                            unsigned long long* __restrict__ key, float* __restrict__ sf,
+                            float* __restrict__ dsf) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ns + Nt + Ne) return;
+  int ids[3];
+  int nv;
+  if (p < Ns) { ids[0] = p; nv = 1; }
+  else if (p < Ns + Nt) { const int t = p - Ns; ids[0] = tris[3 * t]; ids[1] = tris[3 * t + 1]; ids[2] = tris[3 * t + 2]; nv = 3; }
+  else { const int e = p - Ns - Nt; ids[0] = edges[2 * e]; ids[1] = edges[2 * e + 1]; nv = 2; }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int k = 0; k < nv; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double x = s[3 * (size_t)ids[k] + d];
+      lo[d] = fmin(lo[d], x); hi[d] = fmax(hi[d], x);
+      if (ds != nullptr) {
+        const double e = x + ds[3 * (size_t)ids[k] + d];
+        lo[d] = fmin(lo[d], e); hi[d] = fmax(hi[d], e);
+      }
+    }
+  float* b = box + 12 * (size_t)p;
+  unsigned long long* kk = key + 12 * (size_t)p;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double la = lo[d] - pad, ha = hi[d] + pad;    // same rounding as the oracle's test
+    b[d] = __double2float_rd(la);
+    b[3 + d] = __double2float_ru(ha);
+    b[6 + d] = __double2float_rd(lo[d]);
+    b[9 + d] = __double2float_ru(hi[d]);
+    kk[d] = order_key(la);
+    kk[3 + d] = order_key(ha);
+    kk[6 + d] = order_key(lo[d]);
+    kk[9 + d] = order_key(hi[d]);
+  }
+  if (p < Ns) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      sf[3 * (size_t)p + d] = (float)s[3 * (size_t)p + d];
+      if (dsf != nullptr) dsf[3 * (size_t)p + d] = (float)ds[3 * (size_t)p + d];
+    }
+  }
+}
+
+struct Box6 {
+  float v[6];   // lo[3], hi[3]
+};
+
+__device__ __forceinline__ bool ov32(const float* a, const float* b) {   // a inflated, b plain
+  return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+
+__device__ __forceinline__ bool ov64(const unsigned long long* a, const unsigned long long* b) {
+  return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+
+__device__ __forceinline__ void gather_Xf(const float* sf, const int V[4], float X[4][3]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[k][d] = sf[3 * (size_t)V[k] + d];
+}
+
+struct SweepArgs {
+  int Ns, Nt, Ne;
+  const float* box;
+  const unsigned long long* key;
+  const float* sf;
+  const int* tris;
+  const int* edges;
+  float near;                   // float32 distance below which a pair is kept (MODE 0)
+  unsigned long long* out;
+  int* count;
+  int* overflow;
+  int64_t cap;
+};
+
+// MODE 0: pairs whose float32 distance is within `near` (a superset of the
+// d < dhat pairs; decided in float64 by k_near_pairs).  MODE 1: CCD
+// candidates, whose swept boxes (+dhat) overlap by the exact float64 test.
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
+  __shared__ float tb[kTile][6];
+  __shared__ int tid3[kTile][3];
+  __shared__ unsigned long long tk[MODE == 1 ? kTile : 1][6];
+  const int t0 = blockIdx.y * kTile;
+  for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+    const int t = t0 + k;
+    if (t < a.Nt) {
+      const float* b = a.box + 12 * (size_t)(a.Ns + t) + 6;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) tb[k][q] = b[q];
+      tid3[k][0] = a.tris[3 * t]; tid3[k][1] = a.tris[3 * t + 1]; tid3[k][2] = a.tris[3 * t + 2];
+      if (MODE == 1) {
+        const unsigned long long* kk = a.key + 12 * (size_t)(a.Ns + t) + 6;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) tk[k][q] = kk[q];
+      }
+    }
+  }
+  __syncthreads();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.Ns) return;
+  float vb[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) vb[q] = a.box[12 * (size_t)v + q];
+  unsigned long long vk[6];
+  if (MODE == 1) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) vk[q] = a.key[12 * (size_t)v + q];
+  }
+  const int nt = min(kTile, a.Nt - t0);
+  for (int k = 0; k < nt; ++k) {
+    if (!ov32(vb, tb[k])) continue;
+    const int p0 = tid3[k][0], p1 = tid3[k][1], p2 = tid3[k][2];
+    if (p0 == v || p1 == v || p2 == v) continue;
+    if (MODE == 1) {
+      if (ov64(vk, tk[k])) append(pack_key(0, v, t0 + k), a.out, a.count, a.overflow, a.cap);
+    } else {
+      const int V[4] = {v, p0, p1, p2};
+      float X[4][3];
+      gather_Xf(a.sf, V, X);
+      if (pair_distance_f(0, X) <= a.near) append(pack_key(0, v, t0 + k), a.out, a.count, a.overflow, a.cap);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
+  if (blockIdx.y < blockIdx.x) return;        // tiles with j-tile >= i-tile
+  __shared__ float eb[kTile][6];
+  __shared__ int eid[kTile][2];
+  __shared__ unsigned long long ek[MODE == 1 ? kTile : 1][6];
+  const int j0 = blockIdx.y * kTile;
+  const int eoff = a.Ns + a.Nt;
+  for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
+    const int e = j0 + k;
+    if (e < a.Ne) {
+      const float* b = a.box + 12 * (size_t)(eoff + e) + 6;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) eb[k][q] = b[q];
+      eid[k][0] = a.edges[2 * e]; eid[k][1] = a.edges[2 * e + 1];
+      if (MODE == 1) {
+        const unsigned long long* kk = a.key + 12 * (size_t)(eoff + e) + 6;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ek[k][q] = kk[q];
+      }
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kTile + threadIdx.x;
+  if (i >= a.Ne) return;
+  const int i0 = a.edges[2 * i], i1 = a.edges[2 * i + 1];
+  float ib[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) ib[q] = a.box[12 * (size_t)(eoff + i) + q];
+  unsigned long long ikk[6];
+  if (MODE == 1) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) ikk[q] = a.key[12 * (size_t)(eoff + i) + q];
+  }
+  const int ne = min(kTile, a.Ne - j0);
+  for (int k = 0; k < ne; ++k) {
+    const int j = j0 + k;
+    if (j <= i) continue;
+    if (!ov32(ib, eb[k])) continue;
+    const int b0 = eid[k][0], b1 = eid[k][1];
+    if (b0 == i0 || b0 == i1 || b1 == i0 || b1 == i1) continue;
+    if (MODE == 1) {
+      if (ov64(ikk, ek[k])) append(pack_key(1, i, j), a.out, a.count, a.overflow, a.cap);
+    } else {
+      const int V[4] = {i0, i1, b0, b1};
+      float X[4][3];
+      gather_Xf(a.sf, V, X);
+      if (pair_distance_f(1, X) <= a.near) append(pack_key(1, i, j), a.out, a.count, a.overflow, a.cap);
+    }
+  }
+}
+
+// float64 narrow phase of the near pairs (one pair per thread, fixed grid,
+// length read on the device): d < dhat joins C and adds kappa b(d).
+__global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap,
+                             const unsigned long long* __restrict__ nearl,
+                             const double* __restrict__ s, const int* __restrict__ tris,
+                             const int* __restrict__ edges, double dhat, double kappa,
+                             unsigned long long* __restrict__ pairs, int* counters,
+                             double* __restrict__ scal) {
+  int64_t n = *near_count;
+  n = n < cap ? n : cap;
+  double esum = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int type, i, j;
+    unpack_key(nearl[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    double X[4][3];
+    gather_X(s, V, X);
+    const double d = pair_distance(type, X);
+    if (d < dhat) {
+      append(pack_key(type, i, j), pairs, counters + 0, counters + 2, cap);
+      esum += barrier_value(d, dhat);
+      if (!(d > 0.0)) atomicOr(counters + 5, 1);
+    }
+  }
+  if (esum != 0.0) atomicAdd(scal + 0, kappa * esum);
+}
+
+// ACCD over the candidate list (length read on the device); a float32
+// early-out first: when (1 - s) d0 exceeds l_p by a clear margin the first
+// advance passes t = 1 and the float64 march would return "no impact" too.
+__global__ void k_accd_list(const int* __restrict__ cand_count, int64_t cap,
+                            const unsigned long long* __restrict__ cand,
+                            const double* __restrict__ s, const double* __restrict__ ds,
+                            const float* __restrict__ sf, const float* __restrict__ dsf,
+                            const int* __restrict__ tris, const int* __restrict__ edges,
+                            double s_ratio, int max_iters, float slack, double* __restrict__ alpha) {
+  int64_t n = *cand_count;
+  n = n < cap ? n : cap;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int type, i, j;
+    unpack_key(cand[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    {
+      float X[4][3], dX[4][3];
+      gather_Xf(sf, V, X);
+      gather_Xf(dsf, V, dX);
+      float mean[3], nrm[4];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) mean[d] = 0.25f * (dX[0][d] + dX[1][d] + dX[2][d] + dX[3][d]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float a0 = dX[k][0] - mean[0], a1 = dX[k][1] - mean[1], a2 = dX[k][2] - mean[2];
+        nrm[k] = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+      }
+      const float lp = type == 1 ? fmaxf(nrm[0], nrm[1]) + fmaxf(nrm[2], nrm[3])
+                                 : nrm[0] + fmaxf(fmaxf(nrm[1], nrm[2]), nrm[3]);
+      const float df = pair_distance_f(type, X);
+      if ((1.0f - (float)s_ratio) * (df - slack) > lp * 1.001f + slack) continue;
+    }
+    double X[4][3], dX[4][3];
+    gather_X(s, V, X);
+    gather_X(ds, V, dX);
+    const double toi = accd_toi(type, X, dX, s_ratio, max_iters);
+    if (toi < 1.0)
+      atomicMin(reinterpret_cast<unsigned long long*>(alpha), (unsigned long long)__double_as_longlong(toi));
+  }
+}
+
+// ---------------------------------------------------------------------------
 void launch_proxy(cudaStream_t st, const DevMesh& m, const double* x, double* sp) {
   k_proxy<<<(m.Ns + 255) / 256, 256, 0, st>>>(m.Ns, m.Wptr, m.Wcol, m.Wval, x, sp);
   count_launch();
 }
 
+namespace {
+int nprim(const DevMesh& m) { return m.Ns + m.Nt + m.Ne; }
+
+void launch_sweeps(cudaStream_t st, const DevMesh& m, int mode, unsigned long long* out, int* count,
+                   int* overflow, float nearf) {
+  SweepArgs a{m.Ns, m.Nt, m.Ne, m.pbox, m.pkey, m.sf, m.tris, m.edges, nearf, out, count, overflow,
+              m.cap};
+  if (m.Ns > 0 && m.Nt > 0) {
+    dim3 gpt((m.Ns + kTile - 1) / kTile, (m.Nt + kTile - 1) / kTile);
+    if (mode == 0) k_sweep_pt<0><<<gpt, kTile, 0, st>>>(a);
+    else k_sweep_pt<1><<<gpt, kTile, 0, st>>>(a);
+    count_launch();
+  }
+  if (m.Ne > 1) {
+    const int ne = (m.Ne + kTile - 1) / kTile;
+    if (mode == 0) k_sweep_ee<0><<<dim3(ne, ne), kTile, 0, st>>>(a);
+    else k_sweep_ee<1><<<dim3(ne, ne), kTile, 0, st>>>(a);
+    count_launch();
+  }
+}
+}  // namespace
+
+// Constraint set and barrier energy at sp: prep, float32 sweeps into the
+// near list, float64 narrow phase.  Uses counters [0] |C|, [2] overflow,
+// [5] touching, [8] near-list length (all zeroed by the caller).
 void launch_detect(cudaStream_t st, const DevMesh& m, const double* sp, double dhat, double kappa) {
   ProfScope ps(PROF_DETECT, st);
-  if (m.Ns > 0 && m.Nt > 0) {
-    dim3 gpt((m.Ns + kTile - 1) / kTile, (m.Nt + kTile - 1) / kTile);
-    k_pairs_pt<0><<<gpt, kTile, 0, st>>>(m.Ns, m.Nt, sp, nullptr, m.tris, dhat, kappa, m.pairs,
-                                         m.counters, m.cap, m.scal);
-    count_launch();
-  }
-  if (m.Ne > 1) {
-    const int ne = (m.Ne + kTile - 1) / kTile;
-    dim3 gee(ne, ne);
-    k_pairs_ee<0><<<gee, kTile, 0, st>>>(m.Ne, sp, nullptr, m.edges, dhat, kappa, m.pairs,
-                                         m.counters, m.cap, m.scal);
-    count_launch();
-  }
+  const int np = nprim(m);
+  if (np == 0) return;
+  k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, nullptr, m.tris, m.edges, dhat,
+                                                m.pbox, m.pkey, m.sf, nullptr);
+  launch_sweeps(st, m, 0, m.nearl, m.counters + 8, m.counters + 2, 2.0f * (float)dhat);
+  k_near_pairs<<<2 * 152, 128, 0, st>>>(m.counters + 8, m.cap, m.nearl, sp, m.tris, m.edges, dhat,
+                                        kappa, m.pairs, m.counters, m.scal);
+  count_launch(2);
 }
 
-void launch_ccd_candidates(cudaStream_t st, const DevMesh& m, const double* sp, const double* dsp,
-                           double dhat) {
-  ProfScope ps(PROF_CCD, st);
-  if (m.Ns > 0 && m.Nt > 0) {
-    dim3 gpt((m.Ns + kTile - 1) / kTile, (m.Nt + kTile - 1) / kTile);
-    k_pairs_pt<1><<<gpt, kTile, 0, st>>>(m.Ns, m.Nt, sp, dsp, m.tris, dhat, 0.0, m.cand,
-                                         m.counters, m.cap, m.scal);
-    count_launch();
-  }
-  if (m.Ne > 1) {
-    const int ne = (m.Ne + kTile - 1) / kTile;
-    dim3 gee(ne, ne);
-    k_pairs_ee<1><<<gee, kTile, 0, st>>>(m.Ne, sp, dsp, m.edges, dhat, 0.0, m.cand, m.counters,
-                                         m.cap, m.scal);
-    count_launch();
-  }
-}
-
+// CCD candidates of the step sp -> sp + dsp into m.cand ([1] length, [9]
+// overflow) and the additive-CCD step bound (min into m.scal[1]).
 void launch_ccd(cudaStream_t st, const DevMesh& m, const double* sp, const double* dsp, double dhat,
-                double ccd_s, int accd_max_iters, int64_t ncand) {
-  (void)dhat;
-  ncand = ncand < m.cap ? ncand : m.cap;   // an overflowed list holds only cap keys
-  if (ncand <= 0) return;
+                double ccd_s, int accd_max_iters) {
   ProfScope ps(PROF_CCD, st);
-  k_accd<<<(unsigned)((ncand + 127) / 128), 128, 0, st>>>(ncand, m.cand, sp, dsp, m.tris, m.edges,
-                                                         ccd_s, accd_max_iters, m.scal + 1);
-  count_launch();
+  const int np = nprim(m);
+  if (np == 0) return;
+  k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, dsp, m.tris, m.edges, dhat,
+                                                m.pbox, m.pkey, m.sf, m.dsf);
+  launch_sweeps(st, m, 1, m.cand, m.counters + 1, m.counters + 9, 0.0f);
+  // float32 coordinates round by ~6e-8 of their magnitude; the early-out
+  // slack (1e-5 of twice the largest rest coordinate, at least 1% of dhat)
+  // stays two orders of magnitude above that rounding
+  const double slack = fmax(0.01 * dhat, 1e-5 * m.coord_scale);
+  k_accd_list<<<4 * 152, 128, 0, st>>>(m.counters + 1, m.cap, m.cand, sp, dsp, m.sf, m.dsf, m.tris,
+                                       m.edges, ccd_s, accd_max_iters, (float)slack, m.scal + 1);
+  count_launch(2);
 }
 
 void launch_barrier_pairs(cudaStream_t st, const DevMesh& m, int64_t np, const double* sp,
-                          double dhat, double kappa) {
+                          double dhat, double kappa, int precision) {
   np = np < m.cap ? np : m.cap;
   if (np <= 0) return;
   ProfScope ps(PROF_BARRIER, st);
-  k_barrier_pairs<<<(unsigned)((np + 63) / 64), 64, 0, st>>>(np, m.pairs, sp, m.tris, m.edges,
-                                                            m.Wptr, m.Wcol, m.x2of, dhat, kappa,
-                                                            m.pair_grad, m.pair_hess, m.x2mark);
+  const int64_t want = (np + kPairWarps - 1) / kPairWarps;
+  const unsigned grid = (unsigned)(want < 8 * 152 ? want : 8 * 152);
+  if (precision == 0)
+    k_barrier_pairs<double><<<grid, 32 * kPairWarps, 0, st>>>(
+        m.counters, m.cap, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+        m.pair_grad, m.pair_hess, m.x2mark);
+  else
+    k_barrier_pairs<float><<<grid, 32 * kPairWarps, 0, st>>>(
+        m.counters, m.cap, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+        m.pair_grad, m.pair_hess, m.x2mark);
   count_launch();
 }
 

@@ -457,10 +457,10 @@ namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// In-place solve of K11 x = b (3 right-hand sides) with scratch y: forward
-// levels leaves to root (b -> y), backward levels root to leaves (y -> b).
+// Forward pass over the levels (leaves to root): y_J = L_JJ^-1 b_J on the
+// x1 positions, b_R -= L_RJ y_J on every off-diagonal row (x1 and x2).
 template <typename T>
-void trisolve(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y) {
+void trisolve_fwd(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y) {
   for (int l = 0; l < m.n_levels; ++l) {
     const int a = m.h_fwd_ptr[l], e = m.h_fwd_ptr[l + 1];
     if (e <= a) continue;
@@ -470,6 +470,12 @@ void trisolve(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y) {
                                           m.sn_zoff, m.sn_rows, Z, b, y);
     count_launch();
   }
+}
+
+// Backward pass (root to leaves): x_J = L_JJ^-T (y_J - L_RJ^T x_R), reading
+// x_R from b (x1 ancestors solved earlier, x2 rows = dx2), writing b on x1.
+template <typename T>
+void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b) {
   for (int l = m.n_levels - 1; l >= 0; --l) {
     const int a = m.h_bwd_ptr[l], e = m.h_bwd_ptr[l + 1];
     if (e <= a) continue;
@@ -521,75 +527,56 @@ void reduced_solve(cudaStream_t s, const DevMesh& m, const T* Sinv, int nc, cons
   count_launch(9);
 }
 
+// Eq. 8 with H = K (x) I_3 in solver positions [x1 ; x2], r = -g-hat:
+//   lower:    z1 = L1^-1 r1,  y2 = r2 - L21 z1        (one forward pass; the
+//             x2 rows of the supernodes hold L21 = H21 L1^-T)
+//   diagonal: dx2 = Sigma-hat^-1 y2 = u - Sigma^-1 Q^T v,  u = Sigma^-1 y2
+//   upper:    dx1 = L1^-T (z1 - L21^T dx2)             (one backward pass)
 template <typename T>
 void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc, int* info,
                    int num_sms) {
   const int nf = m.nf, n1 = m.n1, n2 = m.n2;
-  double* r = m.r;               // float64 right-hand side / solution (positions)
-  k_gather_rhs<double><<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, g, r);
+  const bool f64 = std::is_same<T, double>::value;
+  double* r = m.r;                                  // float64 work (nf * 3)
+  T* b = f64 ? (T*)m.r : (T*)m.rf;                  // solve vector (nf * 3)
+  T* y = f64 ? (T*)m.y1 : (T*)m.y1f;                // forward result on x1 (n1 * 3)
+  const T* Z = f64 ? (const T*)m.Z : (const T*)m.Zf;
+  k_gather_rhs<T><<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, g, b);
   count_launch();
-  // t1 = K11^-1 r1
-  double* t1 = m.t1;
-  T* w1 = std::is_same<T, double>::value ? (T*)t1 : (T*)m.rf;
-  const T* Z = std::is_same<T, double>::value ? (const T*)m.Z : (const T*)m.Zf;
-  T* ysc = std::is_same<T, double>::value ? (T*)m.y1 : (T*)m.y1f;
-  if (n1 > 0) {
-    if (std::is_same<T, double>::value) {
-      cudaMemcpyAsync(t1, r, sizeof(double) * 3 * (size_t)n1, cudaMemcpyDeviceToDevice, s);
-    } else {
-      k_convert<double, T><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, r, w1);
-      count_launch();
-    }
-    trisolve<T>(s, m, Z, w1, ysc);
-    if (!std::is_same<T, double>::value) {
-      k_convert<T, double><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, w1, t1);
-      count_launch();
-    }
-  }
+  if (n1 > 0) trisolve_fwd<T>(s, m, Z, b, y);
   if (n2 > 0) {
-    double* y2 = r + 3 * (size_t)n1;      // r2 - K21 t1 (in place)
-    if (n1 > 0) {
-      k_spmv3_sub<double><<<nblk(n2, 128), 128, 0, s>>>(n2, m.k21_ptr, m.k21_col, m.k21_val, t1, y2);
-      count_launch();
-    }
+    T* y2 = b + 3 * (size_t)n1;
     double* u = m.u;
-    const T* Sinv = std::is_same<T, double>::value ? (const T*)m.Sinv : (const T*)m.Sinvf;
-    ProfScope psg(PROF_GEMV, s);
-    if (std::is_same<T, double>::value) {
-      k_gemv3<double><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinv, y2, u);
-      count_launch();
-    } else {
-      T* yf = (T*)m.rf;
-      T* uf = yf + 3 * (size_t)n2;
-      k_convert<double, T><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, y2, yf);
-      k_gemv3<T><<<nblk(n2, 8), 256, 0, s>>>(n2, Sinv, yf, uf);
-      k_convert<T, double><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, uf, u);
-      count_launch(3);
+    double* z2 = r + 3 * (size_t)n1;                // float64 dx2
+    {
+      ProfScope psg(PROF_GEMV, s);
+      if (f64) {
+        k_gemv3<double><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinv, (const double*)y2, u);
+        count_launch();
+      } else {
+        float* uf = m.uf;
+        k_gemv3<float><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinvf, (const float*)y2, uf);
+        k_convert<float, double><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, uf, u);
+        count_launch(2);
+      }
     }
-    // z2 (written over y2 in r)
     if (nc > 0) {
       // The reduced system carries the barrier stiffness (cond ~ kappa b''),
       // so it is factored in float64 in both precisions.
       ProfScope psr(PROF_REDUCED, s);
-      reduced_solve<double>(s, m, m.Sinv, nc, u, y2, info, num_sms);
+      reduced_solve<double>(s, m, m.Sinv, nc, u, z2, info, num_sms);
     } else {
-      cudaMemcpyAsync(y2, u, sizeof(double) * 3 * (size_t)n2, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(z2, u, sizeof(double) * 3 * (size_t)n2, cudaMemcpyDeviceToDevice, s);
     }
-    // dx1 = K11^-1 (r1 - K12 dx2): reuse r1 (still -g in r[0:n1])
-    if (n1 > 0) {
-      k_spmv3_sub<double><<<nblk(n1, 128), 128, 0, s>>>(n1, m.k12_ptr, m.k12_col, m.k12_val, y2, r);
+    if (!f64) {
+      k_convert<double, T><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, z2, y2);
       count_launch();
     }
   }
-  if (n1 > 0) {
-    if (std::is_same<T, double>::value) {
-      trisolve<T>(s, m, Z, (T*)r, ysc);
-    } else {
-      k_convert<double, T><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, r, w1);
-      trisolve<T>(s, m, Z, w1, ysc);
-      k_convert<T, double><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, w1, r);
-      count_launch(2);
-    }
+  if (n1 > 0) trisolve_bwd<T>(s, m, Z, y, b);
+  if (!f64) {
+    k_convert<T, double><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, b, r);
+    count_launch();
   }
   cudaMemsetAsync(dx, 0, sizeof(double) * 3 * (size_t)m.n, s);
   k_scatter_dx<<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, r, dx);

@@ -34,7 +34,12 @@ struct DevMesh {
   double* s = nullptr;        // 3 Ns proxy positions at x
   double* st = nullptr;       // 3 Ns proxy positions at the trial point
   double* ds = nullptr;       // 3 Ns proxy step
-  float* box = nullptr;       // scratch boxes (6 floats per primitive)
+  float* pbox = nullptr;      // 12 floats per primitive (verts, tris, edges)
+  unsigned long long* pkey = nullptr;  // 12 order keys per primitive
+  float* sf = nullptr;        // 3 Ns float32 proxy positions
+  float* dsf = nullptr;       // 3 Ns float32 proxy step
+  unsigned long long* nearl = nullptr;  // pairs within 2 dhat in float32 (cap)
+  double coord_scale = 1.0;   // 2 x largest |rest coordinate|
   // solver ordering
   int* perm = nullptr;        // nf: position -> vertex
   int* pos = nullptr;         // n: vertex -> position or -1
@@ -65,12 +70,14 @@ struct DevMesh {
   double* r = nullptr;        // nf*3
   double* t1 = nullptr;       // n1*3
   double* u = nullptr;        // n2*3
+  float* uf = nullptr;        // n2*3 (mixed)
   float* rf = nullptr;        // nf*3 (mixed)
   // contact work
   int64_t cap = 0;            // pair capacity
   unsigned long long* pairs = nullptr;    // keys (type<<62 | i<<31 | j)
   unsigned long long* cand = nullptr;     // CCD candidates
-  int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite
+  int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite [5] touching
+                              // [6..7] Cholesky info [8] near pairs [9] CCD overflow
   double* scal = nullptr;     // [0] barrier energy [1] alpha [2] elastic energy [3] gnorm2 ...
   double* partials = nullptr; // block partial sums
   int n_partials = 0;
@@ -102,14 +109,13 @@ void launch_proxy(cudaStream_t s, const DevMesh& m, const double* x, double* sp)
 // barrier energy to m.scal[0].
 void launch_detect(cudaStream_t s, const DevMesh& m, const double* sp, double dhat, double kappa);
 // Candidate pairs of the swept boxes sp -> sp + dsp (inflated by dhat) and
-// the ACCD time of impact (min into m.scal[1] as ordered bits).
+// the ACCD time of impact (min into m.scal[1] as ordered bits); the caller
+// zeroes counters [1] and [9] and sets scal[1] = 1.
 void launch_ccd(cudaStream_t s, const DevMesh& m, const double* sp, const double* dsp,
-                double dhat, double ccd_s, int accd_max_iters, int64_t ncand_host);
-void launch_ccd_candidates(cudaStream_t s, const DevMesh& m, const double* sp, const double* dsp,
-                           double dhat);
+                double dhat, double ccd_s, int accd_max_iters);
 // Per-pair barrier gradient and PSD Hessian blocks (pass A) and x2 marks.
 void launch_barrier_pairs(cudaStream_t s, const DevMesh& m, int64_t npairs, const double* sp,
-                          double dhat, double kappa);
+                          double dhat, double kappa, int precision);
 void launch_mark_scan(cudaStream_t s, const DevMesh& m);
 // Scatter pair gradients into g and Hessian blocks into the dense B-check (3nc)^2.
 void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, int nc, double* g);

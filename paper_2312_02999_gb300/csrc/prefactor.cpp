@@ -383,22 +383,25 @@ int build_factor(int64_t n, const double* rest, const int32_t* tets, int64_t T,
         }
       }
     });
-    // rows of L_RJ inside x1 come first (R sorted, x2 positions >= n1)
+    // rows of L_RJ inside x1 come first (R sorted, x2 positions >= n1); the
+    // x2 rows are the block H21 L1^-T of Eq. 8 and are kept as well, so that
+    // one forward pass yields y2 = r2 - L21 L1^-1 r1 and one backward pass
+    // consumes dx2
     int nr1 = 0;
     while (nr1 < nr && Rb[nr1] < n1) ++nr1;
     Supernode& s = f.sn[b];
-    s.c0 = c0; s.ns = ns; s.nr1 = nr1; s.level = level[b];
+    s.c0 = c0; s.ns = ns; s.nr1 = nr1; s.nr = nr; s.level = level[b];
     s.rows_off = (int64_t)f.rows.size();
-    for (int k = 0; k < nr1; ++k) f.rows.push_back(Rb[k]);
+    for (int k = 0; k < nr; ++k) f.rows.push_back(Rb[k]);
     s.z_off = (int64_t)f.Z.size();
-    const int ld = ns + nr1;
+    const int ld = ns + nr;
     f.Z.resize(f.Z.size() + (size_t)ld * ns, 0.0);
     std::vector<double> Li((size_t)ns * ns);
     trtri_lower(Fd, m, ns, Li.data());
     double* Z = f.Z.data() + s.z_off;
     for (int r = 0; r < ns; ++r)
       for (int c = 0; c <= r; ++c) Z[(size_t)c * ld + r] = Li[(size_t)r * ns + c];
-    parallel_for(nr1, [&](int64_t a, int64_t e) {
+    parallel_for(nr, [&](int64_t a, int64_t e) {
       for (int64_t i = a; i < e; ++i) {
         const double* li = Fd + (size_t)(ns + i) * m;
         for (int c = 0; c < ns; ++c) {
@@ -408,7 +411,7 @@ int build_factor(int64_t n, const double* rest, const int32_t* tets, int64_t T,
         }
       }
     });
-    nnz += (int64_t)ns * (ns + 1) / 2 + (int64_t)ns * nr1;
+    nnz += (int64_t)ns * (ns + 1) / 2 + (int64_t)ns * nr;
     // roots of the x1 forest pass their (x2-only) update into Sigma
     if (nd.blk_parent[b] < 0) {
       for (int i = 0; i < nr; ++i) {
