@@ -87,10 +87,23 @@ k_fwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const i
   T a0 = 0, a1 = 0, a2 = 0;
   if (lane < rn) {
     const int kmax = r < ns ? r + 1 : ns;
-    for (int k = wid; k < kmax; k += 8) {
+    // four independent loads and accumulators in flight per lane: the loop is
+    // bound by load and FMA latency, not by bandwidth
+    T q0 = 0, q1 = 0, q2 = 0, d0 = 0, d1 = 0, d2 = 0, e0 = 0, e1 = 0, e2 = 0;
+    int k = wid;
+    for (; k + 24 < kmax; k += 32) {
+      const T z0 = Zj[(size_t)k * ld + r], z1 = Zj[(size_t)(k + 8) * ld + r];
+      const T z2 = Zj[(size_t)(k + 16) * ld + r], z3 = Zj[(size_t)(k + 24) * ld + r];
+      a0 += z0 * bj[3 * k]; a1 += z0 * bj[3 * k + 1]; a2 += z0 * bj[3 * k + 2];
+      q0 += z1 * bj[3 * k + 24]; q1 += z1 * bj[3 * k + 25]; q2 += z1 * bj[3 * k + 26];
+      d0 += z2 * bj[3 * k + 48]; d1 += z2 * bj[3 * k + 49]; d2 += z2 * bj[3 * k + 50];
+      e0 += z3 * bj[3 * k + 72]; e1 += z3 * bj[3 * k + 73]; e2 += z3 * bj[3 * k + 74];
+    }
+    for (; k < kmax; k += 8) {
       const T z = Zj[(size_t)k * ld + r];
       a0 += z * bj[3 * k]; a1 += z * bj[3 * k + 1]; a2 += z * bj[3 * k + 2];
     }
+    a0 += (q0 + d0) + e0; a1 += (q1 + d1) + e1; a2 += (q2 + d2) + e2;
   }
   part[wid][lane][0] = a0; part[wid][lane][1] = a1; part[wid][lane][2] = a2;
   __syncthreads();
@@ -132,11 +145,18 @@ k_bwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const i
   for (int kk = wid; kk < kn; kk += 8) {
     const int k = k0 + kk;
     const T* zc = Zj + (size_t)k * ld;
-    T a0 = 0, a1 = 0, a2 = 0;
-    for (int r = k + lane; r < ld; r += 32) {
+    T a0 = 0, a1 = 0, a2 = 0, q0 = 0, q1 = 0, q2 = 0;
+    int r = k + lane;
+    for (; r + 32 < ld; r += 64) {
+      const T z0 = zc[r], z1 = zc[r + 32];
+      a0 += z0 * wv[3 * r]; a1 += z0 * wv[3 * r + 1]; a2 += z0 * wv[3 * r + 2];
+      q0 += z1 * wv[3 * r + 96]; q1 += z1 * wv[3 * r + 97]; q2 += z1 * wv[3 * r + 98];
+    }
+    if (r < ld) {
       const T z = zc[r];
       a0 += z * wv[3 * r]; a1 += z * wv[3 * r + 1]; a2 += z * wv[3 * r + 2];
     }
+    a0 += q0; a1 += q1; a2 += q2;
     a0 = warp_sum_t(a0); a1 = warp_sum_t(a1); a2 = warp_sum_t(a2);
     res[0] = a0; res[1] = a1; res[2] = a2;
     __syncwarp();
@@ -180,277 +200,6 @@ __global__ void k_gemv3(int n2, const T* __restrict__ A, const T* __restrict__ y
 }
 
 // ---------------------------------------------------------------------------
-// reduced system kernels (row-major dense, T = double or float)
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_gather_S(int nc, const int* __restrict__ clist, const T* __restrict__ Sinv,
-                           int n2, T* __restrict__ S) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nc * nc) return;
-  const int i = idx / nc, j = idx % nc;
-  S[idx] = Sinv[(size_t)clist[i] * n2 + clist[j]];
-}
-
-// per-row compaction of the block occupancy: list[i*nc + k], cnt[i]
-__global__ void k_block_lists(int nc, const int* __restrict__ bocc, int* __restrict__ list,
-                              int* __restrict__ cnt) {
-  const int i = blockIdx.x;
-  if (i >= nc) return;
-  const int lane = threadIdx.x;   // one warp
-  int base = 0;
-  for (int j0 = 0; j0 < nc; j0 += 32) {
-    const int j = j0 + lane;
-    const bool f = j < nc && bocc[(size_t)i * nc + j] != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, f);
-    if (f) list[(size_t)i * nc + base + __popc(m & ((1u << lane) - 1u))] = j;
-    base += __popc(m);
-  }
-  if (lane == 0) cnt[i] = base;
-}
-
-// X = B (L (x) I_3): X[(i,a),(k,b)] = sum_{j in occ(i), j >= k} B[(i,a),(j,b)] L[j][k]
-template <typename T>
-__global__ void k_form_X(int nc, const double* __restrict__ Bc, const T* __restrict__ L,
-                         const int* __restrict__ list, const int* __restrict__ cnt, T* __restrict__ X) {
-  const int n3 = 3 * nc;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n3 * n3) return;
-  const int row = (int)(idx / n3), colx = (int)(idx % n3);
-  const int i = row / 3, k = colx / 3, b = colx % 3;
-  const double* brow = Bc + (size_t)row * n3;
-  T acc = 0;
-  const int c = cnt[i];
-  for (int e = 0; e < c; ++e) {
-    const int j = list[(size_t)i * nc + e];
-    if (j < k) continue;
-    acc += (T)brow[3 * j + b] * L[(size_t)j * nc + k];
-  }
-  X[idx] = acc;
-}
-
-// y = B u_c (over occupied blocks), y[(i,a)]
-__global__ void k_bmv(int nc, const double* __restrict__ Bc, const int* __restrict__ list,
-                      const int* __restrict__ cnt, const int* __restrict__ clist,
-                      const double* __restrict__ u, double* __restrict__ y) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n3 = 3 * nc;
-  if (row >= n3) return;
-  const int i = row / 3;
-  const double* brow = Bc + (size_t)row * n3;
-  double acc = 0.0;
-  for (int e = 0; e < cnt[i]; ++e) {
-    const int j = list[(size_t)i * nc + e];
-    const double* uj = u + 3 * (size_t)clist[j];
-    acc += brow[3 * j] * uj[0] + brow[3 * j + 1] * uj[1] + brow[3 * j + 2] * uj[2];
-  }
-  y[row] = acc;
-}
-
-// N = I + (L (x) I_3)^T X (full), and the augmented last row t0 = (L (x) I_3)^T y
-// N[(i,a),(k,b)] = delta + sum_{j >= i} L[j][i] X[(j,a),(k,b)]
-template <typename T>
-__global__ void k_form_N(int nc, const T* __restrict__ L, const T* __restrict__ X,
-                         const double* __restrict__ y, T* __restrict__ N) {
-  const int n3 = 3 * nc;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)(n3 + 1) * n3) return;
-  const int row = (int)(idx / n3), col = (int)(idx % n3);
-  if (row < n3) {
-    const int i = row / 3, a = row % 3;
-    T acc = (row == col) ? T(1) : T(0);
-    for (int j = i; j < nc; ++j) acc += L[(size_t)j * nc + i] * X[(size_t)(3 * j + a) * n3 + col];
-    N[idx] = acc;
-  } else {
-    const int i = col / 3, a = col % 3;
-    T acc = 0;
-    for (int j = i; j < nc; ++j) acc += L[(size_t)j * nc + i] * (T)y[3 * j + a];
-    N[idx] = acc;
-  }
-}
-
-__device__ __forceinline__ double sqrt_any(double v) { return sqrt(v); }
-__device__ __forceinline__ float sqrt_any(float v) { return sqrtf(v); }
-
-// Right-looking blocked Cholesky (lower, row-major, ld) of the leading N x N
-// block of an (N + extra) x N matrix, in one cooperative launch.  The extra
-// rows receive L_extra = A_extra L^-T.  CTA 0 factors each diagonal block
-// right after updating it (look-ahead) while the other CTAs update the rest.
-template <typename T>
-__global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ A, int N, int extra, int ld,
-                                                   int* __restrict__ info) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ T D[32][33];
-  __shared__ T Pi[32][33];
-  __shared__ T Pj[32][33];
-  const int M = N + extra;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-
-  auto factor_diag = [&](int k0) {
-    const int kb = min(32, N - k0);
-    for (int e = tid; e < kb * kb; e += nthr) {
-      const int i = e / kb, j = e % kb;
-      D[i][j] = (j <= i) ? A[(size_t)(k0 + i) * ld + k0 + j] : T(0);
-    }
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-      if (tid == 0) {
-        T d = D[j][j];
-        if (!(d > T(0))) { atomicOr(info, 1); d = T(1); }
-        D[j][j] = sqrt_any(d);
-      }
-      __syncthreads();
-      for (int i = j + 1 + tid; i < kb; i += nthr) D[i][j] /= D[j][j];
-      __syncthreads();
-      const int m = kb - j - 1;
-      for (int e = tid; e < m * m; e += nthr) {
-        const int i = j + 1 + e / m, c = j + 1 + e % m;
-        if (c <= i) D[i][c] -= D[i][j] * D[c][j];
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < kb * kb; e += nthr) {
-      const int i = e / kb, j = e % kb;
-      A[(size_t)(k0 + i) * ld + k0 + j] = (j <= i) ? D[i][j] : T(0);
-    }
-    __syncthreads();
-  };
-
-  if (blockIdx.x == 0) factor_diag(0);
-  grid.sync();
-  for (int k0 = 0; k0 < N; k0 += 32) {
-    const int kb = min(32, N - k0);
-    const int k1 = k0 + kb;
-    // (1) panel: rows [k1, M) of columns [k0, k1) := A L_kk^-T, 8 rows per CTA step
-    for (int e = tid; e < kb * kb; e += nthr) {
-      const int i = e / kb, j = e % kb;
-      D[i][j] = A[(size_t)(k0 + i) * ld + k0 + j];
-    }
-    __syncthreads();
-    {
-      const int nrow = M - k1;
-      const int lane = tid & 31, wid = tid >> 5;
-      // one warp per row: lanes hold the row's kb entries; forward substitution
-      for (int r = blockIdx.x * (nthr >> 5) + wid; r < nrow; r += gridDim.x * (nthr >> 5)) {
-        T* arow = A + (size_t)(k1 + r) * ld + k0;
-        T xv = (lane < kb) ? arow[lane] : T(0);
-        for (int j = 0; j < kb; ++j) {
-          const T xj = __shfl_sync(0xffffffffu, xv, j) / D[j][j];
-          if (lane == j) xv = xj;
-          if (lane > j && lane < kb) xv -= xj * D[lane][j];
-        }
-        if (lane < kb) arow[lane] = xv;
-      }
-    }
-    grid.sync();
-    // (2) trailing update of rows [k1, M) x cols [k1, N), lower part (tiles)
-    if (k1 < N) {
-      const int nrb = (M - k1 + 31) / 32;
-      const int ncb = (N - k1 + 31) / 32;
-      // enumerate tiles (rb, cb) with cb <= rb (cb < ncb); tile 0 = next diagonal
-      int ntiles = 0;
-      for (int rb = 0; rb < nrb; ++rb) ntiles += min(rb + 1, ncb);
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int rb = 0, rem = tile;
-        while (rem >= min(rb + 1, ncb)) { rem -= min(rb + 1, ncb); ++rb; }
-        const int cb = rem;
-        const int r0 = k1 + rb * 32, c0 = k1 + cb * 32;
-        const int rn = min(32, M - r0), cn = min(32, N - c0);
-        for (int e = tid; e < 32 * kb; e += nthr) {
-          const int i = e / kb, l = e % kb;
-          Pi[i][l] = (i < rn) ? A[(size_t)(r0 + i) * ld + k0 + l] : T(0);
-          Pj[i][l] = (i < cn) ? A[(size_t)(c0 + i) * ld + k0 + l] : T(0);
-        }
-        __syncthreads();
-        for (int e = tid; e < 32 * 32; e += nthr) {
-          const int i = e >> 5, j = e & 31;
-          if (i < rn && j < cn && (r0 + i >= c0 + j || r0 + i >= N)) {
-            T acc = 0;
-            for (int l = 0; l < kb; ++l) acc += Pi[i][l] * Pj[j][l];
-            A[(size_t)(r0 + i) * ld + c0 + j] -= acc;
-          }
-        }
-        __syncthreads();
-        if (tile == 0) factor_diag(k1);   // look-ahead: next diagonal block is final
-      }
-    }
-    grid.sync();
-  }
-}
-
-// Single-CTA backward solve L^T x = b (L lower, row-major ld, n x n) for nrhs
-// right-hand sides stored x[i*nrhs + r]; b is overwritten by x.
-template <typename T>
-__global__ void k_trsv_lt(const T* __restrict__ L, int n, int ld, T* __restrict__ b, int nrhs) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  __shared__ T xs[32][4];
-  for (int i1 = n; i1 > 0; i1 -= 32) {
-    const int i0 = max(0, i1 - 32), nb = i1 - i0;
-    // solve the diagonal block (rows i0..i1) by warp 0, lanes = rhs*? (sequential over rows)
-    if (tid < 32) {
-      for (int r = 0; r < nrhs; ++r) {
-        T xv = (tid < nb) ? b[(size_t)(i0 + tid) * nrhs + r] : T(0);
-        for (int j = nb - 1; j >= 0; --j) {
-          const T xj = __shfl_sync(0xffffffffu, xv, j) / L[(size_t)(i0 + j) * ld + i0 + j];
-          if (tid == j) xv = xj;
-          if (tid < j) xv -= L[(size_t)(i0 + j) * ld + i0 + tid] * xj;
-        }
-        if (tid < nb) { b[(size_t)(i0 + tid) * nrhs + r] = xv; xs[tid][r] = xv; }
-      }
-    }
-    __syncthreads();
-    // update rows above: b[i] -= sum_{j in block} L[j][i] x[j]
-    for (int e = tid; e < i0 * nrhs; e += nthr) {
-      const int i = e / nrhs, r = e % nrhs;
-      T acc = 0;
-      for (int j = 0; j < nb; ++j) acc += L[(size_t)(i0 + j) * ld + i] * xs[j][r];
-      b[(size_t)i * nrhs + r] -= acc;
-    }
-    __syncthreads();
-  }
-}
-
-// z2[q] = u[q] - sum_m Sinv[q, c_m] v[m]   (3-vectors), one warp per row q
-template <typename T>
-__global__ void k_z2(int n2, int nc, const T* __restrict__ Sinv, const int* __restrict__ clist,
-                     const T* __restrict__ v, const double* __restrict__ u, double* __restrict__ z) {
-  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (q >= n2) return;
-  const T* a = Sinv + (size_t)q * n2;
-  double a0 = 0, a1 = 0, a2 = 0;
-  for (int m = lane; m < nc; m += 32) {
-    const double s = (double)a[clist[m]];
-    a0 += s * (double)v[3 * m]; a1 += s * (double)v[3 * m + 1]; a2 += s * (double)v[3 * m + 2];
-  }
-  a0 = warp_sum_t(a0); a1 = warp_sum_t(a1); a2 = warp_sum_t(a2);
-  if (lane == 0) {
-    z[3 * q] = u[3 * q] - a0; z[3 * q + 1] = u[3 * q + 1] - a1; z[3 * q + 2] = u[3 * q + 2] - a2;
-  }
-}
-
-__global__ void k_zero_upper(int n, int ld, double* A) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx % n);
-  if (j > i) A[(size_t)i * ld + j] = 0.0;
-}
-
-template <typename T>
-__global__ void k_zero_upper_t(int n, int ld, T* A) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx % n);
-  if (j > i) A[(size_t)i * ld + j] = T(0);
-}
-
-// gather (augmented row -> vector) helper: x[i] = A[row*ld + i]
-template <typename T>
-__global__ void k_copy_row(int n, const T* __restrict__ A, int row, int ld, T* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = A[(size_t)row * ld + i];
-}
-
-// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 namespace {
@@ -487,46 +236,6 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
   }
 }
 
-template <typename T>
-void launch_chol(cudaStream_t s, T* A, int N, int extra, int ld, int* info, int num_sms) {
-  if (N <= 0) return;
-  int tiles = (N + 31) / 32;
-  int grid = std::max(1, std::min(num_sms, tiles * (tiles + 1) / 2));
-  void* args[] = {&A, &N, &extra, &ld, &info};
-  ProfScope ps(PROF_CHOL, s);
-  cudaLaunchCooperativeKernel((void*)k_chol_coop<T>, dim3(grid), dim3(256), args, 0, s);
-  count_launch();
-}
-
-// Reduced push-through system (Eq. 11 reading): z2 = u - Sinv[:,c] v.
-template <typename T>
-void reduced_solve(cudaStream_t s, const DevMesh& m, const T* Sinv, int nc, const double* u,
-                   double* z2, int* info, int num_sms) {
-  const int n3 = 3 * nc;
-  // workspace layout inside m.red / m.redf (capacity red_cap elements)
-  T* base = std::is_same<T, double>::value ? (T*)m.red : (T*)m.redf;
-  T* S = base;                                  // nc*nc (-> L_s)
-  T* X = S + (size_t)nc * nc;                   // n3*n3
-  T* N = X + (size_t)n3 * n3;                   // (n3+1)*n3
-  T* tv = N + (size_t)(n3 + 1) * n3;            // n3 (t, then v)
-  double* y = m.red + m.red_cap - (size_t)n3 - 8;  // float64 B u_c (tail of m.red)
-  int* list = m.bocc + (size_t)nc * nc;         // nc*nc block lists (after bocc)
-  int* cnt = list + (size_t)nc * nc;
-  k_gather_S<T><<<nblk((int64_t)nc * nc, 256), 256, 0, s>>>(nc, m.clist, Sinv, m.n2, S);
-  launch_chol<T>(s, S, nc, 0, nc, info, num_sms);
-  k_zero_upper_t<T><<<nblk((int64_t)nc * nc, 256), 256, 0, s>>>(nc, nc, S);
-  k_block_lists<<<nc, 32, 0, s>>>(nc, m.bocc, list, cnt);
-  k_form_X<T><<<nblk((int64_t)n3 * n3, 256), 256, 0, s>>>(nc, m.Bc, S, list, cnt, X);
-  k_bmv<<<nblk(n3, 128), 128, 0, s>>>(nc, m.Bc, list, cnt, m.clist, u, y);
-  k_form_N<T><<<nblk((int64_t)(n3 + 1) * n3, 256), 256, 0, s>>>(nc, S, X, y, N);
-  launch_chol<T>(s, N, n3, 1, n3, info, num_sms);
-  k_copy_row<T><<<nblk(n3, 256), 256, 0, s>>>(n3, N, n3, n3, tv);
-  k_trsv_lt<T><<<1, 1024, 0, s>>>(N, n3, n3, tv, 1);       // t = L_N^-T l
-  k_trsv_lt<T><<<1, 1024, 0, s>>>(S, nc, nc, tv, 3);       // v = (L_s (x) I)^-T t
-  k_z2<T><<<nblk(m.n2, 8), 256, 0, s>>>(m.n2, nc, Sinv, m.clist, tv, u, z2);
-  count_launch(9);
-}
-
 // Eq. 8 with H = K (x) I_3 in solver positions [x1 ; x2], r = -g-hat:
 //   lower:    z1 = L1^-1 r1,  y2 = r2 - L21 z1        (one forward pass; the
 //             x2 rows of the supernodes hold L21 = H21 L1^-T)
@@ -561,10 +270,10 @@ void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx
       }
     }
     if (nc > 0) {
-      // The reduced system carries the barrier stiffness (cond ~ kappa b''),
-      // so it is factored in float64 in both precisions.
+      // The reduced system carries the barrier stiffness (cond ~ kappa b''):
+      // float64 factors, or float32 factors refined with float64 residuals.
       ProfScope psr(PROF_REDUCED, s);
-      reduced_solve<double>(s, m, m.Sinv, nc, u, z2, info, num_sms);
+      reduced_solve(s, m, nc, u, y2, z2, info, num_sms, f64 ? 0 : 1);
     } else {
       cudaMemcpyAsync(z2, u, sizeof(double) * 3 * (size_t)n2, cudaMemcpyDeviceToDevice, s);
     }
@@ -584,11 +293,6 @@ void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx
 }
 
 }  // namespace
-
-int64_t reduced_workspace_elems(int nc) {
-  const int64_t n3 = 3 * (int64_t)nc;
-  return (int64_t)nc * nc + n3 * n3 + (n3 + 1) * n3 + 2 * n3 + 16;
-}
 
 void set_solver_smem_limits(int max_bytes) {
   cudaFuncSetAttribute(k_fwd_chunk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);

@@ -125,6 +125,12 @@ void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, in
 void global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
                  int precision, int* info_dev, int num_sms);
 int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
+// z2 = u - Sigma^-1 Q^T v with the push-through reduced system (k_reduced.cu);
+// precision 0: float64 factors, 1: float32 factors + float64 refinement.
+// y2 (double for precision 0, float for 1) is the Schur right-hand side with
+// u = Sigma^-1 y2; it scales the refinement's stopping test.
+void reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
+                   double* z2, int* info, int num_sms, int precision);
 void set_solver_smem_limits(int max_bytes);
 
 // ---- misc ------------------------------------------------------------------
