@@ -73,9 +73,11 @@ typedef struct {
   int32_t max_ls;         /* line-search halvings before FSIM_ELS_FAIL          */
   double ccd_s;           /* additive-CCD gap ratio s (pairs keep >= s*d0)      */
   int32_t accd_max_iters; /* additive-CCD advancement cap per pair              */
-  int32_t reserved0;
+  int32_t coop_ctas;      /* CTAs of the cooperative reduced-system kernel;
+                             0 = one per SM (a tuning knob: fewer CTAs make
+                             its grid-wide barriers cheaper)                   */
   int64_t contact_capacity; /* max candidate/active pairs per detection; <= 0
-                               selects 64 * (number of proxy triangles)        */
+                               selects max(2^20, 256 * proxy triangles)        */
 } fsim_params;
 
 /* Per-frame statistics filled by fsim_solve_frame. */
@@ -91,11 +93,14 @@ typedef struct {
   double grad_norm0;      /* ||g-hat_free||_2 at x_t                              */
   double energy;          /* E-hat at the returned positions                      */
   double alpha_min;       /* smallest accepted step of the frame                  */
+  double sum_nc3;         /* sum of n_c^3 over the frame's global steps (the
+                             reduced system's work scales with it)            */
 } fsim_frame_stats;
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
- * contact_capacity auto.  dhat must still be set by the caller. */
+ * coop_ctas 0, contact_capacity auto.  dhat must still be set by the
+ * caller. */
 fsim_status fsim_default_params(fsim_params* p);
 
 /* Create a context on CUDA device `device`; it owns one CUDA stream and all
@@ -279,13 +284,93 @@ fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_dev, int64_t 
                              void* stream);
 
 /* Sizes of a mesh (n, T, Ns, Nt, Ne, free / x1 / x2 vertex counts), the
- * scalar factor's stored entries and supernode / level counts, and the
- * barrier stiffness kappa in use (after fsim_prefactor). */
+ * scalar factor's stored entries and supernode / level counts, the bytes of
+ * one per-solve workspace (what each request-server slot of this mesh
+ * allocates, before its reduced-system buffers grow), and the barrier
+ * stiffness kappa in use (after fsim_prefactor). */
 typedef struct {
   int64_t n, T, Ns, Nt, Ne, n_free, n1, n2, factor_nnz, n_supernodes, n_levels;
+  int64_t workspace_bytes;
   double kappa;
 } fsim_mesh_info;
 fsim_status fsim_mesh_info_get(fsim_ctx_t ctx, int mesh_id, fsim_mesh_info* info);
+
+/* ---- request server: continuous batching of frame solves -----------------
+ * The paper solves one frame at a time; this server is the serving layer on
+ * top of Algorithm 1.  Several frame solves run at once, each on its own
+ * host thread, CUDA stream and workspace slot (a private copy of the
+ * per-solve buffers of its mesh; the factor of K11, Sigma^-1 and the mesh
+ * topology stay shared and resident).  A request that arrives while others
+ * are on the GPU starts as soon as a worker is idle and a slot fits in the
+ * memory budget; idle slots of other meshes are evicted least recently used
+ * first.  Every request carries its own actuation and start positions, so
+ * its result is the same whether it runs alone or among others (up to the
+ * order of floating-point atomics, as for any two runs).
+ */
+typedef struct fsim_server_s* fsim_server_t;
+
+typedef struct {
+  int32_t mesh_id;        /* a prefactored mesh of the server's context        */
+  int32_t precision;      /* FSIM_FP64 or FSIM_MIXED                            */
+  const double* fiber;    /* 3T: per-tet fiber direction                        */
+  const double* stretch;  /* T: per-tet stretch a > 0                           */
+  const double* x_init;   /* 3n start positions, or NULL for the rest pose      */
+  int32_t flags;          /* 0: fiber, stretch and x_init are host arrays,
+                             copied (and checked) at submit.
+                             FSIM_REQ_DEVICE: they are device arrays, read when
+                             the request runs; they must stay valid and
+                             unchanged until it completes and are not checked
+                             on the host (a non-positive stretch surfaces as
+                             FSIM_ENONFINITE)                                 */
+  int32_t reserved0;
+  double* x_out_dev;      /* device, 3n, or NULL: receives the converged
+                             positions before the request completes; with
+                             FSIM_REQ_DEVICE the positions are returned only
+                             here (fsim_server_wait's x_out is then unused)   */
+} fsim_request;
+#define FSIM_REQ_DEVICE 1
+
+typedef struct {
+  int32_t workers;          /* concurrent solves, 1..16                         */
+  int32_t reserved0;
+  int64_t mem_budget_bytes; /* cap on the bytes of all workspace slots; <= 0
+                               means no cap                                     */
+} fsim_server_config;
+
+typedef struct {
+  int32_t workers, slots, peak_slots, peak_running;
+  int64_t queued, completed, bytes_in_use;
+} fsim_server_info;
+
+/* Start the worker threads.  The context must outlive the server; meshes
+ * must be uploaded and prefactored before their requests are submitted.
+ * Errors: FSIM_EINVAL (workers outside 1..16), FSIM_ENOMEM. */
+fsim_status fsim_server_create(fsim_ctx_t ctx, const fsim_server_config* cfg, fsim_server_t* out);
+/* Queue one frame solve; host inputs are copied before return.  *ticket
+ * names it for fsim_server_wait.  Errors: FSIM_EINVAL, FSIM_ENOT_READY (mesh
+ * not prefactored), FSIM_ENONFINITE (stretch <= 0 or a zero / non-finite
+ * fiber), FSIM_ENOMEM (one workspace of this mesh, see fsim_mesh_info's
+ * workspace_bytes, is larger than the memory budget). */
+fsim_status fsim_server_submit(fsim_server_t srv, const fsim_request* req, int64_t* ticket);
+/* *done = 1 once the request has finished (0 while queued or running). */
+fsim_status fsim_server_poll(fsim_server_t srv, int64_t ticket, int32_t* done);
+/* Block until the request finishes; copy its positions (3n, may be NULL) and
+ * statistics, its latency from submit to completion and its queueing time
+ * (submit to start), in milliseconds.  Each ticket is waited for once.
+ * Returns the solve's status (as fsim_solve_frame would).  Must not race
+ * with fsim_server_destroy. */
+fsim_status fsim_server_wait(fsim_server_t srv, int64_t ticket, double* x_out,
+                             fsim_frame_stats* stats, double* latency_ms, double* queue_ms);
+fsim_status fsim_server_info_get(fsim_server_t srv, fsim_server_info* info);
+/* Finish the running solves, drop queued ones and free every slot. */
+fsim_status fsim_server_destroy(fsim_server_t srv);
+
+/* Batched form: solve n_req independent frames on a temporary server with
+ * `workers` concurrent solves; x_out[i] (3n of request i's mesh) and
+ * stats[i] receive the results (either may be NULL).  Returns the first
+ * non-OK status (each stats[i].status has its own). */
+fsim_status fsim_solve_frames(fsim_ctx_t ctx, int32_t n_req, const fsim_request* reqs,
+                              int32_t workers, double* const* x_out, fsim_frame_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -14,46 +14,11 @@
 
 #include "fsim_internal.h"
 #include "kernels.h"
+#include "runtime.h"
 
 using namespace fsim;
 
 namespace {
-
-struct MeshState {
-  DevMesh d;
-  bool prefactored = false, actuated = false;
-  fsim_params p{};
-  double kappa = 0.0;
-  int64_t factor_nnz = 0;
-  std::vector<void*> allocs;     // device buffers owned by this mesh
-  // host copies kept for the prefactor
-  std::vector<double> rest;
-  std::vector<int32_t> tets;
-  std::vector<uint8_t> pinned;
-  std::vector<uint8_t> x2mask;
-  // scratch for the step entry points
-  double* gtmp = nullptr;
-  double* proj = nullptr;
-  double* dxtmp = nullptr;
-  bool has_x = false;
-};
-
-}  // namespace
-
-struct fsim_ctx_s {
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  std::vector<std::unique_ptr<MeshState>> meshes;
-  // pinned host readback area
-  int* h_counters = nullptr;   // kCounters ints
-  double* h_scal = nullptr;    // 8 doubles
-};
-
-namespace {
-
-constexpr int kCounters = 16;
-constexpr int kScal = 8;
 
 #define CK(call)                                                   \
   do {                                                             \
@@ -66,14 +31,17 @@ constexpr int kScal = 8;
   } while (0)
 
 template <typename T>
-int dalloc(MeshState& ms, T** p, size_t count) {
+int dalloc(std::vector<void*>& allocs, T** p, size_t count, size_t* bytes = nullptr) {
   *p = nullptr;
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
   if (e != cudaSuccess) { cudaGetLastError(); return FSIM_ENOMEM; }
-  ms.allocs.push_back(*p);
+  allocs.push_back(*p);
+  if (bytes) *bytes += sizeof(T) * count;
   return FSIM_OK;
 }
+template <typename T>
+int dalloc(MeshState& ms, T** p, size_t count) { return dalloc(ms.allocs, p, count); }
 
 #define TRY(x)                    \
   do {                            \
@@ -96,9 +64,13 @@ MeshState* get_mesh(fsim_ctx_t ctx, int id) {
   return ctx->meshes[id].get();
 }
 
+void free_list(std::vector<void*>& allocs) {
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+}
+
 void free_mesh(MeshState& ms) {
-  for (void* p : ms.allocs) cudaFree(p);
-  ms.allocs.clear();
+  free_list(ms.allocs);
   delete[] ms.d.h_level_ptr;
   delete[] ms.d.h_level_maxns;
   delete[] ms.d.h_level_maxld;
@@ -111,35 +83,88 @@ void free_mesh(MeshState& ms) {
   ms.d.h_bwd_ptr = nullptr;
 }
 
-int sync_read(fsim_ctx_t ctx, const DevMesh& m) {
-  CK(cudaMemcpyAsync(ctx->h_counters, m.counters, sizeof(int) * kCounters, cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaMemcpyAsync(ctx->h_scal, m.scal, sizeof(double) * kScal, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+Exec ctx_exec(fsim_ctx_t ctx, MeshState& ms) {
+  Exec ex;
+  ex.stream = ctx->stream;
+  ex.h_counters = ctx->h_counters;
+  ex.h_scal = ctx->h_scal;
+  ex.coop_ctas = ms.p.coop_ctas > 0 ? std::min(ms.p.coop_ctas, ctx->num_sms) : ctx->num_sms;
+  ex.allocs = &ms.allocs;
+  return ex;
+}
+
+int sync_read(const Exec& ex, const DevMesh& m) {
+  CK(cudaMemcpyAsync(ex.h_counters, m.counters, sizeof(int) * kCounters, cudaMemcpyDeviceToHost,
+                     ex.stream));
+  CK(cudaMemcpyAsync(ex.h_scal, m.scal, sizeof(double) * kScal, cudaMemcpyDeviceToHost, ex.stream));
+  CK(cudaStreamSynchronize(ex.stream));
   return FSIM_OK;
 }
 
-// Make the reduced-system buffers large enough for nc contact vertices.
-int ensure_reduced(fsim_ctx_t ctx, MeshState& ms, int nc) {
-  DevMesh& m = ms.d;
+// Make the reduced-system buffers of workspace m large enough for nc
+// contact vertices (grows by 1.5x, at most to n2).
+int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
   if (nc <= m.nc_cap && m.Bc != nullptr) return FSIM_OK;
   int cap = std::max(nc, std::max(16, m.nc_cap * 3 / 2));
   cap = std::min(cap, std::max(m.n2, 1));
-  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaStreamSynchronize(ex.stream));
   auto release = [&](void* p) {
     if (!p) return;
     cudaFree(p);
-    ms.allocs.erase(std::remove(ms.allocs.begin(), ms.allocs.end(), p), ms.allocs.end());
+    auto& v = *ex.allocs;
+    v.erase(std::remove(v.begin(), v.end(), p), v.end());
   };
   release(m.Bc); release(m.bocc); release(m.red); release(m.redf);
   m.Bc = nullptr; m.bocc = nullptr; m.red = nullptr; m.redf = nullptr;
   const int64_t n3 = 3 * (int64_t)cap;
-  TRY(dalloc(ms, &m.Bc, (size_t)(n3 * n3)));
-  TRY(dalloc(ms, &m.bocc, (size_t)(2 * (int64_t)cap * cap + cap + 32)));
+  TRY(dalloc(*ex.allocs, &m.Bc, (size_t)(n3 * n3), ex.bytes));
+  TRY(dalloc(*ex.allocs, &m.bocc, (size_t)(2 * (int64_t)cap * cap + cap + 32), ex.bytes));
   m.red_cap = reduced_workspace_elems(cap);
-  TRY(dalloc(ms, &m.red, (size_t)m.red_cap));
-  TRY(dalloc(ms, &m.redf, (size_t)m.red_cap));
+  TRY(dalloc(*ex.allocs, &m.red, (size_t)m.red_cap, ex.bytes));
+  TRY(dalloc(*ex.allocs, &m.redf, (size_t)m.red_cap, ex.bytes));
   m.nc_cap = cap;
+  return FSIM_OK;
+}
+
+// Per-solve buffers of a workspace (everything a frame solve writes).  The
+// constant mesh data (factor, Sigma^-1, topology) stays shared.  Used for
+// the mesh's own workspace at prefactor and for the server's extra slots.
+int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, size_t* bytes) {
+  const size_t n = m.n, T = m.T, Ns = m.Ns;
+  const size_t np = (size_t)m.Ns + m.Nt + m.Ne;
+  TRY(dalloc(al, &m.x, 3 * n, bytes));
+  TRY(dalloc(al, &m.xt, 3 * n, bytes));
+  TRY(dalloc(al, &m.dx, 3 * n, bytes));
+  TRY(dalloc(al, &m.g, 3 * n, bytes));
+  TRY(dalloc(al, &m.act, 6 * T, bytes));
+  TRY(dalloc(al, &m.tetf, 12 * T, bytes));
+  TRY(dalloc(al, &m.tetf_t, 12 * T, bytes));
+  TRY(dalloc(al, &m.s, 3 * Ns, bytes));
+  TRY(dalloc(al, &m.st, 3 * Ns, bytes));
+  TRY(dalloc(al, &m.ds, 3 * Ns, bytes));
+  TRY(dalloc(al, &m.pbox, 12 * np, bytes));
+  TRY(dalloc(al, &m.pkey, 12 * np, bytes));
+  TRY(dalloc(al, &m.sf, 3 * Ns, bytes));
+  TRY(dalloc(al, &m.dsf, 3 * Ns, bytes));
+  TRY(dalloc(al, &m.counters, kCounters, bytes));
+  TRY(dalloc(al, &m.scal, kScal, bytes));
+  TRY(dalloc(al, &m.partials, (size_t)m.n_partials, bytes));
+  TRY(dalloc(al, &m.y1, 3 * (size_t)std::max(m.n1, 1), bytes));
+  TRY(dalloc(al, &m.y1f, 3 * (size_t)std::max(m.n1, 1), bytes));
+  TRY(dalloc(al, &m.r, 3 * (size_t)m.nf, bytes));
+  TRY(dalloc(al, &m.u, 3 * (size_t)std::max(m.n2, 1), bytes));
+  TRY(dalloc(al, &m.rf, 3 * (size_t)m.nf + 8, bytes));
+  TRY(dalloc(al, &m.uf, 3 * (size_t)std::max(m.n2, 1), bytes));
+  TRY(dalloc(al, &m.pairs, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.cand, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.nearl, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.x2mark, (size_t)std::max(m.n2, 1), bytes));
+  TRY(dalloc(al, &m.clist, (size_t)std::max(m.n2, 1), bytes));
+  m.Bc = nullptr; m.bocc = nullptr; m.red = nullptr; m.redf = nullptr;
+  m.red_cap = 0; m.nc_cap = 0;
+  (void)ms;
   return FSIM_OK;
 }
 
@@ -148,10 +173,9 @@ int ensure_reduced(fsim_ctx_t ctx, MeshState& ms, int nc) {
 // tetf), proxy positions sb and the constraint set with barrier energy.
 // Leaves E in scal[2], B in scal[0], |C| in counters[0].
 // ---------------------------------------------------------------------------
-int evaluate(fsim_ctx_t ctx, MeshState& ms, const double* xb, double* sb, double* tetf,
-             double* proj, int prec) {
-  DevMesh& m = ms.d;
-  cudaStream_t s = ctx->stream;
+int evaluate(const Exec& ex, const MeshState& ms, const DevMesh& m, const double* xb, double* sb,
+             double* tetf, double* proj, int prec) {
+  cudaStream_t s = ex.stream;
   CK(cudaMemsetAsync(m.counters, 0, sizeof(int) * 3, s));       // |C|, candidates, overflow
   CK(cudaMemsetAsync(m.counters + 5, 0, sizeof(int), s));       // touching pair
   CK(cudaMemsetAsync(m.counters + 8, 0, sizeof(int), s));       // near-pair list
@@ -165,20 +189,20 @@ int evaluate(fsim_ctx_t ctx, MeshState& ms, const double* xb, double* sb, double
 }
 
 // Gradient g-hat (elastic from tetf + barrier over the pairs in m.pairs at
-// sb) into gout, the contact-affected set, B-check (if hess) and ||g||^2.
+// sb) into gout, the contact-affected set, B-check and ||g||^2.
 // Requires counters[0] (|C|) already on the host in npairs.
-int gradient_and_hessian(fsim_ctx_t ctx, MeshState& ms, const double* sb, const double* tetf,
-                         double* gout, int64_t npairs, int prec, int* nc_out, double* gn2_out) {
-  DevMesh& m = ms.d;
-  cudaStream_t s = ctx->stream;
+int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const double* sb,
+                         const double* tetf, double* gout, int64_t npairs, int prec, int* nc_out,
+                         double* gn2_out) {
+  cudaStream_t s = ex.stream;
   launch_gather_forces(s, m, tetf, gout);
   CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
   launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, ms.kappa, prec);
   if (m.n2 > 0) launch_mark_scan(s, m);
   else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
-  TRY(sync_read(ctx, m));
-  int nc = ctx->h_counters[3];
-  TRY(ensure_reduced(ctx, ms, std::max(nc, 1)));
+  TRY(sync_read(ex, m));
+  int nc = ex.h_counters[3];
+  TRY(ensure_reduced(ex, m, std::max(nc, 1)));
   if (nc > 0) {
     CK(cudaMemsetAsync(m.Bc, 0, sizeof(double) * 9 * (size_t)nc * nc, s));
     CK(cudaMemsetAsync(m.bocc, 0, sizeof(int) * (size_t)nc * nc, s));
@@ -187,16 +211,15 @@ int gradient_and_hessian(fsim_ctx_t ctx, MeshState& ms, const double* sb, const 
   const int nb = gnorm_blocks(m.n);
   launch_gnorm2(s, m, gout, m.partials, nb);
   launch_sum_partials(s, m.partials, nb, m.scal + 3);
-  TRY(sync_read(ctx, m));
+  TRY(sync_read(ex, m));
   *nc_out = nc;
-  *gn2_out = ctx->h_scal[3];
+  *gn2_out = ex.h_scal[3];
   return FSIM_OK;
 }
 
-int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool init_is_dev,
-                     int prec, fsim_frame_stats* stats) {
-  DevMesh& m = ms.d;
-  cudaStream_t s = ctx->stream;
+int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
+                     bool init_is_dev, int prec, fsim_frame_stats* stats) {
+  cudaStream_t s = ex.stream;
   const fsim_params& p = ms.p;
   fsim_frame_stats st{};
   st.alpha_min = 1.0;
@@ -207,19 +230,19 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
   launch_reset_pinned(s, m, m.x);
   CK(cudaMemsetAsync(m.counters + 4, 0, sizeof(int), s));
   launch_check_finite(s, 3 * m.n, m.x, m.counters + 4);
-  TRY(evaluate(ctx, ms, m.x, m.s, m.tetf, nullptr, prec));
-  TRY(sync_read(ctx, m));
+  TRY(evaluate(ex, ms, m, m.x, m.s, m.tetf, nullptr, prec));
+  TRY(sync_read(ex, m));
   int rc = FSIM_OK;
-  if (ctx->h_counters[4]) rc = FSIM_ENONFINITE;
-  else if (ctx->h_counters[5]) rc = FSIM_EINTERSECTING;
-  else if (ctx->h_counters[2]) rc = FSIM_ECONTACT_OVERFLOW;
-  int64_t npairs = ctx->h_counters[0];
-  double E = ctx->h_scal[2] + ctx->h_scal[0];
+  if (ex.h_counters[4]) rc = FSIM_ENONFINITE;
+  else if (ex.h_counters[5]) rc = FSIM_EINTERSECTING;
+  else if (ex.h_counters[2]) rc = FSIM_ECONTACT_OVERFLOW;
+  int64_t npairs = ex.h_counters[0];
+  double E = ex.h_scal[2] + ex.h_scal[0];
   double gn = 0.0, tol = 0.0;
   int nc = 0;
   if (rc == FSIM_OK) {
     double gn2;
-    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
+    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
     gn = std::sqrt(gn2);
     st.grad_norm0 = gn;
     tol = std::max(p.tol_abs, p.tol_rel * gn);
@@ -232,8 +255,8 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     if (st.iterations >= p.max_iters) { rc = FSIM_ENOT_CONVERGED; break; }
     // global step (Eq. 4 via Eq. 8-11)
     CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-    global_step(s, m, m.g, m.dx, nc, prec, m.counters + 6, ctx->num_sms);
-    CK(cudaGetLastError());
+    CK(global_step(s, m, m.g, m.dx, nc, prec, m.counters + 6, ex.coop_ctas));
+    st.sum_nc3 += (double)nc * nc * nc;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
     launch_proxy(s, m, m.dx, m.ds);
@@ -248,15 +271,15 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     int64_t np_t = 0;
     for (int k = 0; k <= p.max_ls; ++k) {
       launch_axpy_positions(s, 3 * m.n, m.x, m.dx, m.scal + 1, scale, m.xt);
-      TRY(evaluate(ctx, ms, m.xt, m.st, m.tetf_t, nullptr, prec));
-      TRY(sync_read(ctx, m));
-      if (k == 0 && ctx->h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
-      if (k == 0 && ctx->h_counters[9]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
+      TRY(evaluate(ex, ms, m, m.xt, m.st, m.tetf_t, nullptr, prec));
+      TRY(sync_read(ex, m));
+      if (k == 0 && ex.h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
+      if (k == 0 && ex.h_counters[9]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
       st.ls_trials++;
-      Et = ctx->h_scal[2] + ctx->h_scal[0];
-      np_t = ctx->h_counters[0];
-      if (ctx->h_counters[2]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
-      if (!ctx->h_counters[5] && std::isfinite(Et) && Et <= E + 1e-12 * std::fabs(E)) {
+      Et = ex.h_scal[2] + ex.h_scal[0];
+      np_t = ex.h_counters[0];
+      if (ex.h_counters[2]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
+      if (!ex.h_counters[5] && std::isfinite(Et) && Et <= E + 1e-12 * std::fabs(E)) {
         accepted = true;
         break;
       }
@@ -264,7 +287,7 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     }
     if (rc != FSIM_OK) break;
     if (!accepted) { rc = FSIM_ELS_FAIL; break; }
-    st.alpha_min = std::min(st.alpha_min, ctx->h_scal[1] * scale);
+    st.alpha_min = std::min(st.alpha_min, ex.h_scal[1] * scale);
     std::swap(m.x, m.xt);
     std::swap(m.s, m.st);
     std::swap(m.tetf, m.tetf_t);
@@ -272,11 +295,10 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
     npairs = np_t;
     st.iterations++;
     double gn2;
-    TRY(gradient_and_hessian(ctx, ms, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
+    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
     gn = std::sqrt(gn2);
     if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
   }
-  ms.has_x = true;
   st.status = rc;
   st.grad_norm = gn;
   st.energy = E;
@@ -286,6 +308,26 @@ int solve_frame_impl(fsim_ctx_t ctx, MeshState& ms, const double* x_init, bool i
 }
 
 }  // namespace
+
+namespace fsim {
+int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allocs, size_t* bytes) {
+  return alloc_workspace(ms, m, allocs, bytes);
+}
+int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
+                   bool init_is_dev, int precision, fsim_frame_stats* stats) {
+  return solve_frame_impl(ex, ms, m, x_init, init_is_dev, precision, stats);
+}
+void rt_free_list(std::vector<void*>& allocs) { free_list(allocs); }
+size_t rt_slot_bytes(const MeshState& ms) {
+  if (!ms.prefactored) return 0;
+  const int64_t cap = std::min(std::max(ms.d.n2, 1), 64);
+  const int64_t n3 = 3 * cap;
+  return ms.ws_bytes + sizeof(double) * (size_t)(n3 * n3) +
+         sizeof(int) * (size_t)(2 * cap * cap + cap + 32) +
+         (sizeof(double) + sizeof(float)) * (size_t)reduced_workspace_elems((int)cap);
+}
+MeshState* rt_mesh(fsim_ctx_t ctx, int mesh_id) { return get_mesh(ctx, mesh_id); }
+}  // namespace fsim
 
 // ===========================================================================
 extern "C" {
@@ -415,19 +457,10 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
   }
   std::vector<int> tets_i(tets, tets + 4 * T);
   TRY(upload(ms, s, &m.rest, rest_xyz, 3 * n));
-  TRY(upload(ms, s, &m.x, rest_xyz, 3 * n));
-  TRY(dalloc(ms, &m.xt, 3 * n));
-  TRY(dalloc(ms, &m.dx, 3 * n));
-  TRY(dalloc(ms, &m.g, 3 * n));
-  TRY(dalloc(ms, &ms.gtmp, 3 * n));
-  TRY(dalloc(ms, &ms.dxtmp, 3 * n));
   TRY(upload(ms, s, &m.pinned, pinned, n));
   TRY(upload(ms, s, (int**)&m.tets, tets_i.data(), 4 * T));
-  TRY(dalloc(ms, &m.tetf, 12 * T));
-  TRY(dalloc(ms, &m.tetf_t, 12 * T));
   TRY(upload(ms, s, &m.vinc_ptr, vptr.data(), n + 1));
   TRY(upload(ms, s, &m.vinc_slot, vslot.data(), 4 * T));
-  TRY(dalloc(ms, &m.act, 6 * T));
   if (Ns > 0) {
     TRY(upload(ms, s, &m.Wptr, W_rowptr, Ns + 1));
     TRY(upload(ms, s, &m.Wcol, W_col, W_rowptr[Ns]));
@@ -440,23 +473,12 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
   }
   TRY(upload(ms, s, &m.tris, proxy_tris, 3 * Nt));
   TRY(upload(ms, s, &m.edges, edges.data(), edges.size()));
-  TRY(dalloc(ms, &m.s, 3 * Ns));
-  TRY(dalloc(ms, &m.st, 3 * Ns));
-  TRY(dalloc(ms, &m.ds, 3 * Ns));
   {
-    const int64_t np = Ns + Nt + (int64_t)m.Ne;
-    TRY(dalloc(ms, &m.pbox, 12 * (size_t)np));
-    TRY(dalloc(ms, &m.pkey, 12 * (size_t)np));
-    TRY(dalloc(ms, &m.sf, 3 * (size_t)Ns));
-    TRY(dalloc(ms, &m.dsf, 3 * (size_t)Ns));
     double mx = 0.0;
     for (int64_t k = 0; k < 3 * n; ++k) mx = std::max(mx, std::fabs(rest_xyz[k]));
     m.coord_scale = 2.0 * std::max(mx, 1e-30);
   }
-  TRY(dalloc(ms, &m.counters, kCounters));
-  TRY(dalloc(ms, &m.scal, kScal));
   m.n_partials = std::max(elastic_blocks(m.T), gnorm_blocks(m.n)) + 16;
-  TRY(dalloc(ms, &m.partials, m.n_partials));
   CK(cudaStreamSynchronize(s));
   ctx->meshes.push_back(std::move(msp));
   *mesh_id = (int)ctx->meshes.size() - 1;
@@ -466,7 +488,8 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
 fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   MeshState* msp = get_mesh(ctx, mesh_id);
   if (!msp || !p || !(p->dhat > 0.0) || !(p->weight_scale > 0.0) || p->max_iters < 0 ||
-      p->max_ls < 0 || !(p->ccd_s > 0.0 && p->ccd_s < 1.0) || p->accd_max_iters <= 0)
+      p->max_ls < 0 || !(p->ccd_s > 0.0 && p->ccd_s < 1.0) || p->accd_max_iters <= 0 ||
+      p->coop_ctas < 0)
     return FSIM_EINVAL;
   if (msp->prefactored) return FSIM_EINVAL;
   cudaSetDevice(ctx->device);
@@ -546,36 +569,24 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   }
   TRY(upload(ms, s, &m.fwd_items, fwd.data(), fwd.size()));
   TRY(upload(ms, s, &m.bwd_items, bwd.data(), bwd.size()));
-  TRY(dalloc(ms, &m.y1, 3 * (size_t)std::max(m.n1, 1)));
-  TRY(dalloc(ms, &m.y1f, 3 * (size_t)std::max(m.n1, 1)));
-  TRY(upload(ms, s, &m.k12_ptr, f.k12_ptr.data(), f.k12_ptr.size()));
-  TRY(upload(ms, s, &m.k12_col, f.k12_col.data(), f.k12_col.size()));
-  TRY(upload(ms, s, &m.k12_val, f.k12_val.data(), f.k12_val.size()));
-  TRY(upload(ms, s, &m.k21_ptr, f.k21_ptr.data(), f.k21_ptr.size()));
-  TRY(upload(ms, s, &m.k21_col, f.k21_col.data(), f.k21_col.size()));
-  TRY(upload(ms, s, &m.k21_val, f.k21_val.data(), f.k21_val.size()));
   TRY(upload(ms, s, &m.Sinv, f.sigma_inv.data(), f.sigma_inv.size()));
   {
     std::vector<float> sf(f.sigma_inv.begin(), f.sigma_inv.end());
     TRY(upload(ms, s, &m.Sinvf, sf.data(), sf.size()));
     CK(cudaStreamSynchronize(s));
   }
-  TRY(dalloc(ms, &m.r, 3 * (size_t)m.nf));
-  TRY(dalloc(ms, &m.t1, 3 * (size_t)std::max(m.n1, 1)));
-  TRY(dalloc(ms, &m.u, 3 * (size_t)std::max(m.n2, 1)));
-  TRY(dalloc(ms, &m.rf, 3 * (size_t)m.nf + 8));
-  TRY(dalloc(ms, &m.uf, 3 * (size_t)std::max(m.n2, 1)));
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
                                   : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
   if (m.cap >= (1LL << 31)) return FSIM_EINVAL;
-  TRY(dalloc(ms, &m.pairs, m.cap));
-  TRY(dalloc(ms, &m.cand, m.cap));
-  TRY(dalloc(ms, &m.nearl, m.cap));
-  TRY(dalloc(ms, &m.pair_grad, 12 * (size_t)m.cap));
-  TRY(dalloc(ms, &m.pair_hess, 144 * (size_t)m.cap));
-  TRY(dalloc(ms, &m.x2mark, std::max(m.n2, 1)));
-  TRY(dalloc(ms, &m.clist, std::max(m.n2, 1)));
-  TRY(ensure_reduced(ctx, ms, std::min(std::max(m.n2, 1), 64)));
+  TRY(dalloc(ms, &ms.gtmp, 3 * (size_t)m.n));
+  TRY(dalloc(ms, &ms.dxtmp, 3 * (size_t)m.n));
+  ms.ws_bytes = 0;
+  TRY(alloc_workspace(ms, m, ms.allocs, &ms.ws_bytes));
+  CK(cudaMemcpyAsync(m.x, m.rest, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToDevice, s));
+  {
+    Exec ex = ctx_exec(ctx, ms);
+    TRY(ensure_reduced(ex, m, std::min(std::max(m.n2, 1), 64)));
+  }
   CK(cudaStreamSynchronize(s));
   ms.prefactored = true;
   return FSIM_OK;
@@ -584,6 +595,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
 fsim_status fsim_set_actuation(fsim_ctx_t ctx, int mesh_id, const double* fiber, const double* stretch) {
   MeshState* msp = get_mesh(ctx, mesh_id);
   if (!msp || !fiber || !stretch) return FSIM_EINVAL;
+  if (!msp->prefactored) return FSIM_ENOT_READY;
   const int T = msp->d.T;
   for (int t = 0; t < T; ++t) {
     const double a = stretch[t];
@@ -607,6 +619,7 @@ fsim_status fsim_set_actuation_dev(fsim_ctx_t ctx, int mesh_id, const double* fi
                                    const double* stretch_dev) {
   MeshState* msp = get_mesh(ctx, mesh_id);
   if (!msp || !fiber_dev || !stretch_dev) return FSIM_EINVAL;
+  if (!msp->prefactored) return FSIM_ENOT_READY;
   cudaSetDevice(ctx->device);
   launch_actuation(ctx->stream, msp->d.T, fiber_dev, stretch_dev, msp->d.act);
   CK(cudaGetLastError());
@@ -653,7 +666,10 @@ fsim_status fsim_solve_frame(fsim_ctx_t ctx, int mesh_id, const double* x_init, 
   TRY(ready(ms));
   if (precision != FSIM_FP64 && precision != FSIM_MIXED) return FSIM_EINVAL;
   cudaSetDevice(ctx->device);
-  return solve_frame_impl(ctx, *ms, x_init, false, precision, stats);
+  const Exec ex = ctx_exec(ctx, *ms);
+  const int rc = solve_frame_impl(ex, *ms, ms->d, x_init, false, precision, stats);
+  ms->has_x = true;
+  return rc;
 }
 
 fsim_status fsim_solve_frame_dev(fsim_ctx_t ctx, int mesh_id, const double* x_init_dev,
@@ -662,7 +678,10 @@ fsim_status fsim_solve_frame_dev(fsim_ctx_t ctx, int mesh_id, const double* x_in
   TRY(ready(ms));
   if (precision != FSIM_FP64 && precision != FSIM_MIXED) return FSIM_EINVAL;
   cudaSetDevice(ctx->device);
-  return solve_frame_impl(ctx, *ms, x_init_dev, true, precision, stats);
+  const Exec ex = ctx_exec(ctx, *ms);
+  const int rc = solve_frame_impl(ex, *ms, ms->d, x_init_dev, true, precision, stats);
+  ms->has_x = true;
+  return rc;
 }
 
 fsim_status fsim_read_positions(fsim_ctx_t ctx, int mesh_id, double* xyz_out) {
@@ -710,8 +729,9 @@ fsim_status fsim_read_contacts(fsim_ctx_t ctx, int mesh_id, int32_t* keys, int64
   if (!count || (cap > 0 && !keys)) return FSIM_EINVAL;
   cudaSetDevice(ctx->device);
   DevMesh& m = ms->d;
-  TRY(evaluate(ctx, *ms, m.x, m.st, m.tetf_t, nullptr, 0));
-  TRY(sync_read(ctx, m));
+  const Exec ex = ctx_exec(ctx, *ms);
+  TRY(evaluate(ex, *ms, m, m.x, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   return copy_keys(ctx, *ms, ctx->h_counters[0], keys, cap, count);
 }
@@ -736,7 +756,7 @@ fsim_status fsim_eval_elastic(fsim_ctx_t ctx, int mesh_id, const double* x, int 
   launch_elastic(s, m, m.xt, m.tetf_t, proj_out ? ms->proj : nullptr, m.partials, precision);
   launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
   launch_gather_forces(s, m, m.tetf_t, ms->gtmp);
-  TRY(sync_read(ctx, m));
+  TRY(sync_read(ctx_exec(ctx, *ms), m));
   if (energy_out) *energy_out = ctx->h_scal[2];
   if (grad_out)
     CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
@@ -748,6 +768,7 @@ fsim_status fsim_eval_elastic(fsim_ctx_t ctx, int mesh_id, const double* x, int 
 fsim_status fsim_eval_proxy(fsim_ctx_t ctx, int mesh_id, const double* x, double* s_out) {
   MeshState* ms = get_mesh(ctx, mesh_id);
   if (!ms || !x || !s_out) return FSIM_EINVAL;
+  if (!ms->prefactored) return FSIM_ENOT_READY;
   cudaSetDevice(ctx->device);
   DevMesh& m = ms->d;
   TRY(stage_x(ctx, *ms, x));
@@ -765,8 +786,9 @@ fsim_status fsim_eval_contacts(fsim_ctx_t ctx, int mesh_id, const double* x, int
   cudaSetDevice(ctx->device);
   DevMesh& m = ms->d;
   TRY(stage_x(ctx, *ms, x));
-  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, 0));
-  TRY(sync_read(ctx, m));
+  const Exec ex = ctx_exec(ctx, *ms);
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   if (barrier_energy_out) *barrier_energy_out = ctx->h_scal[0];
   return copy_keys(ctx, *ms, ctx->h_counters[0], keys, cap, count);
@@ -781,15 +803,16 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
   DevMesh& m = ms->d;
   cudaStream_t s = ctx->stream;
   TRY(stage_x(ctx, *ms, x));
-  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, 0));
-  TRY(sync_read(ctx, m));
+  const Exec ex = ctx_exec(ctx, *ms);
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const int64_t np = ctx->h_counters[0];
   // barrier gradient only: zero elastic forces by gathering a zero tetf
   CK(cudaMemsetAsync(m.tetf_t, 0, sizeof(double) * 12 * (size_t)m.T, s));
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
   if (n_c) *n_c = nc;
   if (grad_out)
     CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
@@ -811,17 +834,17 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   DevMesh& m = ms->d;
   cudaStream_t s = ctx->stream;
   TRY(stage_x(ctx, *ms, x));
-  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, precision));
-  TRY(sync_read(ctx, m));
+  const Exec ex = ctx_exec(ctx, *ms);
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
   CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-  global_step(s, m, ms->gtmp, ms->dxtmp, nc, precision, m.counters + 6, ctx->num_sms);
-  CK(cudaGetLastError());
-  TRY(sync_read(ctx, m));
+  CK(global_step(s, m, ms->gtmp, ms->dxtmp, nc, precision, m.counters + 6, ex.coop_ctas));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
   CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
   return FSIM_OK;
@@ -844,7 +867,7 @@ fsim_status fsim_eval_ccd(fsim_ctx_t ctx, int mesh_id, const double* x, const do
   const double one = 1.0;
   CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
   launch_ccd(s, m, m.st, m.ds, ms->p.dhat, ms->p.ccd_s, ms->p.accd_max_iters);
-  TRY(sync_read(ctx, m));
+  TRY(sync_read(ctx_exec(ctx, *ms), m));
   if (ctx->h_counters[9]) return FSIM_ECONTACT_OVERFLOW;
   *alpha_out = ctx->h_scal[1];
   return FSIM_OK;
@@ -858,14 +881,15 @@ fsim_status fsim_eval_energy(fsim_ctx_t ctx, int mesh_id, const double* x, int p
   cudaSetDevice(ctx->device);
   DevMesh& m = ms->d;
   TRY(stage_x(ctx, *ms, x));
-  TRY(evaluate(ctx, *ms, m.xt, m.st, m.tetf_t, nullptr, precision));
-  TRY(sync_read(ctx, m));
+  const Exec ex = ctx_exec(ctx, *ms);
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const double E = ctx->h_scal[2] + ctx->h_scal[0];
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ctx, *ms, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
   if (energy_out) *energy_out = E;
   if (grad_norm_out) *grad_norm_out = std::sqrt(gn2);
   return FSIM_OK;
@@ -880,6 +904,7 @@ fsim_status fsim_mesh_info_get(fsim_ctx_t ctx, int mesh_id, fsim_mesh_info* info
   info->factor_nnz = ms->factor_nnz;
   info->n_supernodes = m.n_sn;
   info->n_levels = m.n_levels;
+  info->workspace_bytes = (int64_t)rt_slot_bytes(*ms);
   info->kappa = ms->kappa;
   return FSIM_OK;
 }

@@ -6,7 +6,9 @@
 // contribution w D gradN_a of each of its four vertices (the row form of
 // w_i G_i^T (G_i x - p_i)).  Forces are written per tet and gathered per
 // vertex in a fixed order (deterministic sums, no atomics).
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -15,7 +17,9 @@
 namespace fsim {
 
 namespace {
-std::int64_t g_launches = 0;
+std::atomic<std::int64_t> g_launches{0};
+// ProfScope may be used from several host threads (server workers)
+std::mutex g_prof_mu;
 
 // event-pair pool for ProfScope; resolved (summed per class) in prof_read
 struct Prof {
@@ -41,10 +45,11 @@ void prof_resolve() {
 }
 }  // namespace
 
-int64_t launch_counter() { return g_launches; }
+int64_t launch_counter() { return g_launches.load(); }
 void count_launch(int k) { g_launches += k; }
 
 ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!(g_prof.mask & (1u << c))) return;
   if (g_prof.pending.size() >= 4096) prof_resolve();
   if (g_prof.free_slots.empty()) {
@@ -62,14 +67,19 @@ ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
 
 ProfScope::~ProfScope() {
   if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEventRecord(g_prof.ev1[slot], stream);
   g_prof.pending.push_back(slot);
 }
 
-void prof_set_mask(unsigned mask) { g_prof.mask = mask; }
+void prof_set_mask(unsigned mask) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.mask = mask;
+}
 
 int prof_read(int c, int64_t* launches, double* total_ms) {
   if (c < 0 || c >= PROF_NCLASS) return -1;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_resolve();
   *launches = g_prof.launches[c];
   *total_ms = g_prof.ms[c];
@@ -77,6 +87,7 @@ int prof_read(int c, int64_t* launches, double* total_ms) {
 }
 
 void prof_reset() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_resolve();
   for (int c = 0; c < PROF_NCLASS; ++c) { g_prof.launches[c] = 0; g_prof.ms[c] = 0.0; }
 }

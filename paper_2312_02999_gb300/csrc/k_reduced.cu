@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
 }
 
 template <typename FT>
-void launch_reduced_t(cudaStream_t s, const DevMesh& m, int nc, const double* u, const FT* y2,
+cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, int nc, const double* u, const FT* y2,
                       double* z2, int* info, int num_sms, int refine) {
   const int64_t n3 = 3 * (int64_t)nc;
   FT* base = std::is_same<FT, double>::value ? (FT*)m.red : (FT*)m.redf;
@@ -421,8 +421,9 @@ void launch_reduced_t(cudaStream_t s, const DevMesh& m, int nc, const double* u,
   void* args[] = {&a};
   const int grid = std::max(1, num_sms);
   ProfScope ps(PROF_CHOL, s);
-  cudaLaunchCooperativeKernel((void*)k_reduced<FT>, dim3(grid), dim3(kRT), args, 0, s);
+  const cudaError_t e = cudaLaunchCooperativeKernel((void*)k_reduced<FT>, dim3(grid), dim3(kRT), args, 0, s);
   count_launch();
+  return e;
 }
 
 }  // namespace
@@ -434,12 +435,11 @@ int64_t reduced_workspace_elems(int nc) {
   return (int64_t)nc * nc + n3 * n3 + (n3 + 1) * n3 + nc + n3 + 2 * n3 + 4 * n3 + 64;
 }
 
-void reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
-                   double* z2, int* info, int num_sms, int precision) {
+cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
+                          double* z2, int* info, int num_sms, int precision) {
   if (precision == 0)
-    launch_reduced_t<double>(s, m, nc, u, (const double*)y2, z2, info, num_sms, 0);
-  else
-    launch_reduced_t<float>(s, m, nc, u, (const float*)y2, z2, info, num_sms, 4);
+    return launch_reduced_t<double>(s, m, nc, u, (const double*)y2, z2, info, num_sms, 0);
+  return launch_reduced_t<float>(s, m, nc, u, (const float*)y2, z2, info, num_sms, 4);
 }
 
 }  // namespace fsim

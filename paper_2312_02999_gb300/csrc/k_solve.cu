@@ -242,8 +242,8 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
 //   diagonal: dx2 = Sigma-hat^-1 y2 = u - Sigma^-1 Q^T v,  u = Sigma^-1 y2
 //   upper:    dx1 = L1^-T (z1 - L21^T dx2)             (one backward pass)
 template <typename T>
-void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc, int* info,
-                   int num_sms) {
+cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
+                          int* info, int num_sms) {
   const int nf = m.nf, n1 = m.n1, n2 = m.n2;
   const bool f64 = std::is_same<T, double>::value;
   double* r = m.r;                                  // float64 work (nf * 3)
@@ -273,7 +273,8 @@ void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx
       // The reduced system carries the barrier stiffness (cond ~ kappa b''):
       // float64 factors, or float32 factors refined with float64 residuals.
       ProfScope psr(PROF_REDUCED, s);
-      reduced_solve(s, m, nc, u, y2, z2, info, num_sms, f64 ? 0 : 1);
+      const cudaError_t e = reduced_solve(s, m, nc, u, y2, z2, info, num_sms, f64 ? 0 : 1);
+      if (e != cudaSuccess) return e;
     } else {
       cudaMemcpyAsync(z2, u, sizeof(double) * 3 * (size_t)n2, cudaMemcpyDeviceToDevice, s);
     }
@@ -290,6 +291,7 @@ void global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx
   cudaMemsetAsync(dx, 0, sizeof(double) * 3 * (size_t)m.n, s);
   k_scatter_dx<<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, r, dx);
   count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -301,10 +303,10 @@ void set_solver_smem_limits(int max_bytes) {
   cudaFuncSetAttribute(k_bwd_chunk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }
 
-void global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
-                 int precision, int* info_dev, int num_sms) {
-  if (precision == 0) global_step_t<double>(s, m, g, dx, nc, info_dev, num_sms);
-  else global_step_t<float>(s, m, g, dx, nc, info_dev, num_sms);
+cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
+                        int precision, int* info_dev, int num_sms) {
+  if (precision == 0) return global_step_t<double>(s, m, g, dx, nc, info_dev, num_sms);
+  return global_step_t<float>(s, m, g, dx, nc, info_dev, num_sms);
 }
 
 }  // namespace fsim

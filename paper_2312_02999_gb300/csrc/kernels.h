@@ -61,14 +61,10 @@ struct DevMesh {
   int* h_bwd_ptr = nullptr;   // HOST (n_levels + 1)
   double* y1 = nullptr;       // n1*3 forward-solve scratch
   float* y1f = nullptr;
-  // couplings
-  int* k12_ptr = nullptr; int* k12_col = nullptr; double* k12_val = nullptr;
-  int* k21_ptr = nullptr; int* k21_col = nullptr; double* k21_val = nullptr;
-  double* Sinv = nullptr;     // n2 x n2
+  double* Sinv = nullptr;     // n2 x n2 Schur-complement inverse (Sec. 3.2)
   float* Sinvf = nullptr;
   // global-step work (solver positions, AoS 3)
   double* r = nullptr;        // nf*3
-  double* t1 = nullptr;       // n1*3
   double* u = nullptr;        // n2*3
   float* uf = nullptr;        // n2*3 (mixed)
   float* rf = nullptr;        // nf*3 (mixed)
@@ -122,15 +118,16 @@ void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, in
 
 // ---- global step (k_solve.cu) ----------------------------------------------
 // dx (by vertex) solving (H + B) dx = -g, with B-check already assembled for nc.
-void global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
-                 int precision, int* info_dev, int num_sms);
+// num_sms is the CTA count of the cooperative reduced-system launch.
+cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
+                        int precision, int* info_dev, int num_sms);
 int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
 // z2 = u - Sigma^-1 Q^T v with the push-through reduced system (k_reduced.cu);
 // precision 0: float64 factors, 1: float32 factors + float64 refinement.
 // y2 (double for precision 0, float for 1) is the Schur right-hand side with
 // u = Sigma^-1 y2; it scales the refinement's stopping test.
-void reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
-                   double* z2, int* info, int num_sms, int precision);
+cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
+                          double* z2, int* info, int num_sms, int precision);
 void set_solver_smem_limits(int max_bytes);
 
 // ---- misc ------------------------------------------------------------------

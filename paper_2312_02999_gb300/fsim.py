@@ -43,14 +43,14 @@ class Params(C.Structure):
     _fields_ = [("weight_scale", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
-                ("reserved0", C.c_int32), ("contact_capacity", C.c_int64)]
+                ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64)]
 
 
 class FrameStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("ls_trials", C.c_int32),
                 ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("reserved0", C.c_int32),
                 ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
-                ("energy", C.c_double), ("alpha_min", C.c_double)]
+                ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -58,8 +58,32 @@ class FrameStats(C.Structure):
 
 class MeshInfo(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("n", "T", "Ns", "Nt", "Ne", "n_free", "n1", "n2",
-                                         "factor_nnz", "n_supernodes", "n_levels")] + \
+                                         "factor_nnz", "n_supernodes", "n_levels",
+                                         "workspace_bytes")] + \
                [("kappa", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FSIM_REQ_DEVICE = 1
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh_id", C.c_int32), ("precision", C.c_int32),
+                ("fiber", C.POINTER(C.c_double)), ("stretch", C.POINTER(C.c_double)),
+                ("x_init", C.POINTER(C.c_double)), ("flags", C.c_int32), ("reserved0", C.c_int32),
+                ("x_out_dev", C.POINTER(C.c_double))]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("reserved0", C.c_int32), ("mem_budget_bytes", C.c_int64)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("slots", C.c_int32), ("peak_slots", C.c_int32),
+                ("peak_running", C.c_int32), ("queued", C.c_int64), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +124,14 @@ _SIGS = {
     "fsim_profile_reset": [_P],
     "fsim_ccd_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                          C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_void_p, C.c_void_p],
+    "fsim_server_create": [_P, C.POINTER(ServerConfig), C.POINTER(_P)],
+    "fsim_server_submit": [_P, C.POINTER(Request), _I64],
+    "fsim_server_poll": [_P, C.c_int64, _I32],
+    "fsim_server_wait": [_P, C.c_int64, _D, C.POINTER(FrameStats), _D, _D],
+    "fsim_server_info_get": [_P, C.POINTER(ServerInfo)],
+    "fsim_server_destroy": [_P],
+    "fsim_solve_frames": [_P, C.c_int32, C.POINTER(Request), C.c_int32, C.POINTER(_D),
+                          C.POINTER(FrameStats)],
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
@@ -345,3 +377,101 @@ def params_for(mesh, **kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+class Server:
+    """Continuous-batching request server (fsim_server_*): `workers` frame
+    solves run at once, each on its own CUDA stream and workspace slot."""
+
+    def __init__(self, ctx: "Context", workers: int = 4, mem_budget_bytes: int = 0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        cfg = ServerConfig(int(workers), 0, int(mem_budget_bytes))
+        h = _P()
+        _chk(self.lib.fsim_server_create(ctx.h, C.byref(cfg), C.byref(h)), "fsim_server_create")
+        self.h = h
+        self._n = {}
+
+    def submit(self, mesh: "Mesh", fiber, stretch, x_init=None, precision: int = 1) -> int:
+        fiber = np.ascontiguousarray(fiber, dtype=np.float64)
+        stretch = np.ascontiguousarray(stretch, dtype=np.float64)
+        if fiber.size != 3 * mesh.T or stretch.size != mesh.T:
+            raise ValueError("actuation arrays do not match the mesh")
+        xi = None
+        if x_init is not None:
+            xi = np.ascontiguousarray(x_init, dtype=np.float64)
+            if xi.size != 3 * mesh.n:
+                raise ValueError("x_init does not match the mesh")
+        req = Request(mesh.id, int(precision), _d(fiber), _d(stretch), _d(xi), 0, 0, None)
+        t = C.c_int64()
+        _chk(self.lib.fsim_server_submit(self.h, C.byref(req), C.byref(t)), "fsim_server_submit")
+        self._n[int(t.value)] = mesh.n
+        return int(t.value)
+
+    def submit_dev(self, mesh: "Mesh", fiber_ptr: int, stretch_ptr: int, x_init_ptr: int = 0,
+                   x_out_ptr: int = 0, precision: int = 1) -> int:
+        """Request whose inputs (and output) are device arrays (FSIM_REQ_DEVICE);
+        they must stay valid until the request completes."""
+        dp = lambda p: C.cast(C.c_void_p(p), _D) if p else None
+        req = Request(mesh.id, int(precision), dp(fiber_ptr), dp(stretch_ptr), dp(x_init_ptr),
+                      FSIM_REQ_DEVICE, 0, dp(x_out_ptr))
+        t = C.c_int64()
+        _chk(self.lib.fsim_server_submit(self.h, C.byref(req), C.byref(t)), "fsim_server_submit")
+        self._n[int(t.value)] = 0
+        return int(t.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32()
+        _chk(self.lib.fsim_server_poll(self.h, int(ticket), C.byref(d)), "fsim_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int):
+        """(status, positions (n, 3), stats dict, latency ms, queue ms)"""
+        n = self._n.pop(int(ticket))
+        x = np.empty((n, 3), dtype=np.float64) if n else None
+        st = FrameStats()
+        lat, q = C.c_double(), C.c_double()
+        rc = self.lib.fsim_server_wait(self.h, int(ticket), _d(x), C.byref(st), C.byref(lat),
+                                       C.byref(q))
+        return int(rc), x, st.as_dict(), float(lat.value), float(q.value)
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        _chk(self.lib.fsim_server_info_get(self.h, C.byref(i)), "fsim_server_info_get")
+        return i.as_dict()
+
+    def close(self):
+        if self.h:
+            self.lib.fsim_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_frames(ctx: "Context", requests, workers: int = 4):
+    """Batched form (fsim_solve_frames): requests are (mesh, fiber, stretch,
+    x_init or None, precision) tuples; returns (status, [positions], [stats])."""
+    n = len(requests)
+    keep, reqs = [], (Request * max(n, 1))()
+    outs = []
+    for i, (mesh, fiber, stretch, x_init, prec) in enumerate(requests):
+        f = np.ascontiguousarray(fiber, dtype=np.float64)
+        a = np.ascontiguousarray(stretch, dtype=np.float64)
+        xi = None if x_init is None else np.ascontiguousarray(x_init, dtype=np.float64)
+        keep += [f, a, xi]
+        reqs[i] = Request(mesh.id, int(prec), _d(f), _d(a), _d(xi), 0, 0, None)
+        outs.append(np.empty((mesh.n, 3), dtype=np.float64))
+    ptrs = (_D * max(n, 1))(*[_d(o) for o in outs])
+    stats = (FrameStats * max(n, 1))()
+    rc = ctx.lib.fsim_solve_frames(ctx.h, n, reqs, int(workers), ptrs, stats)
+    return int(rc), outs, [stats[i].as_dict() for i in range(n)]
