@@ -69,7 +69,10 @@ void free_list(std::vector<void*>& allocs) {
   allocs.clear();
 }
 
+void destroy_graphs(DevMesh& m);
+
 void free_mesh(MeshState& ms) {
+  destroy_graphs(ms.d);
   free_list(ms.allocs);
   delete[] ms.d.h_level_ptr;
   delete[] ms.d.h_level_maxns;
@@ -123,6 +126,7 @@ int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
   TRY(dalloc(*ex.allocs, &m.red, (size_t)m.red_cap, ex.bytes));
   TRY(dalloc(*ex.allocs, &m.redf, (size_t)m.red_cap, ex.bytes));
   m.nc_cap = cap;
+  m.red_gen++;
   return FSIM_OK;
 }
 
@@ -130,6 +134,9 @@ int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
 // constant mesh data (factor, Sigma^-1, topology) stays shared.  Used for
 // the mesh's own workspace at prefactor and for the server's extra slots.
 int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, size_t* bytes) {
+  // a copy must never replay (or destroy) another workspace's graphs
+  for (auto& g : m.graphs) g = DevMesh::Graph{};
+  m.red_gen = 0;
   const size_t n = m.n, T = m.T, Ns = m.Ns;
   const size_t np = (size_t)m.Ns + m.Nt + m.Ne;
   TRY(dalloc(al, &m.x, 3 * n, bytes));
@@ -166,6 +173,78 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   m.red_cap = 0; m.nc_cap = 0;
   (void)ms;
   return FSIM_OK;
+}
+
+void destroy_graphs(DevMesh& m) {
+  for (auto& g : m.graphs) {
+    if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+    g = DevMesh::Graph{};
+  }
+}
+
+// Run a fixed launch sequence through a CUDA graph captured on first use
+// (one host launch instead of one per kernel).  The graph is recaptured
+// when its key buffer, precision, reduced-buffer generation or cooperative
+// CTA count changes; with the event profiler on, or where capture is not
+// supported, the sequence is launched directly.
+template <typename F>
+int with_graph(const Exec& ex, DevMesh& m, int slot, const void* key, int key2, int gen, F&& body) {
+  DevMesh::Graph& g = m.graphs[slot];
+  if (g.failed || prof_active()) return body();
+  if (g.exec && (g.key != key || g.key2 != key2 || g.gen != gen || g.coop != ex.coop_ctas ||
+                 g.alone != ex.alone)) {
+    cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+    g.exec = nullptr;
+  }
+  if (!g.exec) {
+    if (cudaStreamBeginCapture(ex.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g.failed = true;
+      return body();
+    }
+    set_capturing(true);
+    const int rc = body();
+    set_capturing(false);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ex.stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == FSIM_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    int64_t kernels = 0;
+    if (graph) {
+      size_t nn = 0;
+      cudaGraphGetNodes(graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+      cudaGraphDestroy(graph);
+    }
+    if (rc != FSIM_OK || e != cudaSuccess || !exec) {
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      g.failed = true;
+      return body();      // nothing ran during the capture: launch directly
+    }
+    g.exec = exec; g.key = key; g.key2 = key2; g.gen = gen; g.coop = ex.coop_ctas; g.alone = ex.alone;
+    g.kernels = kernels;
+  }
+  CK(cudaGraphLaunch((cudaGraphExec_t)g.exec, ex.stream));
+  count_launch((int)g.kernels);
+  return FSIM_OK;
+}
+
+// graph slots: 0-1 global step (by precision), 2-5 evaluation (by position
+// buffer and precision), 6-7 CCD (by proxy-position buffer)
+int graph_slot(const DevMesh& m, int first, int count, const void* key, int key2) {
+  for (int k = first; k < first + count; ++k)
+    if (m.graphs[k].exec && m.graphs[k].key == key && m.graphs[k].key2 == key2) return k;
+  for (int k = first; k < first + count; ++k)
+    if (!m.graphs[k].exec && !m.graphs[k].failed) return k;
+  for (int k = first; k < first + count; ++k)
+    if (!m.graphs[k].failed) return k;
+  return first;
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +309,12 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
   launch_reset_pinned(s, m, m.x);
   CK(cudaMemsetAsync(m.counters + 4, 0, sizeof(int), s));
   launch_check_finite(s, 3 * m.n, m.x, m.counters + 4);
-  TRY(evaluate(ex, ms, m, m.x, m.s, m.tetf, nullptr, prec));
+  auto eval_at = [&](double* xb, double* sb, double* tetf) -> int {
+    const int slot = graph_slot(m, 2, 4, xb, prec);
+    return with_graph(ex, m, slot, xb, prec, 0,
+                      [&] { return evaluate(ex, ms, m, xb, sb, tetf, nullptr, prec); });
+  };
+  TRY(eval_at(m.x, m.s, m.tetf));
   TRY(sync_read(ex, m));
   int rc = FSIM_OK;
   if (ex.h_counters[4]) rc = FSIM_ENONFINITE;
@@ -254,24 +338,28 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     if (gn <= tol) break;
     if (st.iterations >= p.max_iters) { rc = FSIM_ENOT_CONVERGED; break; }
     // global step (Eq. 4 via Eq. 8-11)
-    CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-    CK(global_step(s, m, m.g, m.dx, nc, prec, m.counters + 6, ex.coop_ctas));
+    TRY(with_graph(ex, m, prec, m.g, prec, m.red_gen, [&]() -> int {
+      CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
+      CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone));
+      return FSIM_OK;
+    }));
     st.sum_nc3 += (double)nc * nc * nc;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
-    launch_proxy(s, m, m.dx, m.ds);
-    CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int), s));
-    CK(cudaMemsetAsync(m.counters + 9, 0, sizeof(int), s));
-    const double one = 1.0;
-    CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
+    TRY(with_graph(ex, m, graph_slot(m, 6, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
+      launch_proxy(s, m, m.dx, m.ds);
+      launch_ccd_reset(s, m);
+      launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
+      CK(cudaGetLastError());
+      return FSIM_OK;
+    }));
     // backtracking line search from alpha_m on E-hat = E + B
     bool accepted = false;
     double scale = 1.0, Et = 0.0;
     int64_t np_t = 0;
     for (int k = 0; k <= p.max_ls; ++k) {
       launch_axpy_positions(s, 3 * m.n, m.x, m.dx, m.scal + 1, scale, m.xt);
-      TRY(evaluate(ex, ms, m, m.xt, m.st, m.tetf_t, nullptr, prec));
+      TRY(eval_at(m.xt, m.st, m.tetf_t));
       TRY(sync_read(ex, m));
       if (k == 0 && ex.h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
       if (k == 0 && ex.h_counters[9]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
@@ -318,6 +406,7 @@ int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double
   return solve_frame_impl(ex, ms, m, x_init, init_is_dev, precision, stats);
 }
 void rt_free_list(std::vector<void*>& allocs) { free_list(allocs); }
+void rt_destroy_graphs(DevMesh& m) { destroy_graphs(m); }
 size_t rt_slot_bytes(const MeshState& ms) {
   if (!ms.prefactored) return 0;
   const int64_t cap = std::min(std::max(ms.d.n2, 1), 64);
@@ -547,7 +636,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   m.h_level_maxld = new int[std::max(f.n_levels, 1)];
   m.h_fwd_ptr = new int[f.n_levels + 1];
   m.h_bwd_ptr = new int[f.n_levels + 1];
-  // work items: forward = 32-row chunks of Z_J, backward = 16-column chunks
+  // work items: forward = 32-row chunks of Z_J, backward = 8-column chunks
   std::vector<int4> fwd, bwd;
   m.h_fwd_ptr[0] = 0;
   m.h_bwd_ptr[0] = 0;
@@ -560,7 +649,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
       mx = std::max(mx, ns[J]);
       mxld = std::max(mxld, ldj);
       for (int r0 = 0; r0 < ldj; r0 += 32) fwd.push_back(make_int4(J, r0, std::min(32, ldj - r0), 0));
-      for (int k0 = 0; k0 < ns[J]; k0 += 16) bwd.push_back(make_int4(J, k0, std::min(16, ns[J] - k0), 0));
+      for (int k0 = 0; k0 < ns[J]; k0 += 8) bwd.push_back(make_int4(J, k0, std::min(8, ns[J] - k0), 0));
     }
     m.h_level_maxns[l] = mx;
     m.h_level_maxld[l] = mxld;
@@ -843,7 +932,7 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   double gn2 = 0.0;
   TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
   CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-  CK(global_step(s, m, ms->gtmp, ms->dxtmp, nc, precision, m.counters + 6, ex.coop_ctas));
+  CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
   CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
@@ -862,10 +951,7 @@ fsim_status fsim_eval_ccd(fsim_ctx_t ctx, int mesh_id, const double* x, const do
   CK(cudaMemcpyAsync(ms->dxtmp, dx, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyHostToDevice, s));
   launch_proxy(s, m, m.xt, m.st);
   launch_proxy(s, m, ms->dxtmp, m.ds);
-  CK(cudaMemsetAsync(m.counters + 1, 0, sizeof(int), s));
-  CK(cudaMemsetAsync(m.counters + 9, 0, sizeof(int), s));
-  const double one = 1.0;
-  CK(cudaMemcpyAsync(m.scal + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_ccd_reset(s, m);
   launch_ccd(s, m, m.st, m.ds, ms->p.dhat, ms->p.ccd_s, ms->p.accd_max_iters);
   TRY(sync_read(ctx_exec(ctx, *ms), m));
   if (ctx->h_counters[9]) return FSIM_ECONTACT_OVERFLOW;

@@ -843,6 +843,17 @@ void launch_mark_scan(cudaStream_t st, const DevMesh& m) {
   count_launch();
 }
 
+__global__ void k_ccd_reset(int* counters, double* scal) {
+  counters[1] = 0;
+  counters[9] = 0;
+  scal[1] = 1.0;
+}
+
+void launch_ccd_reset(cudaStream_t st, const DevMesh& m) {
+  k_ccd_reset<<<1, 1, 0, st>>>(m.counters, m.scal);
+  count_launch();
+}
+
 void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int nc, double* g) {
   np = np < m.cap ? np : m.cap;
   if (np <= 0) return;

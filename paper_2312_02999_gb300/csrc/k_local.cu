@@ -45,8 +45,12 @@ void prof_resolve() {
 }
 }  // namespace
 
+thread_local bool tl_capturing = false;
 int64_t launch_counter() { return g_launches.load(); }
-void count_launch(int k) { g_launches += k; }
+void count_launch(int k) {
+  if (!tl_capturing) g_launches += k;
+}
+void set_capturing(bool on) { tl_capturing = on; }
 
 ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -75,6 +79,11 @@ ProfScope::~ProfScope() {
 void prof_set_mask(unsigned mask) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof.mask = mask;
+}
+
+bool prof_active() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof.mask != 0;
 }
 
 int prof_read(int c, int64_t* launches, double* total_ms) {

@@ -39,6 +39,10 @@ constexpr int kRT = 256;   // threads per CTA
 template <typename FT>
 struct RedArgs {
   int nc, n2, refine;
+  const int* nc_dev;    // n_c on the device (set by the contact-marking scan)
+  FT* base;             // FT workspace: S, X, N, 1/diag, FT vectors (offsets from n_c)
+  double* dtail_end;    // end of the float64 workspace; float64 vectors sit before it
+  int* ibase;           // int workspace after the block occupancy: lists, counts
   const int* clist;
   const double* Sinv;   // n2 x n2
   const double* Bc;     // (3nc)^2, row-major
@@ -245,10 +249,27 @@ template <typename FT>
 __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
   cg::grid_group grid = cg::this_grid();
   __shared__ Smem<FT> sm;
-  const int nc = a.nc, n3 = 3 * nc;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int gtid = blockIdx.x * kRT + tid, gsz = gridDim.x * kRT;
   const int gwarp = blockIdx.x * (kRT / 32) + wid, nwarps = gridDim.x * (kRT / 32);
+  // n_c is read on the device, so the launch (and a captured graph) does not
+  // depend on it; every thread reads the same value
+  const int nc = *a.nc_dev, n3 = 3 * nc;
+  if (nc == 0) {          // no contact: Sigma-hat = Sigma, z2 = u
+    for (int e = gtid; e < 3 * a.n2; e += gsz) a.z2[e] = a.u[e];
+    return;
+  }
+  a.nc = nc;
+  a.S = a.base;
+  a.X = a.S + (size_t)nc * nc;
+  a.N = a.X + (size_t)n3 * n3;
+  a.dinv_s = a.N + (size_t)(n3 + 1) * n3;
+  a.dinv_n = a.dinv_s + nc;
+  a.fv = a.dinv_n + n3;
+  a.y = a.dtail_end - 4 * (size_t)n3 - 8;
+  a.v = a.y + n3; a.rho = a.v + n3; a.w = a.rho + n3; a.nrm = a.w + n3;
+  a.list = a.ibase;
+  a.cnt = a.list + (size_t)nc * nc;
 
   // 1. S, block lists, y = B u_c
   if (gtid == 0) a.nrm[2] = 0.0;
@@ -399,24 +420,16 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
 }
 
 template <typename FT>
-cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, int nc, const double* u, const FT* y2,
-                      double* z2, int* info, int num_sms, int refine) {
-  const int64_t n3 = 3 * (int64_t)nc;
-  FT* base = std::is_same<FT, double>::value ? (FT*)m.red : (FT*)m.redf;
-  RedArgs<FT> a;
-  a.nc = nc; a.n2 = m.n2; a.refine = refine;
+cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, const FT* y2,
+                             double* z2, int* info, int num_sms, int refine) {
+  RedArgs<FT> a{};
+  a.n2 = m.n2; a.refine = refine;
+  a.nc_dev = m.counters + 3;
+  a.base = std::is_same<FT, double>::value ? (FT*)m.red : (FT*)m.redf;
+  a.dtail_end = m.red + m.red_cap;      // float64 vectors at the tail of m.red
+  a.ibase = m.bocc + (size_t)m.nc_cap * m.nc_cap;
   a.clist = m.clist; a.Sinv = m.Sinv; a.Bc = m.Bc; a.bocc = m.bocc;
-  a.list = m.bocc + (size_t)nc * nc;
-  a.cnt = a.list + (size_t)nc * nc;
   a.u = u; a.y2 = y2; a.z2 = z2;
-  a.S = base;
-  a.X = a.S + (size_t)nc * nc;
-  a.N = a.X + (size_t)n3 * n3;
-  a.dinv_s = a.N + (size_t)(n3 + 1) * n3;
-  a.dinv_n = a.dinv_s + nc;
-  a.fv = a.dinv_n + n3;
-  double* dtail = m.red + m.red_cap - 4 * n3 - 8;     // float64 vectors at the tail of m.red
-  a.y = dtail; a.v = a.y + n3; a.rho = a.v + n3; a.w = a.rho + n3; a.nrm = a.w + n3;
   a.info = info;
   void* args[] = {&a};
   const int grid = std::max(1, num_sms);
@@ -435,11 +448,11 @@ int64_t reduced_workspace_elems(int nc) {
   return (int64_t)nc * nc + n3 * n3 + (n3 + 1) * n3 + nc + n3 + 2 * n3 + 4 * n3 + 64;
 }
 
-cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
+cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
                           double* z2, int* info, int num_sms, int precision) {
   if (precision == 0)
-    return launch_reduced_t<double>(s, m, nc, u, (const double*)y2, z2, info, num_sms, 0);
-  return launch_reduced_t<float>(s, m, nc, u, (const float*)y2, z2, info, num_sms, 4);
+    return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0);
+  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4);
 }
 
 }  // namespace fsim

@@ -64,18 +64,27 @@ __global__ void k_convert(int n, const S* __restrict__ a, T* __restrict__ b) {
 // supernodal triangular solves with Z_J = [L_JJ^-1 ; L_RJ L_JJ^-1]
 // ---------------------------------------------------------------------------
 // Chunked forms: a level is a list of work items (J, first row/column, count)
-// so that one large supernode spreads over many CTAs.  Forward item: rows
-// [r0, r0+32) of Z_J times b_J; lanes own rows (coalesced column-major reads),
-// the 8 warps split the inner index and reduce through shared memory.
-template <typename T>
-__global__ void __launch_bounds__(256)
+// so that one large supernode spreads over many CTAs.  A level's work is a
+// handful of dependent GEMV chunks, so the serial chain per lane sets its
+// time: a solve that has the GPU to itself uses 32 warps per item (NT =
+// 1024); solves that share the GPU with others, and the float64 form (bound
+// by the float64 pipe), use 8 warps per item (NT = 256) so that more items fit
+// on an SM.
+constexpr int kBwdCols = 8;                       // columns per backward item
+
+// Forward item: rows [r0, r0+32) of Z_J times b_J; lanes own rows (coalesced
+// column-major reads), the 32 warps split the inner index and reduce through
+// shared memory.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
 k_fwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
             const int* __restrict__ nra, const int64_t* __restrict__ roff,
             const int64_t* __restrict__ zoff, const int* __restrict__ rows,
             const T* __restrict__ Z, T* __restrict__ b, T* __restrict__ y) {
   extern __shared__ unsigned char smem_raw[];
+  constexpr int kSolveWarps = NT / 32;
   T* bj = reinterpret_cast<T*>(smem_raw);
-  __shared__ T part[8][32][3];
+  __shared__ T part[kSolveWarps][32][3];
   const int4 it = items[blockIdx.x];
   const int J = it.x, r0 = it.y, rn = it.z;
   const int c0 = c0a[J], ns = nsa[J], nr = nra[J], ld = ns + nr;
@@ -87,49 +96,49 @@ k_fwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const i
   T a0 = 0, a1 = 0, a2 = 0;
   if (lane < rn) {
     const int kmax = r < ns ? r + 1 : ns;
-    // four independent loads and accumulators in flight per lane: the loop is
-    // bound by load and FMA latency, not by bandwidth
-    T q0 = 0, q1 = 0, q2 = 0, d0 = 0, d1 = 0, d2 = 0, e0 = 0, e1 = 0, e2 = 0;
+    // two independent loads and accumulators in flight per lane
+    T q0 = 0, q1 = 0, q2 = 0;
     int k = wid;
-    for (; k + 24 < kmax; k += 32) {
-      const T z0 = Zj[(size_t)k * ld + r], z1 = Zj[(size_t)(k + 8) * ld + r];
-      const T z2 = Zj[(size_t)(k + 16) * ld + r], z3 = Zj[(size_t)(k + 24) * ld + r];
+    for (; k + kSolveWarps < kmax; k += 2 * kSolveWarps) {
+      const T z0 = Zj[(size_t)k * ld + r], z1 = Zj[(size_t)(k + kSolveWarps) * ld + r];
+      const int k1 = k + kSolveWarps;
       a0 += z0 * bj[3 * k]; a1 += z0 * bj[3 * k + 1]; a2 += z0 * bj[3 * k + 2];
-      q0 += z1 * bj[3 * k + 24]; q1 += z1 * bj[3 * k + 25]; q2 += z1 * bj[3 * k + 26];
-      d0 += z2 * bj[3 * k + 48]; d1 += z2 * bj[3 * k + 49]; d2 += z2 * bj[3 * k + 50];
-      e0 += z3 * bj[3 * k + 72]; e1 += z3 * bj[3 * k + 73]; e2 += z3 * bj[3 * k + 74];
+      q0 += z1 * bj[3 * k1]; q1 += z1 * bj[3 * k1 + 1]; q2 += z1 * bj[3 * k1 + 2];
     }
-    for (; k < kmax; k += 8) {
+    if (k < kmax) {
       const T z = Zj[(size_t)k * ld + r];
       a0 += z * bj[3 * k]; a1 += z * bj[3 * k + 1]; a2 += z * bj[3 * k + 2];
     }
-    a0 += (q0 + d0) + e0; a1 += (q1 + d1) + e1; a2 += (q2 + d2) + e2;
+    a0 += q0; a1 += q1; a2 += q2;
   }
   part[wid][lane][0] = a0; part[wid][lane][1] = a1; part[wid][lane][2] = a2;
   __syncthreads();
-  if (wid == 0 && lane < rn) {
-#pragma unroll
-    for (int w = 1; w < 8; ++w) { a0 += part[w][lane][0]; a1 += part[w][lane][1]; a2 += part[w][lane][2]; }
-    if (r < ns) {
-      T* o = y + 3 * (size_t)(c0 + r);
-      o[0] = a0; o[1] = a1; o[2] = a2;
-    } else {
-      T* o = b + 3 * (size_t)rows[roff[J] + r - ns];
-      atomicAdd(o, -a0); atomicAdd(o + 1, -a1); atomicAdd(o + 2, -a2);
+  if (threadIdx.x < 96) {
+    const int rl = threadIdx.x / 3, d = threadIdx.x % 3;
+    if (rl < rn) {
+      T acc = 0;
+#pragma unroll 8
+      for (int w = 0; w < kSolveWarps; ++w) acc += part[w][rl][d];
+      const int rr = r0 + rl;
+      if (rr < ns) y[3 * (size_t)(c0 + rr) + d] = acc;
+      else atomicAdd(b + 3 * (size_t)rows[roff[J] + rr - ns] + d, -acc);
     }
   }
 }
 
-// Backward item: columns [k0, k0+kn) of Z_J^T [y_J ; -x_R]; one warp per column.
-// Reads y (forward result) and the ancestors' x, writes x_J (x may alias b).
-template <typename T>
-__global__ void __launch_bounds__(256)
+// Backward item: columns [k0, k0+kn) (kn <= 8) of Z_J^T [y_J ; -x_R]; NT/256
+// warps per column split its rows.  Reads y (forward result) and the
+// ancestors' x, writes x_J (x may alias b).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
 k_bwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
             const int* __restrict__ nra, const int64_t* __restrict__ roff,
             const int64_t* __restrict__ zoff, const int* __restrict__ rows,
             const T* __restrict__ Z, const T* __restrict__ y, T* __restrict__ x) {
   extern __shared__ unsigned char smem_raw[];
+  constexpr int kBwdWarpsPerCol = NT / 32 / kBwdCols;
   T* wv = reinterpret_cast<T*>(smem_raw);
+  __shared__ T part[kBwdCols][kBwdWarpsPerCol][3];
   const int4 it = items[blockIdx.x];
   const int J = it.x, k0 = it.y, kn = it.z;
   const int c0 = c0a[J], ns = nsa[J], nr = nra[J], ld = ns + nr;
@@ -141,46 +150,38 @@ k_bwd_chunk(const int4* __restrict__ items, const int* __restrict__ c0a, const i
     wv[3 * ns + k] = -x[3 * (size_t)Rj[k / 3] + (k % 3)];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T res[3] = {0, 0, 0};
-  for (int kk = wid; kk < kn; kk += 8) {
-    const int k = k0 + kk;
+  const int c = wid / kBwdWarpsPerCol, qw = wid % kBwdWarpsPerCol;
+  constexpr int kStride = 32 * kBwdWarpsPerCol;
+  T a0 = 0, a1 = 0, a2 = 0;
+  if (c < kn) {
+    const int k = k0 + c;
     const T* zc = Zj + (size_t)k * ld;
-    T a0 = 0, a1 = 0, a2 = 0, q0 = 0, q1 = 0, q2 = 0;
-    int r = k + lane;
-    for (; r + 32 < ld; r += 64) {
-      const T z0 = zc[r], z1 = zc[r + 32];
+    T q0 = 0, q1 = 0, q2 = 0;
+    int r = k + qw * 32 + lane;
+    for (; r + kStride < ld; r += 2 * kStride) {
+      const T z0 = zc[r], z1 = zc[r + kStride];
+      const int s1 = r + kStride;
       a0 += z0 * wv[3 * r]; a1 += z0 * wv[3 * r + 1]; a2 += z0 * wv[3 * r + 2];
-      q0 += z1 * wv[3 * r + 96]; q1 += z1 * wv[3 * r + 97]; q2 += z1 * wv[3 * r + 98];
+      q0 += z1 * wv[3 * s1]; q1 += z1 * wv[3 * s1 + 1]; q2 += z1 * wv[3 * s1 + 2];
     }
     if (r < ld) {
       const T z = zc[r];
       a0 += z * wv[3 * r]; a1 += z * wv[3 * r + 1]; a2 += z * wv[3 * r + 2];
     }
     a0 += q0; a1 += q1; a2 += q2;
-    a0 = warp_sum_t(a0); a1 = warp_sum_t(a1); a2 = warp_sum_t(a2);
-    res[0] = a0; res[1] = a1; res[2] = a2;
-    __syncwarp();
-    if (lane == 0) {
-      T* o = x + 3 * (size_t)(c0 + k);
-      o[0] = res[0]; o[1] = res[1]; o[2] = res[2];
+  }
+  a0 = warp_sum_t(a0); a1 = warp_sum_t(a1); a2 = warp_sum_t(a2);
+  if (lane == 0) { part[c][qw][0] = a0; part[c][qw][1] = a1; part[c][qw][2] = a2; }
+  __syncthreads();
+  if (threadIdx.x < 3 * kBwdCols) {
+    const int cc = threadIdx.x / 3, d = threadIdx.x % 3;
+    if (cc < kn) {
+      T acc = 0;
+#pragma unroll
+      for (int w = 0; w < kBwdWarpsPerCol; ++w) acc += part[cc][w][d];
+      x[3 * (size_t)(c0 + k0 + cc) + d] = acc;
     }
   }
-}
-
-// y[i] -= sum_e val[e] * x[col[e]]   (3-vectors; K (x) I_3 applied blockwise)
-template <typename T>
-__global__ void k_spmv3_sub(int nrows, const int* __restrict__ ptr, const int* __restrict__ col,
-                            const double* __restrict__ val, const T* __restrict__ x,
-                            T* __restrict__ y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrows) return;
-  T a0 = 0, a1 = 0, a2 = 0;
-  for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-    const T v = (T)val[e];
-    const T* xs = x + 3 * (size_t)col[e];
-    a0 += v * xs[0]; a1 += v * xs[1]; a2 += v * xs[2];
-  }
-  y[3 * (size_t)i] -= a0; y[3 * (size_t)i + 1] -= a1; y[3 * (size_t)i + 2] -= a2;
 }
 
 // u = Sinv y (n2 x n2 dense, 3 right-hand sides), one warp per row
@@ -209,14 +210,18 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 // Forward pass over the levels (leaves to root): y_J = L_JJ^-1 b_J on the
 // x1 positions, b_R -= L_RJ y_J on every off-diagonal row (x1 and x2).
 template <typename T>
-void trisolve_fwd(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y) {
+void trisolve_fwd(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y, bool wide) {
   for (int l = 0; l < m.n_levels; ++l) {
     const int a = m.h_fwd_ptr[l], e = m.h_fwd_ptr[l + 1];
     if (e <= a) continue;
     const size_t sm = sizeof(T) * 3 * (size_t)m.h_level_maxns[l];
     ProfScope ps(PROF_TRSV_FWD, s);
-    k_fwd_chunk<T><<<e - a, 256, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1, m.sn_roff,
-                                          m.sn_zoff, m.sn_rows, Z, b, y);
+    if (wide)
+      k_fwd_chunk<T, 1024><<<e - a, 1024, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                   m.sn_roff, m.sn_zoff, m.sn_rows, Z, b, y);
+    else
+      k_fwd_chunk<T, 256><<<e - a, 256, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                 m.sn_roff, m.sn_zoff, m.sn_rows, Z, b, y);
     count_launch();
   }
 }
@@ -224,14 +229,18 @@ void trisolve_fwd(cudaStream_t s, const DevMesh& m, const T* Z, T* b, T* y) {
 // Backward pass (root to leaves): x_J = L_JJ^-T (y_J - L_RJ^T x_R), reading
 // x_R from b (x1 ancestors solved earlier, x2 rows = dx2), writing b on x1.
 template <typename T>
-void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b) {
+void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b, bool wide) {
   for (int l = m.n_levels - 1; l >= 0; --l) {
     const int a = m.h_bwd_ptr[l], e = m.h_bwd_ptr[l + 1];
     if (e <= a) continue;
     const size_t sm = sizeof(T) * 3 * (size_t)m.h_level_maxld[l];
     ProfScope ps(PROF_TRSV_BWD, s);
-    k_bwd_chunk<T><<<e - a, 256, sm, s>>>(m.bwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1, m.sn_roff,
-                                          m.sn_zoff, m.sn_rows, Z, y, b);
+    if (wide)
+      k_bwd_chunk<T, 1024><<<e - a, 1024, sm, s>>>(m.bwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                   m.sn_roff, m.sn_zoff, m.sn_rows, Z, y, b);
+    else
+      k_bwd_chunk<T, 256><<<e - a, 256, sm, s>>>(m.bwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                 m.sn_roff, m.sn_zoff, m.sn_rows, Z, y, b);
     count_launch();
   }
 }
@@ -242,8 +251,8 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
 //   diagonal: dx2 = Sigma-hat^-1 y2 = u - Sigma^-1 Q^T v,  u = Sigma^-1 y2
 //   upper:    dx1 = L1^-T (z1 - L21^T dx2)             (one backward pass)
 template <typename T>
-cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
-                          int* info, int num_sms) {
+cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int* info,
+                          int num_sms, bool wide) {
   const int nf = m.nf, n1 = m.n1, n2 = m.n2;
   const bool f64 = std::is_same<T, double>::value;
   double* r = m.r;                                  // float64 work (nf * 3)
@@ -252,7 +261,7 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
   const T* Z = f64 ? (const T*)m.Z : (const T*)m.Zf;
   k_gather_rhs<T><<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, g, b);
   count_launch();
-  if (n1 > 0) trisolve_fwd<T>(s, m, Z, b, y);
+  if (n1 > 0) trisolve_fwd<T>(s, m, Z, b, y, wide);
   if (n2 > 0) {
     T* y2 = b + 3 * (size_t)n1;
     double* u = m.u;
@@ -269,21 +278,20 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
         count_launch(2);
       }
     }
-    if (nc > 0) {
+    {
       // The reduced system carries the barrier stiffness (cond ~ kappa b''):
       // float64 factors, or float32 factors refined with float64 residuals.
+      // n_c is read on the device (z2 = u when it is 0).
       ProfScope psr(PROF_REDUCED, s);
-      const cudaError_t e = reduced_solve(s, m, nc, u, y2, z2, info, num_sms, f64 ? 0 : 1);
+      const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, f64 ? 0 : 1);
       if (e != cudaSuccess) return e;
-    } else {
-      cudaMemcpyAsync(z2, u, sizeof(double) * 3 * (size_t)n2, cudaMemcpyDeviceToDevice, s);
     }
     if (!f64) {
       k_convert<double, T><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, z2, y2);
       count_launch();
     }
   }
-  if (n1 > 0) trisolve_bwd<T>(s, m, Z, y, b);
+  if (n1 > 0) trisolve_bwd<T>(s, m, Z, y, b, wide);
   if (!f64) {
     k_convert<T, double><<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(3 * n1, b, r);
     count_launch();
@@ -297,16 +305,22 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
 }  // namespace
 
 void set_solver_smem_limits(int max_bytes) {
-  cudaFuncSetAttribute(k_fwd_chunk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-  cudaFuncSetAttribute(k_bwd_chunk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-  cudaFuncSetAttribute(k_fwd_chunk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-  cudaFuncSetAttribute(k_bwd_chunk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
+  cudaFuncSetAttribute(k_bwd_chunk<double, 256>, a, max_bytes);
+  cudaFuncSetAttribute(k_fwd_chunk<float, 256>, a, max_bytes);
+  cudaFuncSetAttribute(k_bwd_chunk<float, 256>, a, max_bytes);
+  cudaFuncSetAttribute(k_fwd_chunk<double, 1024>, a, max_bytes);
+  cudaFuncSetAttribute(k_bwd_chunk<double, 1024>, a, max_bytes);
+  cudaFuncSetAttribute(k_fwd_chunk<float, 1024>, a, max_bytes);
+  cudaFuncSetAttribute(k_bwd_chunk<float, 1024>, a, max_bytes);
 }
 
-cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
-                        int precision, int* info_dev, int num_sms) {
-  if (precision == 0) return global_step_t<double>(s, m, g, dx, nc, info_dev, num_sms);
-  return global_step_t<float>(s, m, g, dx, nc, info_dev, num_sms);
+cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
+                        int* info_dev, int num_sms, bool alone) {
+  // 32-warp solve items only for a float32 solve that has the GPU to itself
+  if (precision == 0) return global_step_t<double>(s, m, g, dx, info_dev, num_sms, false);
+  return global_step_t<float>(s, m, g, dx, info_dev, num_sms, alone);
 }
 
 }  // namespace fsim

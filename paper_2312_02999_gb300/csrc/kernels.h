@@ -88,6 +88,19 @@ struct DevMesh {
   float* redf = nullptr;
   int64_t red_cap = 0;        // elements of red / redf
   int nc_cap = 0;             // n_c the reduced buffers are sized for
+  // Host handles of CUDA graphs replaying fixed launch sequences on this
+  // workspace (capi.cu); a fresh workspace copy starts with none.
+  struct Graph {
+    void* exec = nullptr;       // cudaGraphExec_t
+    const void* key = nullptr;  // buffer the sequence was captured on
+    int key2 = 0, gen = -1, coop = 0;
+    bool alone = true;
+    int64_t kernels = 0;        // kernel nodes (counted as launches per replay)
+    bool failed = false;        // capture unsupported: launch directly
+  };
+  static constexpr int kGraphs = 8;
+  Graph graphs[kGraphs];
+  int red_gen = 0;            // bumped whenever the reduced buffers move
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------
@@ -115,18 +128,23 @@ void launch_barrier_pairs(cudaStream_t s, const DevMesh& m, int64_t npairs, cons
 void launch_mark_scan(cudaStream_t s, const DevMesh& m);
 // Scatter pair gradients into g and Hessian blocks into the dense B-check (3nc)^2.
 void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, int nc, double* g);
+// Reset the CCD outputs: counters[1] = counters[9] = 0 and scal[1] = 1.
+void launch_ccd_reset(cudaStream_t s, const DevMesh& m);
 
 // ---- global step (k_solve.cu) ----------------------------------------------
-// dx (by vertex) solving (H + B) dx = -g, with B-check already assembled for nc.
-// num_sms is the CTA count of the cooperative reduced-system launch.
-cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int nc,
-                        int precision, int* info_dev, int num_sms);
+// dx (by vertex) solving (H + B) dx = -g, with B-check already assembled for
+// the n_c in counters[3] (read on the device: the launch sequence is fixed
+// per workspace and can be captured in a CUDA graph).  num_sms is the CTA
+// count of the cooperative reduced-system launch; alone = no other solve
+// shares the GPU (selects wider triangular-solve work items).
+cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
+                        int* info_dev, int num_sms, bool alone);
 int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
 // z2 = u - Sigma^-1 Q^T v with the push-through reduced system (k_reduced.cu);
 // precision 0: float64 factors, 1: float32 factors + float64 refinement.
 // y2 (double for precision 0, float for 1) is the Schur right-hand side with
 // u = Sigma^-1 y2; it scales the refinement's stopping test.
-cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, int nc, const double* u, const void* y2,
+cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
                           double* z2, int* info, int num_sms, int precision);
 void set_solver_smem_limits(int max_bytes);
 
@@ -154,6 +172,10 @@ struct ProfScope {
   cudaStream_t stream;
 };
 void prof_set_mask(unsigned mask);
+bool prof_active();
+// While a thread captures a CUDA graph its launches are not counted (the
+// replays count the graph's kernel nodes instead).
+void set_capturing(bool on);
 int prof_read(int cls, int64_t* launches, double* total_ms);
 void prof_reset();
 

@@ -45,6 +45,7 @@ struct Exec {
   int* h_counters = nullptr;     // kCounters pinned ints
   double* h_scal = nullptr;      // kScal pinned doubles
   int coop_ctas = 1;
+  bool alone = true;             // no other solve shares the GPU
   std::vector<void*>* allocs = nullptr;
   size_t* bytes = nullptr;
 };
@@ -56,6 +57,7 @@ int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allo
 int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                    bool init_is_dev, int precision, fsim_frame_stats* stats);
 void rt_free_list(std::vector<void*>& allocs);
+void rt_destroy_graphs(DevMesh& m);
 // Bytes a new workspace of this mesh takes (per-solve buffers plus the
 // reduced-system buffers at their initial size).
 size_t rt_slot_bytes(const MeshState& ms);

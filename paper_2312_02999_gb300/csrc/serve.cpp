@@ -104,6 +104,7 @@ struct fsim_server_s {
 namespace {
 
 void free_slot(Slot& s) {
+  rt_destroy_graphs(s.d);
   rt_free_list(s.allocs);
   if (s.h_x) cudaFreeHost(s.h_x);
   if (s.h_act) cudaFreeHost(s.h_act);
@@ -139,6 +140,7 @@ int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J) {
   ex.h_counters = w.h_counters;
   ex.h_scal = w.h_scal;
   ex.coop_ctas = sv->coop_ctas;
+  ex.alone = sv->n_workers == 1;
   ex.allocs = &s.allocs;
   ex.bytes = &s.bytes;
   // actuation A = a f f^T + a^-1/2 (I - f f^T) per tet; host arrays go
