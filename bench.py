@@ -48,6 +48,10 @@ def parse():
                     help="concurrent frame sequences (server workers)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the float64 served leg and the host-buffer leg")
+    ap.add_argument("--legs", choices=["all", "single"], default="all",
+                    help="single: only the single-sequence legs (profiling runs)")
+    ap.add_argument("--first-frame", type=int, default=20,
+                    help="first frame of each sequence (solved from rest, untimed)")
     return ap.parse_args()
 
 
@@ -135,7 +139,7 @@ pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr
                mesh.W_val, S.Params(dhat=mesh.dhat, tol_abs=mesh.tol_abs, tol_rel=mesh.tol_rel))
 setup = time.perf_counter() - t0
 for k in range({steps}):
-    a = I.bump_actuation(field, coeffs[1 + k])
+    a = I.bump_actuation(field, coeffs[min({first} + k, len(coeffs) - 1)])
     pr.set_actuation(a.fiber, a.stretch)
     t = time.perf_counter()
     x, st = pr.solve_frame(mesh.rest, max_iters={iters}, record=False)
@@ -144,9 +148,9 @@ print(json.dumps({{"setup_s": setup, "samples": out}}))
 """
 
 
-def run_oracle_sample(n_target, steps, iters):
+def run_oracle_sample(n_target, steps, iters, first):
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, n=n_target, steps=steps, iters=iters)
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n_target, steps=steps, iters=iters, first=first)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
     if r.returncode != 0:
@@ -157,10 +161,10 @@ def run_oracle_sample(n_target, steps, iters):
     return 1.0 / s_per_frame, res
 
 
-def cpu_baseline(n_target):
-    fps, res = run_oracle_sample(n_target, steps=1, iters=2)
+def cpu_baseline(n_target, first):
+    fps, res = run_oracle_sample(n_target, steps=1, iters=2, first=first)
     return {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": (f"2 iterations of face frame 1 (full sparse LU of the contact system each "
+            "sample": (f"2 iterations of face frame {first} (full sparse LU of the contact system each "
                        f"iteration), {res['samples'][0][0]:.1f} s; frames/s = 1 / (s per iteration x "
                        f"{ORACLE_ITERS_PER_FRAME} iterations per frame); single thread")}
 
@@ -170,6 +174,8 @@ def bench_config(args, world):
     return {"workload": "face_shell_30k", "n_target": args.n_target, "form": "served",
             "streams": S, "workers": S, "frames_per_stream": K, "precision": "mixed",
             "step": f"{S} frames, one per stream (each warm-started from its own previous frame)",
+            "frames": f"sequence frames {args.first_frame}.. (first solved from rest, then "
+                      f"{args.warmup - 1} warm-up frames, then the timed frames)",
             "l2": ("served legs: each frame is ~80 solver iterations over >129 MB of distinct "
                    "data (shared factor and Sigma^-1, per-slot workspaces); single-stream legs "
                    "flush L2 (256 MB write) before every frame"),
@@ -182,7 +188,7 @@ def reference_arm(args):
     if rank != 0:
         return
     n = args.warmup + args.steps
-    fps, res = run_oracle_sample(args.n_target, steps=n, iters=1)
+    fps, res = run_oracle_sample(args.n_target, steps=n, iters=1, first=args.first_frame)
     timed = res["samples"][args.warmup:]
     per_iter = [t / max(it, 1) for t, it in timed]
     s_frame = statistics.mean(per_iter) * ORACLE_ITERS_PER_FRAME
@@ -211,9 +217,11 @@ def percentile(v, q):
     return s[k]
 
 
-def stream_actuations(I, field, n_frames, seed):
+def stream_actuations(I, field, first, n_frames, seed):
+    # entry 0 is unused (index 1 = the sequence's frame `first`)
     coeffs = I.keyframe_coeffs(seed=seed)
-    return [I.bump_actuation(field, coeffs[f]) for f in range(n_frames + 1)]
+    return [I.bump_actuation(field, coeffs[min(first + f - 1, len(coeffs) - 1)])
+            for f in range(n_frames + 1)]
 
 
 def run_ours(args):
@@ -235,7 +243,8 @@ def run_ours(args):
     mesh = I.face_shell(n_target=args.n_target)
     field = I.bump_field(mesh, seed=2)
     # stream s of rank r animates its own keyframe sequence (its own "actor")
-    acts = [stream_actuations(I, field, W + K, seed=3 + rank * S + s) for s in range(S)]
+    F0 = args.first_frame
+    acts = [stream_actuations(I, field, F0, W + K, seed=3 + rank * S + s) for s in range(S)]
     ctx = fsim.Context(local)
     m = ctx.upload(mesh)
     m.prefactor(fsim.params_for(mesh))
@@ -374,6 +383,15 @@ def run_ours(args):
     results = {}
     results["single_mixed"] = single(fsim.MIXED, profile=True)
     results["single_fp64"] = single(fsim.FP64, profile=False)
+    if args.legs == "single":
+        if rank == 0:
+            sm = results["single_mixed"]
+            print(json.dumps({"partial": "single-sequence legs only",
+                              "mixed_ms_per_frame": statistics.mean(sm["times"]),
+                              "fp64_ms_per_frame": statistics.mean(results["single_fp64"]["times"]),
+                              "iterations": [st["iterations"] for st in sm["stats"]]}), flush=True)
+        ctx.close()
+        return
     results["served_mixed"] = served(fsim.MIXED, True, timed_clock=True)
     if not args.quick:
         results["served_fp64"] = served(fsim.FP64, True)
@@ -431,7 +449,7 @@ def run_ours(args):
                        "latency_ms": {"p50": percentile(e["lat"], 50), "p99": percentile(e["lat"], 99)}}
     if not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline(args.n_target)
+            line["cpu_baseline"] = cpu_baseline(args.n_target, args.first_frame)
         except Exception as ex:  # reported, never silently replaced
             line["cpu_baseline"] = {"error": str(ex)[-300:]}
     print(json.dumps(line), flush=True)

@@ -76,8 +76,14 @@ typedef struct {
   int32_t coop_ctas;      /* CTAs of the cooperative reduced-system kernel;
                              0 = one per SM (a tuning knob: fewer CTAs make
                              its grid-wide barriers cheaper)                   */
-  int64_t contact_capacity; /* max candidate/active pairs per detection; <= 0
+  int64_t contact_capacity; /* max near pairs (within 2 d0 in the float32
+                               prefilter) and CCD candidates per pass; <= 0
                                selects max(2^20, 256 * proxy triangles)        */
+  int64_t active_capacity;  /* max |C| (pairs with d < d0, each holding a
+                               12-vector and a 12x12 block); <= 0 selects
+                               max(2^16, 16 * proxy triangles), at most
+                               contact_capacity.  More pairs than either
+                               capacity return FSIM_ECONTACT_OVERFLOW         */
 } fsim_params;
 
 /* Per-frame statistics filled by fsim_solve_frame. */
@@ -99,8 +105,8 @@ typedef struct {
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
- * coop_ctas 0, contact_capacity auto.  dhat must still be set by the
- * caller. */
+ * coop_ctas 0, contact_capacity and active_capacity auto.  dhat must still
+ * be set by the caller. */
 fsim_status fsim_default_params(fsim_params* p);
 
 /* Create a context on CUDA device `device`; it owns one CUDA stream and all

@@ -162,11 +162,11 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.u, 3 * (size_t)std::max(m.n2, 1), bytes));
   TRY(dalloc(al, &m.rf, 3 * (size_t)m.nf + 8, bytes));
   TRY(dalloc(al, &m.uf, 3 * (size_t)std::max(m.n2, 1), bytes));
-  TRY(dalloc(al, &m.pairs, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.pairs, (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.cand, (size_t)m.cap, bytes));
   TRY(dalloc(al, &m.nearl, (size_t)m.cap, bytes));
-  TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap, bytes));
-  TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap_act, bytes));
+  TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.x2mark, (size_t)std::max(m.n2, 1), bytes));
   TRY(dalloc(al, &m.clist, (size_t)std::max(m.n2, 1), bytes));
   m.Bc = nullptr; m.bocc = nullptr; m.red = nullptr; m.redf = nullptr;
@@ -434,6 +434,7 @@ fsim_status fsim_default_params(fsim_params* p) {
   p->ccd_s = 0.1;
   p->accd_max_iters = 2000;
   p->contact_capacity = 0;
+  p->active_capacity = 0;
   return FSIM_OK;
 }
 
@@ -461,6 +462,7 @@ fsim_status fsim_create(fsim_ctx_t* out, int device) {
     return FSIM_ENOMEM;
   }
   set_solver_smem_limits(200 * 1024);
+  set_reduced_smem_limits();
   *out = c;
   return FSIM_OK;
 }
@@ -666,6 +668,9 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   }
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
                                   : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
+  m.cap_act = p->active_capacity > 0 ? p->active_capacity
+                                     : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));
+  m.cap_act = std::min(m.cap_act, m.cap);
   if (m.cap >= (1LL << 31)) return FSIM_EINVAL;
   TRY(dalloc(ms, &ms.gtmp, 3 * (size_t)m.n));
   TRY(dalloc(ms, &ms.dxtmp, 3 * (size_t)m.n));

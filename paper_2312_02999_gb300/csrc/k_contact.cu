@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
 
 // float64 narrow phase of the near pairs (one pair per thread, fixed grid,
 // length read on the device): d < dhat joins C and adds kappa b(d).
-__global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap,
+__global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, int64_t cap_act,
                              const unsigned long long* __restrict__ nearl,
                              const double* __restrict__ s, const int* __restrict__ tris,
                              const int* __restrict__ edges, double dhat, double kappa,
@@ -707,7 +707,7 @@ __global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap,
     gather_X(s, V, X);
     const double d = pair_distance(type, X);
     if (d < dhat) {
-      append(pack_key(type, i, j), pairs, counters + 0, counters + 2, cap);
+      append(pack_key(type, i, j), pairs, counters + 0, counters + 2, cap_act);
       esum += barrier_value(d, dhat);
       if (!(d > 0.0)) atomicOr(counters + 5, 1);
     }
@@ -796,7 +796,8 @@ void launch_detect(cudaStream_t st, const DevMesh& m, const double* sp, double d
   k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, nullptr, m.tris, m.edges, dhat,
                                                 m.pbox, m.pkey, m.sf, nullptr);
   launch_sweeps(st, m, 0, m.nearl, m.counters + 8, m.counters + 2, 2.0f * (float)dhat);
-  k_near_pairs<<<2 * 152, 128, 0, st>>>(m.counters + 8, m.cap, m.nearl, sp, m.tris, m.edges, dhat,
+  k_near_pairs<<<2 * 152, 128, 0, st>>>(m.counters + 8, m.cap, m.cap_act, m.nearl, sp, m.tris,
+                                        m.edges, dhat,
                                         kappa, m.pairs, m.counters, m.scal);
   count_launch(2);
 }
@@ -822,18 +823,18 @@ void launch_ccd(cudaStream_t st, const DevMesh& m, const double* sp, const doubl
 
 void launch_barrier_pairs(cudaStream_t st, const DevMesh& m, int64_t np, const double* sp,
                           double dhat, double kappa, int precision) {
-  np = np < m.cap ? np : m.cap;
+  np = np < m.cap_act ? np : m.cap_act;
   if (np <= 0) return;
   ProfScope ps(PROF_BARRIER, st);
   const int64_t want = (np + kPairWarps - 1) / kPairWarps;
   const unsigned grid = (unsigned)(want < 8 * 152 ? want : 8 * 152);
   if (precision == 0)
     k_barrier_pairs<double><<<grid, 32 * kPairWarps, 0, st>>>(
-        m.counters, m.cap, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+        m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);
   else
     k_barrier_pairs<float><<<grid, 32 * kPairWarps, 0, st>>>(
-        m.counters, m.cap, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+        m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);
   count_launch();
 }
@@ -855,7 +856,7 @@ void launch_ccd_reset(cudaStream_t st, const DevMesh& m) {
 }
 
 void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int nc, double* g) {
-  np = np < m.cap ? np : m.cap;
+  np = np < m.cap_act ? np : m.cap_act;
   if (np <= 0) return;
   k_barrier_scatter<<<(unsigned)((np + 63) / 64), 64, 0, st>>>(np, m.pairs, m.tris, m.edges,
                                                               m.Wptr, m.Wcol, m.Wval, m.x2of,

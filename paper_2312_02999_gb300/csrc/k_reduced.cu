@@ -63,8 +63,34 @@ struct RedArgs {
   double* rho;          // n3
   double* w;            // n3
   double* nrm;          // 3: |rho|^2 of a refinement step, unused, |y2|^2
+  double* S64;          // one-CTA path: Sigma^-1[c, c] in float64 (n_c x n_c)
   int* info;
+  int small_lim;        // n_c handled by the one-CTA path (0: none)
+  FT* spk;              // one-CTA path: L_s packed, diagonal blocks inverted
 };
+
+// Offsets of the workspace for a given n_c (every kernel of the reduced solve
+// derives them from the n_c it reads on the device).
+template <typename FT>
+__device__ __forceinline__ void red_layout(RedArgs<FT>& a, int nc) {
+  const int n3 = 3 * nc;
+  // every segment starts on a 16-byte boundary (vector loads)
+  constexpr size_t q = 16 / sizeof(FT);
+  auto al = [](size_t x) { return (x + q - 1) / q * q; };
+  a.nc = nc;
+  a.S = a.base;
+  a.X = a.S + al((size_t)nc * nc);
+  a.N = a.X + al((size_t)n3 * n3);
+  a.dinv_s = a.N + al((size_t)(n3 + 1) * n3);
+  a.dinv_n = a.dinv_s + al(nc);
+  a.fv = a.dinv_n + al(n3);
+  a.spk = a.fv + al(2 * (size_t)n3);
+  a.y = a.dtail_end - 4 * (size_t)n3 - 8;
+  a.v = a.y + n3; a.rho = a.v + n3; a.w = a.rho + n3; a.nrm = a.w + n3;
+  a.S64 = a.y - (size_t)nc * nc;
+  a.list = a.ibase;
+  a.cnt = a.list + (size_t)nc * nc;
+}
 
 __device__ __forceinline__ double rsqrt_refined(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
@@ -259,112 +285,24 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
     for (int e = gtid; e < 3 * a.n2; e += gsz) a.z2[e] = a.u[e];
     return;
   }
-  a.nc = nc;
-  a.S = a.base;
-  a.X = a.S + (size_t)nc * nc;
-  a.N = a.X + (size_t)n3 * n3;
-  a.dinv_s = a.N + (size_t)(n3 + 1) * n3;
-  a.dinv_n = a.dinv_s + nc;
-  a.fv = a.dinv_n + n3;
-  a.y = a.dtail_end - 4 * (size_t)n3 - 8;
-  a.v = a.y + n3; a.rho = a.v + n3; a.w = a.rho + n3; a.nrm = a.w + n3;
-  a.list = a.ibase;
-  a.cnt = a.list + (size_t)nc * nc;
-
-  // 1. S, block lists, y = B u_c
-  if (gtid == 0) a.nrm[2] = 0.0;
-  for (int e = gtid; e < nc * nc; e += gsz) {
-    const int i = e / nc, j = e % nc;
-    a.S[e] = (FT)a.Sinv[(size_t)a.clist[i] * a.n2 + a.clist[j]];
-  }
-  for (int i = gwarp; i < nc; i += nwarps) {
-    int base = 0;
-    for (int j0 = 0; j0 < nc; j0 += 32) {
-      const int j = j0 + lane;
-      const bool f = j < nc && a.bocc[(size_t)i * nc + j] != 0;
-      const unsigned msk = __ballot_sync(0xffffffffu, f);
-      if (f) a.list[(size_t)i * nc + base + __popc(msk & ((1u << lane) - 1u))] = j;
-      base += __popc(msk);
+  red_layout(a, nc);
+  if (nc > a.small_lim) {   // otherwise phases 1-7 ran in the one-CTA path
+    // 1. S, block lists, y = B u_c
+    if (gtid == 0) a.nrm[2] = 0.0;
+    for (int e = gtid; e < nc * nc; e += gsz) {
+      const int i = e / nc, j = e % nc;
+      a.S[e] = (FT)a.Sinv[(size_t)a.clist[i] * a.n2 + a.clist[j]];
     }
-    if (lane == 0) a.cnt[i] = base;
-  }
-  grid.sync();
-  for (int row = gtid; row < n3; row += gsz) {
-    const int i = row / 3;
-    const double* brow = a.Bc + (size_t)row * n3;
-    double acc = 0.0;
-    for (int e = 0; e < a.cnt[i]; ++e) {
-      const int j = a.list[(size_t)i * nc + e];
-      const double* uj = a.u + 3 * (size_t)a.clist[j];
-      acc += brow[3 * j] * uj[0] + brow[3 * j + 1] * uj[1] + brow[3 * j + 2] * uj[2];
-    }
-    a.y[row] = acc;
-  }
-  if (a.refine > 0) {
-    double q = 0.0;
-    for (int e = gtid; e < 3 * a.n2; e += gsz) q += (double)a.y2[e] * (double)a.y2[e];
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (lane == 0 && q != 0.0) atomicAdd(&a.nrm[2], q);
-  }
-  // 2. L_s
-  coop_chol<FT>(grid, a.S, nc, 0, nc, a.dinv_s, a.info, sm);
-  // 3. X[(i,a),(k,b)] = sum_{j in row i, j >= k} B[(i,a),(j,b)] L_s[j][k]
-  for (int64_t e = gtid; e < (int64_t)n3 * n3; e += gsz) {
-    const int row = (int)(e / n3), colx = (int)(e % n3);
-    const int i = row / 3, k = colx / 3, b = colx % 3;
-    const double* brow = a.Bc + (size_t)row * n3;
-    double acc = 0.0;
-    for (int q = 0; q < a.cnt[i]; ++q) {
-      const int j = a.list[(size_t)i * nc + q];
-      if (j >= k) acc += brow[3 * j + b] * (double)a.S[(size_t)j * nc + k];
-    }
-    a.X[e] = (FT)acc;
-  }
-  grid.sync();
-  // 4. N = I + (L_s (x) I)^T X (lower part suffices) and t0
-  for (int64_t e = gtid; e < (int64_t)(n3 + 1) * n3; e += gsz) {
-    const int row = (int)(e / n3), col = (int)(e % n3);
-    double acc;
-    if (row < n3) {
-      if (col > row) continue;
-      const int i = row / 3, ax = row % 3;
-      acc = (row == col) ? 1.0 : 0.0;
-      for (int j = i; j < nc; ++j)
-        acc += (double)a.S[(size_t)j * nc + i] * (double)a.X[(size_t)(3 * j + ax) * n3 + col];
-    } else {
-      const int i = col / 3, ax = col % 3;
-      acc = 0.0;
-      for (int j = i; j < nc; ++j) acc += (double)a.S[(size_t)j * nc + i] * a.y[3 * j + ax];
-    }
-    a.N[e] = (FT)acc;
-  }
-  grid.sync();
-  // 5. L_N (the extra row becomes l = L_N^-1 t0)
-  coop_chol<FT>(grid, a.N, n3, 1, n3, a.dinv_n, a.info, sm);
-  // 6. v = (L_s (x) I)^-T L_N^-T l
-  FT* t = a.fv;
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < n3; e += kRT) t[e] = a.N[(size_t)n3 * n3 + e];
-    __syncthreads();
-    cta_trsv<FT, true>(a.N, a.dinv_n, n3, n3, t, 1, sm);
-    cta_trsv<FT, true>(a.S, a.dinv_s, nc, nc, t, 3, sm);
-    for (int e = tid; e < n3; e += kRT) a.v[e] = (double)t[e];
-  }
-  grid.sync();
-  // 7. refinement with float64 residuals (float32 factors), until
-  //    |rho| <= 1e-7 |y2|, until a step fails to halve |rho|, or after
-  //    a.refine steps
-  double prev = -1.0;
-  for (int it = 0; it < a.refine; ++it) {
-    if (gtid == 0) a.nrm[0] = 0.0;
-    grid.sync();
-    // w = S v with S = Sigma^-1[c, c] (x) I_3 in float64
-    for (int e = gtid; e < n3; e += gsz) {
-      const int i = e / 3, ax = e % 3;
-      const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
-      double acc = 0.0;
-      for (int j = 0; j < nc; ++j) acc += srow[a.clist[j]] * a.v[3 * j + ax];
-      a.w[e] = acc;
+    for (int i = gwarp; i < nc; i += nwarps) {
+      int base = 0;
+      for (int j0 = 0; j0 < nc; j0 += 32) {
+        const int j = j0 + lane;
+        const bool f = j < nc && a.bocc[(size_t)i * nc + j] != 0;
+        const unsigned msk = __ballot_sync(0xffffffffu, f);
+        if (f) a.list[(size_t)i * nc + base + __popc(msk & ((1u << lane) - 1u))] = j;
+        base += __popc(msk);
+      }
+      if (lane == 0) a.cnt[i] = base;
     }
     grid.sync();
     for (int row = gtid; row < n3; row += gsz) {
@@ -373,29 +311,108 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
       double acc = 0.0;
       for (int e = 0; e < a.cnt[i]; ++e) {
         const int j = a.list[(size_t)i * nc + e];
-        acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
-               brow[3 * j + 2] * a.w[3 * j + 2];
+        const double* uj = a.u + 3 * (size_t)a.clist[j];
+        acc += brow[3 * j] * uj[0] + brow[3 * j + 1] * uj[1] + brow[3 * j + 2] * uj[2];
       }
-      const double rr = a.y[row] - a.v[row] - acc;
-      a.rho[row] = rr;
-      atomicAdd(&a.nrm[0], rr * rr);
+      a.y[row] = acc;
+    }
+    if (a.refine > 0) {
+      double q = 0.0;
+      for (int e = gtid; e < 3 * a.n2; e += gsz) q += (double)a.y2[e] * (double)a.y2[e];
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0 && q != 0.0) atomicAdd(&a.nrm[2], q);
+    }
+    // 2. L_s
+    coop_chol<FT>(grid, a.S, nc, 0, nc, a.dinv_s, a.info, sm);
+    // 3. X[(i,a),(k,b)] = sum_{j in row i, j >= k} B[(i,a),(j,b)] L_s[j][k]
+    for (int64_t e = gtid; e < (int64_t)n3 * n3; e += gsz) {
+      const int row = (int)(e / n3), colx = (int)(e % n3);
+      const int i = row / 3, k = colx / 3, b = colx % 3;
+      const double* brow = a.Bc + (size_t)row * n3;
+      double acc = 0.0;
+      for (int q = 0; q < a.cnt[i]; ++q) {
+        const int j = a.list[(size_t)i * nc + q];
+        if (j >= k) acc += brow[3 * j + b] * (double)a.S[(size_t)j * nc + k];
+      }
+      a.X[e] = (FT)acc;
     }
     grid.sync();
-    {   // the same values for every thread of the grid: a uniform decision
-      const double r2 = __ldcg(a.nrm), ys = __ldcg(a.nrm + 2);
-      if (!(r2 > 1e-14 * ys)) break;
-      if (prev >= 0.0 && !(r2 < 0.25 * prev)) break;
-      prev = r2;
+    // 4. N = I + (L_s (x) I)^T X (lower part suffices) and t0
+    for (int64_t e = gtid; e < (int64_t)(n3 + 1) * n3; e += gsz) {
+      const int row = (int)(e / n3), col = (int)(e % n3);
+      double acc;
+      if (row < n3) {
+        if (col > row) continue;
+        const int i = row / 3, ax = row % 3;
+        acc = (row == col) ? 1.0 : 0.0;
+        for (int j = i; j < nc; ++j)
+          acc += (double)a.S[(size_t)j * nc + i] * (double)a.X[(size_t)(3 * j + ax) * n3 + col];
+      } else {
+        const int i = col / 3, ax = col % 3;
+        acc = 0.0;
+        for (int j = i; j < nc; ++j) acc += (double)a.S[(size_t)j * nc + i] * a.y[3 * j + ax];
+      }
+      a.N[e] = (FT)acc;
     }
+    grid.sync();
+    // 5. L_N (the extra row becomes l = L_N^-1 t0)
+    coop_chol<FT>(grid, a.N, n3, 1, n3, a.dinv_n, a.info, sm);
+    // 6. v = (L_s (x) I)^-T L_N^-T l
+    FT* t = a.fv;
     if (blockIdx.x == 0) {
-      cta_lt_apply<FT, double>(a.S, nc, a.rho, t);
+      for (int e = tid; e < n3; e += kRT) t[e] = a.N[(size_t)n3 * n3 + e];
       __syncthreads();
-      cta_trsv<FT, false>(a.N, a.dinv_n, n3, n3, t, 1, sm);
       cta_trsv<FT, true>(a.N, a.dinv_n, n3, n3, t, 1, sm);
       cta_trsv<FT, true>(a.S, a.dinv_s, nc, nc, t, 3, sm);
-      for (int e = tid; e < n3; e += kRT) a.v[e] += (double)t[e];
+      for (int e = tid; e < n3; e += kRT) a.v[e] = (double)t[e];
     }
     grid.sync();
+    // 7. refinement with float64 residuals (float32 factors), until
+    //    |rho| <= 1e-7 |y2|, until a step fails to halve |rho|, or after
+    //    a.refine steps
+    double prev = -1.0;
+    for (int it = 0; it < a.refine; ++it) {
+      if (gtid == 0) a.nrm[0] = 0.0;
+      grid.sync();
+      // w = S v with S = Sigma^-1[c, c] (x) I_3 in float64
+      for (int e = gtid; e < n3; e += gsz) {
+        const int i = e / 3, ax = e % 3;
+        const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
+        double acc = 0.0;
+        for (int j = 0; j < nc; ++j) acc += srow[a.clist[j]] * a.v[3 * j + ax];
+        a.w[e] = acc;
+      }
+      grid.sync();
+      for (int row = gtid; row < n3; row += gsz) {
+        const int i = row / 3;
+        const double* brow = a.Bc + (size_t)row * n3;
+        double acc = 0.0;
+        for (int e = 0; e < a.cnt[i]; ++e) {
+          const int j = a.list[(size_t)i * nc + e];
+          acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
+                 brow[3 * j + 2] * a.w[3 * j + 2];
+        }
+        const double rr = a.y[row] - a.v[row] - acc;
+        a.rho[row] = rr;
+        atomicAdd(&a.nrm[0], rr * rr);
+      }
+      grid.sync();
+      {   // the same values for every thread of the grid: a uniform decision
+        const double r2 = __ldcg(a.nrm), ys = __ldcg(a.nrm + 2);
+        if (!(r2 > 1e-14 * ys)) break;
+        if (prev >= 0.0 && !(r2 < 0.25 * prev)) break;
+        prev = r2;
+      }
+      if (blockIdx.x == 0) {
+        cta_lt_apply<FT, double>(a.S, nc, a.rho, t);
+        __syncthreads();
+        cta_trsv<FT, false>(a.N, a.dinv_n, n3, n3, t, 1, sm);
+        cta_trsv<FT, true>(a.N, a.dinv_n, n3, n3, t, 1, sm);
+        cta_trsv<FT, true>(a.S, a.dinv_s, nc, nc, t, 3, sm);
+        for (int e = tid; e < n3; e += kRT) a.v[e] += (double)t[e];
+      }
+      grid.sync();
+    }
   }
   // 8. z2 = u - (Sigma^-1[:, c] (x) I_3) v, one warp per row
   for (int q = gwarp; q < a.n2; q += nwarps) {
@@ -419,6 +436,433 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-CTA path for small n_c (float32 factors): the two factorisations and
+// all triangular solves run inside one CTA with the matrix in shared memory,
+// so no grid-wide barrier is needed; only the data-parallel products run
+// over the grid.  Launch sequence (all read n_c on the device and return
+// when 0 < n_c <= kSmallNc does not hold):
+//   k_small_s   (1 CTA)  S = Sigma^-1[c,c], L_s, block lists of B
+//   k_small_x   (grid)   y = B u_c (float64), |y2|^2, X = B (L_s (x) I_3)
+//   k_small_n   (grid)   N = I + (L_s (x) I_3)^T X  (lower part)
+//   k_small_v   (1 CTA)  L_N, v = L^-T N^-1 L^T y and its float64 refinement
+// then the cooperative kernel runs only its z2 update.
+// ---------------------------------------------------------------------------
+constexpr int kSmallNc = 96;               // 3 n_c <= 288 fits in shared memory
+constexpr int kSmallN3 = 3 * kSmallNc;
+constexpr int kST = 512;                   // threads of the one-CTA kernels
+constexpr int kSW = kST / 32;
+
+// Padded packed lower storage: row i holds columns 0..i, padded to a
+// multiple of 4 floats, so 32-column segments of a row are 16-byte aligned.
+__host__ __device__ constexpr int prow(int i) {
+  const int q = i >> 2;
+  return 8 * q * (q + 1) + (i - 4 * q) * 4 * (q + 1);
+}
+constexpr int kPtLd = kSmallN3;            // panel scratch: 32 x kPtLd floats
+
+// Blocked right-looking Cholesky of the packed n x n matrix A in shared
+// memory by one CTA (kST threads); 32-wide panels.  Per panel: the diagonal
+// block is factored in shared memory by all threads (outer-product form, one
+// barrier per column), every row below solves its own panel segment by
+// substitution (one thread per row) while the last warp inverts the
+// diagonal block, and the trailing update A -= P P^T runs with 4 x 4
+// register tiles from a transposed copy Pt of the panel.  With inv_diag
+// the diagonal blocks are left holding L_kk^-1 (for the solves below);
+// Lout (row-major, leading dimension ldo), if given, receives the plain
+// diagonal blocks.  Loops stay rolled: straight-line code this size would
+// run out of the instruction cache.
+__device__ void cta_chol_packed(float* A, int n, float* Pt, int* info, bool inv_diag, float* Lout,
+                                int ldo, float* DIout) {
+  __shared__ float Ds[32][33];
+  __shared__ float Li[32][33];
+  __shared__ float dv[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0), k1 = k0 + kb, m = n - k1;
+    for (int e = tid; e < 32 * 32; e += kST) {
+      const int i = e >> 5, j = e & 31;
+      Ds[i][j] = (i < kb && j <= i) ? A[prow(k0 + i) + k0 + j] : 0.f;
+    }
+    __syncthreads();
+    // outer-product elimination on the unscaled block: after step j,
+    // Ds[i][c] (c > j) holds the Schur complement; Ds[.][j] is scaled below.
+    // Thread (r, c) with r = tid / 32 owns rows r and r + 16 of column c.
+    {
+      const int r0 = tid >> 5, c = lane;
+      for (int j = 0; j < kb; ++j) {
+        const float inv = 1.f / Ds[j][j];
+        if (c > j) {
+          const float lcj = Ds[c][j] * inv;
+          if (r0 >= c) Ds[r0][c] -= Ds[r0][j] * lcj;
+          if (r0 + 16 >= c) Ds[r0 + 16][c] -= Ds[r0 + 16][j] * lcj;
+        }
+        __syncthreads();
+      }
+    }
+    if (tid < kb) {
+      float d = Ds[tid][tid];
+      if (!(d > 0.f)) {
+        atomicOr(info, 1);
+        d = 1.f;
+        Ds[tid][tid] = 1.f;
+      }
+      float rs = rsqrtf(d);
+      rs = rs * (1.5f - 0.5f * d * rs * rs);
+      dv[tid] = rs;
+    } else if (tid < 32) {
+      dv[tid] = 1.f;        // padding of a last, narrower block
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * 32; e += kST) {
+      const int i = e >> 5, j = e & 31;
+      if (j < i) Ds[i][j] *= dv[j];
+    }
+    __syncthreads();
+    if (tid < kb) Ds[tid][tid] = Ds[tid][tid] * dv[tid];    // sqrt(d)
+    __syncthreads();
+    if (Lout) {
+      for (int e = tid; e < kb * 32; e += kST) {
+        const int i = e >> 5, j = e & 31;
+        if (j <= i) Lout[(size_t)(k0 + i) * ldo + k0 + j] = Ds[i][j];
+      }
+    }
+    if (tid < m) {
+      // row k1 + tid: x L_kk^T = a in registers (right-looking, so the
+      // dependent chain is one FMA per column), then its transposed copy
+      float* row = A + prow(k1 + tid) + k0;
+      float x[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) x[l] = row[l];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        x[q] *= dv[q];
+#pragma unroll
+        for (int l = q + 1; l < 32; ++l) x[l] -= x[q] * Ds[l][q];
+      }
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        row[l] = x[l];
+        Pt[l * kPtLd + tid] = x[l];
+      }
+    } else if (wid == kSW - 1) {
+      // Li = L_kk^-1, column `lane` in registers (right-looking)
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        x[i] *= dv[i];
+#pragma unroll
+        for (int l = i + 1; l < 32; ++l) x[l] -= Ds[l][i] * x[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Li[i][lane] = (i >= lane) ? x[i] : 0.f;
+    }
+    __syncthreads();
+    if (m > 0) {
+      // trailing update A -= P P^T, 4 x 4 tiles of the lower triangle
+      const int mb = (m + 3) >> 2, nt = mb * (mb + 1) / 2;
+      for (int t = tid; t < nt; t += kST) {
+        int I = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+        while ((I + 1) * (I + 2) / 2 <= t) ++I;
+        while (I * (I + 1) / 2 > t) --I;
+        const int J = t - I * (I + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          const float4 av = *reinterpret_cast<const float4*>(Pt + l * kPtLd + 4 * I);
+          const float4 bv = *reinterpret_cast<const float4*>(Pt + l * kPtLd + 4 * J);
+          const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] += ar[p] * br[q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int i = 4 * I + p;
+          if (i >= m) break;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * J + q;
+            if (jj <= i) A[prow(k1 + i) + k1 + jj] -= acc[p][q];
+          }
+        }
+      }
+    }
+    // the diagonal block: plain factor, or its inverse for the solves
+    for (int e = tid; e < kb * 32; e += kST) {
+      const int i = e >> 5, j = e & 31;
+      if (j <= i) A[prow(k0 + i) + k0 + j] = inv_diag ? Li[i][j] : Ds[i][j];
+      if (DIout) DIout[(size_t)(k0 >> 5) * 1024 + e] = (j <= i) ? Li[i][j] : 0.f;
+    }
+    __syncthreads();
+  }
+}
+
+// Solve L x = t (TRANS = false) or L^T x = t (TRANS = true) in place for a
+// packed factor, with nr interleaved right-hand sides t[i * nr + r].  The
+// inverted diagonal blocks come from DI (32 x 32 row-major per block) or,
+// when DI is null, from the diagonal blocks of A itself (cta_chol_packed
+// with inv_diag).  The 32-term dot products are unrolled so that their
+// shared-memory loads overlap.
+template <bool TRANS>
+__device__ void cta_trsv_packed(const float* A, const float* DI, int n, float* t, int nr) {
+  __shared__ float xb[32 * 3];
+  __shared__ int rp[32];
+  const int tid = threadIdx.x;
+  const int nblk = (n + 31) / 32;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = TRANS ? nblk - 1 - bi : bi;
+    const int k0 = blk * 32, kb = min(32, n - k0), k1 = k0 + kb;
+    if (tid < 32) rp[tid] = prow(k0 + tid);
+    // x_k = Linv_kk t_k (or Linv_kk^T t_k): one thread per (row, rhs)
+    if (tid < kb * nr) {
+      const int i = tid / nr, r = tid % nr;
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        if (l < kb && (TRANS ? l >= i : l <= i)) {
+          const int rr = TRANS ? l : i, cc = TRANS ? i : l;
+          const float d = DI ? DI[(size_t)blk * 1024 + rr * 32 + cc] : A[prow(k0 + rr) + k0 + cc];
+          acc += d * t[(k0 + l) * nr + r];
+        }
+      }
+      xb[i * nr + r] = acc;
+    }
+    __syncthreads();
+    if (tid < kb * nr) t[k0 * nr + tid] = xb[tid];
+    if (TRANS) {      // rows above: t[j] -= sum_l L[k0 + l][j] x_l
+      for (int e = tid; e < k0 * nr; e += kST) {
+        const int j = e / nr, r = e % nr;
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 0; l < 32; ++l)
+          if (l < kb) acc += A[rp[l] + j] * xb[l * nr + r];
+        t[e] -= acc;
+      }
+    } else {          // rows below: t[i] -= sum_l L[i][k0 + l] x_l (kb = 32 here)
+      for (int e = tid; e < (n - k1) * nr; e += kST) {
+        const int i = k1 + e / nr, r = e % nr;
+        const float4* arow = reinterpret_cast<const float4*>(A + prow(i) + k0);
+        float acc = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < 8; ++l4) {
+          const float4 v = arow[l4];
+          acc += v.x * xb[(4 * l4) * nr + r] + v.y * xb[(4 * l4 + 1) * nr + r] +
+                 v.z * xb[(4 * l4 + 2) * nr + r] + v.w * xb[(4 * l4 + 3) * nr + r];
+        }
+        t[k1 * nr + e] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kSW; ++w) t += red[w];
+  return t;
+}
+
+// k_small_s: S = Sigma^-1[c, c], its factor (plain, row-major into a.S for
+// the products; packed with inverted diagonal blocks into a.spk for the
+// solves) and the block-row lists of B.
+__global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
+  extern __shared__ float smem_f[];
+  const int nc = *a.nc_dev;
+  if (nc == 0 || nc > a.small_lim) return;
+  red_layout(a, nc);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float* P = smem_f;                      // prow(kSmallNc) floats
+  float* Pt = P + prow(kSmallNc);         // 32 x kPtLd
+  if (tid == 0) a.nrm[2] = 0.0;
+  for (int i = wid; i < nc; i += kSW) {
+    const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
+    for (int j = lane; j < nc; j += 32) {
+      const double sv = srow[a.clist[j]];
+      a.S64[(size_t)i * nc + j] = sv;
+      if (j <= i) P[prow(i) + j] = (float)sv;
+    }
+  }
+  for (int i = wid; i < nc; i += kSW) {
+    int base = 0;
+    for (int j0 = 0; j0 < nc; j0 += 32) {
+      const int j = j0 + lane;
+      const bool f = j < nc && a.bocc[(size_t)i * nc + j] != 0;
+      const unsigned msk = __ballot_sync(0xffffffffu, f);
+      if (f) a.list[(size_t)i * nc + base + __popc(msk & ((1u << lane) - 1u))] = j;
+      base += __popc(msk);
+    }
+    if (lane == 0) a.cnt[i] = base;
+  }
+  __syncthreads();
+  // L_s: row-major into a.S (for the grid products), packed plain into
+  // a.spk followed by its inverted diagonal blocks (for the one-CTA solves)
+  cta_chol_packed(P, nc, Pt, a.info, false, nullptr, 0, a.spk + prow(nc));
+  for (int e = tid; e < nc * nc; e += kST) {
+    const int i = e / nc, j = e % nc;
+    a.S[e] = (j <= i) ? P[prow(i) + j] : 0.f;
+  }
+  for (int e = tid; e < prow(nc); e += kST) a.spk[e] = P[e];
+}
+
+// k_small_x (grid): y = B u_c in float64, |y2|^2, X = B (L_s (x) I_3).
+__global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
+  const int nc = *a.nc_dev;
+  if (nc == 0 || nc > a.small_lim) return;
+  red_layout(a, nc);
+  const int n3 = 3 * nc;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int row = gtid; row < n3; row += gsz) {
+    const int i = row / 3;
+    const double* brow = a.Bc + (size_t)row * n3;
+    double acc = 0.0;
+    for (int e = 0; e < a.cnt[i]; ++e) {
+      const int j = a.list[(size_t)i * nc + e];
+      const double* uj = a.u + 3 * (size_t)a.clist[j];
+      acc += brow[3 * j] * uj[0] + brow[3 * j + 1] * uj[1] + brow[3 * j + 2] * uj[2];
+    }
+    a.y[row] = acc;
+  }
+  {
+    double q = 0.0;
+    for (int e = gtid; e < 3 * a.n2; e += gsz) q += (double)a.y2[e] * (double)a.y2[e];
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0 && q != 0.0) atomicAdd(&a.nrm[2], q);
+  }
+  for (int e = gtid; e < n3 * n3; e += gsz) {
+    const int row = e / n3, colx = e % n3;
+    const int i = row / 3, k = colx / 3, b = colx % 3;
+    const double* brow = a.Bc + (size_t)row * n3;
+    float acc = 0.f;
+    for (int q = 0; q < a.cnt[i]; ++q) {
+      const int j = a.list[(size_t)i * nc + q];
+      if (j >= k) acc += (float)brow[3 * j + b] * a.S[(size_t)j * nc + k];
+    }
+    a.X[e] = acc;
+  }
+}
+
+// k_small_n (grid): N = I + (L_s (x) I_3)^T X, lower part, packed.
+__global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
+  const int nc = *a.nc_dev;
+  if (nc == 0 || nc > a.small_lim) return;
+  red_layout(a, nc);
+  const int n3 = 3 * nc;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  for (int e = gtid; e < n3 * n3; e += gsz) {
+    const int row = e / n3, col = e % n3;
+    if (col > row) continue;
+    const int i = row / 3, ax = row % 3;
+    float acc = (row == col) ? 1.f : 0.f;
+    for (int j = i; j < nc; ++j) acc += a.S[(size_t)j * nc + i] * a.X[(size_t)(3 * j + ax) * n3 + col];
+    a.N[prow(row) + col] = acc;        // packed lower, the layout k_small_v factors in
+  }
+}
+
+// q = (L_s (x) I_3)^T p (float; L_s packed plain, in shared memory)
+__device__ void cta_lt_apply_f(const float* Lp, int nc, const double* p, float* q) {
+  for (int e = threadIdx.x; e < 3 * nc; e += kST) {
+    const int i = e / 3, ax = e % 3;
+    float acc = 0.f;
+    for (int j = i; j < nc; ++j) acc += Lp[prow(j) + i] * (float)p[3 * j + ax];
+    q[e] = acc;
+  }
+}
+
+// k_small_v (1 CTA): L_N in shared memory, v = (L_s (x) I)^-T N^-1 (L_s (x) I)^T y
+// and the float64-residual refinement of v (same stopping rule as the
+// cooperative kernel).
+__global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
+  extern __shared__ float smem_f[];
+  __shared__ double red[kSW];
+  const int nc = *a.nc_dev;
+  if (nc == 0 || nc > a.small_lim) return;
+  red_layout(a, nc);
+  const int n3 = 3 * nc;
+  const int tid = threadIdx.x;
+  float* A = smem_f;                      // prow(kSmallN3) floats
+  float* Pt = A + prow(kSmallN3);         // 32 x kPtLd
+  float* t = Pt + 32 * kPtLd;             // n3
+  {   // packed N (padding included: prow(n3) is a multiple of 4)
+    const float4* src = reinterpret_cast<const float4*>(a.N);
+    float4* dst = reinterpret_cast<float4*>(A);
+    for (int e = tid; e < prow(n3) / 4; e += kST) dst[e] = src[e];
+  }
+  __syncthreads();
+  cta_chol_packed(A, n3, Pt, a.info, true, nullptr, 0, nullptr);
+  // L_s (packed plain + inverted diagonal blocks) into the panel scratch
+  float* Ls = Pt;
+  const float* LsDI = Pt + prow(nc);
+  for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
+  __syncthreads();
+  cta_lt_apply_f(Ls, nc, a.y, t);
+  __syncthreads();
+  cta_trsv_packed<false>(A, nullptr, n3, t, 1);
+  cta_trsv_packed<true>(A, nullptr, n3, t, 1);
+  cta_trsv_packed<true>(Ls, LsDI, nc, t, 3);
+  for (int e = tid; e < n3; e += kST) a.v[e] = (double)t[e];
+  __syncthreads();
+  double prev = -1.0;
+  for (int it = 0; it < a.refine; ++it) {
+    // w = S v with S = Sigma^-1[c, c] (x) I_3 in float64 (S gathered by k_small_s)
+    for (int e = tid; e < n3; e += kST) {
+      const int i = e / 3, ax = e % 3;
+      const double* srow = a.S64 + (size_t)i * nc;
+      double acc0 = 0.0, acc1 = 0.0;
+      int j = 0;
+      for (; j + 1 < nc; j += 2) {
+        acc0 += srow[j] * a.v[3 * j + ax];
+        acc1 += srow[j + 1] * a.v[3 * j + 3 + ax];
+      }
+      if (j < nc) acc0 += srow[j] * a.v[3 * j + ax];
+      a.w[e] = acc0 + acc1;
+    }
+    __syncthreads();
+    double r2 = 0.0;
+    for (int row = tid; row < n3; row += kST) {
+      const int i = row / 3;
+      const double* brow = a.Bc + (size_t)row * n3;
+      double acc = 0.0;
+      for (int e = 0; e < a.cnt[i]; ++e) {
+        const int j = a.list[(size_t)i * nc + e];
+        acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
+               brow[3 * j + 2] * a.w[3 * j + 2];
+      }
+      const double rr = a.y[row] - a.v[row] - acc;
+      a.rho[row] = rr;
+      r2 += rr * rr;
+    }
+    r2 = block_sum_d(r2, red);
+    const double ys = __ldcg(a.nrm + 2);
+    if (!(r2 > 1e-14 * ys)) break;
+    if (prev >= 0.0 && !(r2 < 0.25 * prev)) break;
+    prev = r2;
+    cta_lt_apply_f(Ls, nc, a.rho, t);
+    __syncthreads();
+    cta_trsv_packed<false>(A, nullptr, n3, t, 1);
+    cta_trsv_packed<true>(A, nullptr, n3, t, 1);
+    cta_trsv_packed<true>(Ls, LsDI, nc, t, 3);
+    for (int e = tid; e < n3; e += kST) a.v[e] += (double)t[e];
+    __syncthreads();
+  }
+}
+
+constexpr size_t kSmallSmemS = sizeof(float) * ((size_t)prow(kSmallNc) + 32 * kPtLd);
+constexpr size_t kSmallSmemV = sizeof(float) * ((size_t)prow(kSmallN3) + 32 * kPtLd + kSmallN3);
+
 template <typename FT>
 cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, const FT* y2,
                              double* z2, int* info, int num_sms, int refine) {
@@ -431,6 +875,17 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
   a.clist = m.clist; a.Sinv = m.Sinv; a.Bc = m.Bc; a.bocc = m.bocc;
   a.u = u; a.y2 = y2; a.z2 = z2;
   a.info = info;
+  a.small_lim = 0;
+  if constexpr (std::is_same<FT, float>::value) {
+    // one-CTA path for 0 < n_c <= kSmallNc (the kernels exit otherwise)
+    a.small_lim = kSmallNc;
+    ProfScope ps(PROF_CHOL, s);
+    k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
+    k_small_x<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+    k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+    k_small_v<<<1, kST, kSmallSmemV, s>>>(a);
+    count_launch(4);
+  }
   void* args[] = {&a};
   const int grid = std::max(1, num_sms);
   ProfScope ps(PROF_CHOL, s);
@@ -443,9 +898,10 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
 
 int64_t reduced_workspace_elems(int nc) {
   const int64_t n3 = 3 * (int64_t)nc;
-  // S, X, N (+1 row), 1/diag of both factors, two FT vectors, and (at the
-  // tail of the float64 buffer) four float64 vectors
-  return (int64_t)nc * nc + n3 * n3 + (n3 + 1) * n3 + nc + n3 + 2 * n3 + 4 * n3 + 64;
+  // S, X, N (+1 row), 1/diag of both factors, two FT vectors, packed L_s, and
+  // (at the tail of the float64 buffer) four float64 vectors
+  return (int64_t)nc * nc + n3 * n3 + (n3 + 1) * n3 + nc + n3 + 2 * n3 +
+         (prow(nc) + 1024 * ((int64_t)nc + 31) / 32 + 16) + 4 * n3 + (int64_t)nc * nc + 128;
 }
 
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
@@ -455,4 +911,11 @@ cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, con
   return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4);
 }
 
+}  // namespace fsim
+
+namespace fsim {
+void set_reduced_smem_limits() {
+  cudaFuncSetAttribute(k_small_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemS);
+  cudaFuncSetAttribute(k_small_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemV);
+}
 }  // namespace fsim

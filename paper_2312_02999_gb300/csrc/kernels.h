@@ -69,7 +69,8 @@ struct DevMesh {
   float* uf = nullptr;        // n2*3 (mixed)
   float* rf = nullptr;        // nf*3 (mixed)
   // contact work
-  int64_t cap = 0;            // pair capacity
+  int64_t cap = 0;            // capacity of the near-pair and CCD candidate lists
+  int64_t cap_act = 0;        // capacity of the constraint set C (pairs, per-pair derivatives)
   unsigned long long* pairs = nullptr;    // keys (type<<62 | i<<31 | j)
   unsigned long long* cand = nullptr;     // CCD candidates
   int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite [5] touching
@@ -147,6 +148,7 @@ int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the 
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
                           double* z2, int* info, int num_sms, int precision);
 void set_solver_smem_limits(int max_bytes);
+void set_reduced_smem_limits();
 
 // ---- misc ------------------------------------------------------------------
 void launch_axpy_positions(cudaStream_t s, int n3, const double* x, const double* dx,

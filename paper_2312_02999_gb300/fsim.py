@@ -43,7 +43,8 @@ class Params(C.Structure):
     _fields_ = [("weight_scale", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double),
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
-                ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64)]
+                ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
+                ("active_capacity", C.c_int64)]
 
 
 class FrameStats(C.Structure):

@@ -280,6 +280,14 @@ def test_error_paths(fsim, ctx):
     # a context stays usable after the errors
     rc, st = m2.solve_frame(x_init=mesh.rest, check=False)
     assert rc == fsim.FSIM_ECONTACT_OVERFLOW
+    # more active pairs (d < dhat) than the constraint-set capacity
+    m3, _ = _pair(fsim, ctx, mesh, act, active_capacity=2)
+    x = mesh.rest.copy()
+    x[top & (mesh.pinned == 0), 2] -= 0.0045        # gap 0.0005 < dhat everywhere
+    rc, _ = m3.solve_frame(x_init=x, check=False)
+    assert rc == fsim.FSIM_ECONTACT_OVERFLOW
+    rc, _ = m.solve_frame(x_init=x, check=False)    # the default capacity holds them
+    assert rc in (fsim.FSIM_OK, fsim.FSIM_ENOT_CONVERGED)
 
 
 def test_kappa_auto_matches_oracle(fsim, ctx):
