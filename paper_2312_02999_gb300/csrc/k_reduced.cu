@@ -448,8 +448,11 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
 //   k_small_v   (1 CTA)  L_N, v = L^-T N^-1 L^T y and its float64 refinement
 // then the cooperative kernel runs only its z2 update.
 // ---------------------------------------------------------------------------
-constexpr int kSmallNc = 96;               // 3 n_c <= 288 fits in shared memory
+constexpr int kSmallNc = 96;               // 3 n_c <= 288 fits in one CTA's shared memory
 constexpr int kSmallN3 = 3 * kSmallNc;
+constexpr int kClusNc = 128;               // 3 n_c <= 384 fits in a 4-CTA cluster
+constexpr int kClusN3 = 3 * kClusNc;
+constexpr int kCl = 4;                     // CTAs per cluster
 constexpr int kST = 512;                   // threads of the one-CTA kernels
 constexpr int kSW = kST / 32;
 
@@ -684,8 +687,8 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
   if (nc == 0 || nc > a.small_lim) return;
   red_layout(a, nc);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float* P = smem_f;                      // prow(kSmallNc) floats
-  float* Pt = P + prow(kSmallNc);         // 32 x kPtLd
+  float* P = smem_f;                      // prow(kClusNc) floats
+  float* Pt = P + prow(kClusNc);          // 32 x kPtLd
   if (tid == 0) a.nrm[2] = 0.0;
   for (int i = wid; i < nc; i += kSW) {
     const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
@@ -789,7 +792,7 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   extern __shared__ float smem_f[];
   __shared__ double red[kSW];
   const int nc = *a.nc_dev;
-  if (nc == 0 || nc > a.small_lim) return;
+  if (nc == 0 || nc > kSmallNc) return;
   red_layout(a, nc);
   const int n3 = 3 * nc;
   const int tid = threadIdx.x;
@@ -860,7 +863,378 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   }
 }
 
-constexpr size_t kSmallSmemS = sizeof(float) * ((size_t)prow(kSmallNc) + 32 * kPtLd);
+// ---------------------------------------------------------------------------
+// k_clus_v: the same solve for kSmallNc < n_c <= kClusNc on a cluster of kCl
+// CTAs.  32-row blocks of the packed N are spread block-cyclically over the
+// CTAs' shared memory; the owner of a panel factors its diagonal block and
+// the others read it (with its inverse) through distributed shared memory;
+// each CTA solves and updates only its own rows, after gathering the whole
+// panel from the other CTAs.  The triangular solves pass 32-value blocks
+// through distributed shared memory with one cluster barrier per block, and
+// the float64 residuals of the refinement are split over the CTAs.
+// ---------------------------------------------------------------------------
+constexpr int kClusRowsMax = 32 * ((kClusN3 / 32 + kCl - 1) / kCl);   // own rows per CTA
+// largest packed storage of the rows one CTA owns (padded row lengths)
+constexpr int clus_aloc() {
+  int mx = 0;
+  for (int rank = 0; rank < kCl; ++rank) {
+    int tot = 0;
+    for (int b = rank; b < kClusN3 / 32; b += kCl)
+      for (int rr = 0; rr < 32; ++rr) tot += 4 * ((32 * b + rr + 4) / 4);
+    mx = tot > mx ? tot : mx;
+  }
+  return mx + 64;
+}
+constexpr int kClusALoc = clus_aloc();
+static_assert(kClusALoc % 4 == 0, "panel scratch must stay 16-byte aligned");
+constexpr size_t kClusSmem =
+    sizeof(float) * ((size_t)kClusALoc + 32 * (size_t)kClusN3 + (size_t)prow(kClusNc) +
+                     1024 * (kClusNc / 32) + 2 * (size_t)kClusN3);
+
+__global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
+  namespace cgx = cooperative_groups;
+  cgx::cluster_group cl = cgx::this_cluster();
+  extern __shared__ float smem_f[];
+  __shared__ float Ds[32][33];
+  __shared__ float Li[32][33];
+  __shared__ float dv[32];
+  __shared__ float xb[2][32];
+  __shared__ float part[2][kCl][32];
+  __shared__ double nrm_parts[kCl];
+  __shared__ float wsum[kSW][32];
+  __shared__ int loff[kClusRowsMax];
+  __shared__ double red[kSW];
+  const int nc = *a.nc_dev;
+  if (nc <= kSmallNc || nc > kClusNc) return;       // uniform over the cluster
+  red_layout(a, nc);
+  const int n3 = 3 * nc, nblk = (n3 + 31) / 32;
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float* A = smem_f;                               // own rows, packed
+  float* Pt = A + kClusALoc;                       // 32 x kClusN3, panel by global row - k1
+  float* Ls = Pt + 32 * kClusN3;                   // L_s packed plain, then inverted blocks
+  float* LsDI = Ls + prow(nc);
+  float* t = Ls + prow(kClusNc) + 1024 * (kClusNc / 32);   // n3: rhs / solution (own rows valid)
+  float* xg = t + kClusN3;                         // n3: gathered solution (rank 0)
+  // own rows: block b is owned by b % kCl; local row lb * 32 + (r % 32)
+  auto own = [&](int r) { return ((r >> 5) % kCl) == rank; };
+  auto lrow = [&](int r) { return ((r >> 5) / kCl) * 32 + (r & 31); };
+  if (tid < kClusRowsMax) {
+    int off = 0;
+    for (int lr = 0; lr < tid; ++lr) {
+      const int r = ((lr >> 5) * kCl + rank) * 32 + (lr & 31);
+      off += 4 * ((r + 4) / 4);                    // padded length of row r
+    }
+    loff[tid] = off;
+  }
+  __syncthreads();
+  auto Ael = [&](int r, int c) -> float& { return A[loff[lrow(r)] + c]; };
+  // load own rows of the packed N and L_s
+  for (int b = rank; b < nblk; b += kCl)
+    for (int e = tid; e < 32 * 32 * (b + 1); e += kST) {
+      const int rr = e / (32 * (b + 1)), c = e % (32 * (b + 1));
+      const int r = b * 32 + rr;
+      if (r < n3 && c <= r) Ael(r, c) = a.N[prow(r) + c];
+    }
+  for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
+  __syncthreads();
+
+  // ---- Cholesky of N over the cluster --------------------------------------
+  for (int k = 0; k < nblk; ++k) {
+    const int k0 = 32 * k, kb = min(32, n3 - k0), k1 = k0 + kb, m = n3 - k1;
+    const int owner = k % kCl;
+    if (rank == owner) {
+      for (int e = tid; e < 32 * 32; e += kST) {
+        const int i = e >> 5, j = e & 31;
+        Ds[i][j] = (i < kb && j <= i) ? Ael(k0 + i, k0 + j) : 0.f;
+      }
+      __syncthreads();
+      {
+        const int r0 = tid >> 5, c = lane;
+        for (int j = 0; j < kb; ++j) {
+          const float inv = 1.f / Ds[j][j];
+          if (c > j) {
+            const float lcj = Ds[c][j] * inv;
+            if (r0 >= c) Ds[r0][c] -= Ds[r0][j] * lcj;
+            if (r0 + 16 >= c) Ds[r0 + 16][c] -= Ds[r0 + 16][j] * lcj;
+          }
+          __syncthreads();
+        }
+      }
+      if (tid < kb) {
+        float d = Ds[tid][tid];
+        if (!(d > 0.f)) {
+          atomicOr(a.info, 1);
+          d = 1.f;
+          Ds[tid][tid] = 1.f;
+        }
+        float rs = rsqrtf(d);
+        rs = rs * (1.5f - 0.5f * d * rs * rs);
+        dv[tid] = rs;
+      } else if (tid < 32) {
+        dv[tid] = 1.f;
+      }
+      __syncthreads();
+      for (int e = tid; e < kb * 32; e += kST) {
+        const int i = e >> 5, j = e & 31;
+        if (j < i) Ds[i][j] *= dv[j];
+      }
+      __syncthreads();
+      if (tid < kb) Ds[tid][tid] = Ds[tid][tid] * dv[tid];
+      __syncthreads();
+      if (wid == 0) {
+        float x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          x[i] *= dv[i];
+#pragma unroll
+          for (int l = i + 1; l < 32; ++l) x[l] -= Ds[l][i] * x[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Li[i][lane] = (i >= lane) ? x[i] : 0.f;
+      }
+    }
+    cl.sync();
+    if (rank != owner) {     // the owner's diagonal factor, its inverse and 1/diag
+      const float* rD = cl.map_shared_rank(&Ds[0][0], owner);
+      const float* rL = cl.map_shared_rank(&Li[0][0], owner);
+      const float* rv = cl.map_shared_rank(&dv[0], owner);
+      for (int e = tid; e < 32 * 33; e += kST) {
+        (&Ds[0][0])[e] = rD[e];
+        (&Li[0][0])[e] = rL[e];
+      }
+      if (tid < 32) dv[tid] = rv[tid];
+    }
+    __syncthreads();
+    // own panel rows: x L_kk^T = a (registers), into A and the panel copy;
+    // one warp per own block below the panel
+    for (int idx = tid; idx < kClusRowsMax; idx += kST) {
+      const int b = ((idx >> 5) * kCl) + rank;
+      const int r = 32 * b + (idx & 31);
+      if (b > k && r < n3) {
+        float* row = &Ael(r, k0);
+        float x[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) x[l] = row[l];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          x[q] *= dv[q];
+#pragma unroll
+          for (int l = q + 1; l < 32; ++l) x[l] -= x[q] * Ds[l][q];
+        }
+#pragma unroll
+        for (int l = 0; l < 32; ++l) {
+          row[l] = x[l];
+          Pt[l * kClusN3 + (r - k1)] = x[l];
+        }
+      }
+    }
+    cl.sync();
+    // gather the other CTAs' panel rows
+    for (int q = 0; q < kCl; ++q) {
+      if (q == rank) continue;
+      const float* rP = cl.map_shared_rank(Pt, q);
+      for (int b = q; b < nblk; b += kCl) {
+        if (b <= k) continue;
+        const int rows = min(32, n3 - 32 * b);
+        for (int e = tid; e < 32 * rows; e += kST) {
+          const int l = e / rows, rr = 32 * b + e % rows - k1;
+          Pt[l * kClusN3 + rr] = rP[l * kClusN3 + rr];
+        }
+      }
+    }
+    __syncthreads();
+    // trailing update of own rows: A(i, j) -= P_i . P_j, 4 x 4 tiles
+    if (m > 0) {
+      const int mb = (m + 3) >> 2, nt = mb * (mb + 1) / 2;
+      for (int tt = tid; tt < nt; tt += kST) {
+        int I = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
+        while ((I + 1) * (I + 2) / 2 <= tt) ++I;
+        while (I * (I + 1) / 2 > tt) --I;
+        if (!own(k1 + 4 * I)) continue;            // 4-row tiles never straddle a block
+        const int J = tt - I * (I + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          const float4 av = *reinterpret_cast<const float4*>(Pt + l * kClusN3 + 4 * I);
+          const float4 bv = *reinterpret_cast<const float4*>(Pt + l * kClusN3 + 4 * J);
+          const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] += ar[p] * br[q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int i = 4 * I + p;
+          if (i >= m) break;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = 4 * J + q;
+            if (jj <= i) Ael(k1 + i, k1 + jj) -= acc[p][q];
+          }
+        }
+      }
+    }
+    if (rank == owner)
+      for (int e = tid; e < kb * 32; e += kST) {
+        const int i = e >> 5, j = e & 31;
+        if (j <= i) Ael(k0 + i, k0 + j) = Li[i][j];    // inverted diagonal block
+      }
+    __syncthreads();
+  }
+  cl.sync();
+
+  // ---- distributed solves with L_N (own rows of t hold the values) ---------
+  auto solve_n = [&]() {
+    // forward: L x = t
+    for (int k = 0; k < nblk; ++k) {
+      const int k0 = 32 * k, kb = min(32, n3 - k0), owner = k % kCl, buf = k & 1;
+      if (rank == owner) {
+        if (tid < kb) {
+          float acc = 0.f;
+          for (int l = 0; l <= tid; ++l) acc += Ael(k0 + tid, k0 + l) * t[k0 + l];
+          xb[buf][tid] = acc;
+        }
+        __syncthreads();
+        if (tid < kb) {
+          t[k0 + tid] = xb[buf][tid];
+          for (int q = 0; q < kCl; ++q)
+            if (q != rank) cl.map_shared_rank(&xb[buf][0], q)[tid] = xb[buf][tid];
+        }
+      }
+      cl.sync();
+      for (int idx = tid; idx < kClusRowsMax; idx += kST) {
+        const int b = ((idx >> 5) * kCl) + rank;
+        const int r = 32 * b + (idx & 31);
+        if (b > k && r < n3) {
+          const float* row = &Ael(r, k0);
+          float acc = 0.f;
+#pragma unroll
+          for (int l = 0; l < 32; ++l) acc += row[l] * xb[buf][l];
+          t[r] -= acc;
+        }
+      }
+      __syncthreads();
+    }
+    // backward: L^T x = t
+    for (int k = nblk - 1; k >= 0; --k) {
+      const int k0 = 32 * k, kb = min(32, n3 - k0), owner = k % kCl, buf = k & 1;
+      // partial sums over own rows below block k for its columns: warp w
+      // takes own rows w, w + 16, ...; lane = column
+      {
+        float acc = 0.f;
+        if (lane < kb)
+          for (int idx = wid; idx < kClusRowsMax; idx += kSW) {
+            const int b = ((idx >> 5) * kCl) + rank;
+            const int r = 32 * b + (idx & 31);
+            if (b > k && r < n3) acc += Ael(r, k0 + lane) * t[r];
+          }
+        wsum[wid][lane] = acc;
+        __syncthreads();
+        if (tid < 32) {
+          float tot = 0.f;
+          for (int w = 0; w < kSW; ++w) tot += wsum[w][tid];
+          cl.map_shared_rank(&part[buf][0][0], owner)[rank * 32 + tid] = tot;
+        }
+      }
+      cl.sync();
+      if (rank == owner) {
+        if (tid < kb) {
+          float s = t[k0 + tid];
+          for (int q = 0; q < kCl; ++q) s -= part[buf][q][tid];
+          xb[buf][tid] = s;
+        }
+        __syncthreads();
+        if (tid < kb) {
+          float acc = 0.f;
+          for (int l = tid; l < kb; ++l) acc += Ael(k0 + l, k0 + tid) * xb[buf][l];
+          t[k0 + tid] = acc;
+        }
+        __syncthreads();
+      }
+    }
+    cl.sync();
+  };
+  // (L_s (x) I)^-T on the gathered solution (rank 0), result into a.v / added to it
+  auto finish = [&](bool add) {
+    if (rank == 0) {
+      for (int q = 0; q < kCl; ++q) {
+        const float* rt = (q == 0) ? t : cl.map_shared_rank(t, q);
+        for (int b = q; b < nblk; b += kCl)
+          for (int e = tid; e < 32; e += kST)
+            if (32 * b + e < n3) xg[32 * b + e] = rt[32 * b + e];
+      }
+      __syncthreads();
+      cta_trsv_packed<true>(Ls, LsDI, nc, xg, 3);
+      for (int e = tid; e < n3; e += kST) a.v[e] = (add ? a.v[e] : 0.0) + (double)xg[e];
+    }
+    cl.sync();
+  };
+  // t = (L_s (x) I_3)^T p on own rows
+  auto lt_own = [&](const double* p) {
+    for (int b = rank; b < nblk; b += kCl)
+      for (int e = tid; e < 32; e += kST) {
+        const int r = 32 * b + e;
+        if (r >= n3) continue;
+        const int i = r / 3, ax = r % 3;
+        float acc = 0.f;
+        for (int j = i; j < nc; ++j) acc += Ls[prow(j) + i] * (float)p[3 * j + ax];
+        t[r] = acc;
+      }
+    __syncthreads();
+  };
+  lt_own(a.y);
+  solve_n();
+  finish(false);
+
+  // ---- float64 refinement, rows split over the cluster ----------------------
+  double prev = -1.0;
+  for (int it = 0; it < a.refine; ++it) {
+    for (int e = rank * kST + tid; e < n3; e += kCl * kST) {
+      const int i = e / 3, ax = e % 3;
+      const double* srow = a.S64 + (size_t)i * nc;
+      double acc = 0.0;
+      for (int j = 0; j < nc; ++j) acc += srow[j] * a.v[3 * j + ax];
+      a.w[e] = acc;
+    }
+    cl.sync();
+    double r2 = 0.0;
+    for (int row = rank * kST + tid; row < n3; row += kCl * kST) {
+      const int i = row / 3;
+      const double* brow = a.Bc + (size_t)row * n3;
+      double acc = 0.0;
+      for (int e = 0; e < a.cnt[i]; ++e) {
+        const int j = a.list[(size_t)i * nc + e];
+        acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
+               brow[3 * j + 2] * a.w[3 * j + 2];
+      }
+      const double rr = a.y[row] - a.v[row] - acc;
+      a.rho[row] = rr;
+      r2 += rr * rr;
+    }
+    r2 = block_sum_d(r2, red);
+    if (tid < kCl) cl.map_shared_rank(&nrm_parts[0], tid)[rank] = r2;
+    cl.sync();
+    double tot = 0.0;
+    for (int q = 0; q < kCl; ++q) tot += nrm_parts[q];     // same order everywhere
+    const double ys = __ldcg(a.nrm + 2);
+    if (!(tot > 1e-14 * ys)) break;
+    if (prev >= 0.0 && !(tot < 0.25 * prev)) break;
+    prev = tot;
+    lt_own(a.rho);
+    solve_n();
+    finish(true);
+  }
+}
+
+constexpr size_t kSmallSmemS = sizeof(float) * ((size_t)prow(kClusNc) + 32 * kPtLd);
 constexpr size_t kSmallSmemV = sizeof(float) * ((size_t)prow(kSmallN3) + 32 * kPtLd + kSmallN3);
 
 template <typename FT>
@@ -877,14 +1251,31 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
   a.info = info;
   a.small_lim = 0;
   if constexpr (std::is_same<FT, float>::value) {
-    // one-CTA path for 0 < n_c <= kSmallNc (the kernels exit otherwise)
-    a.small_lim = kSmallNc;
+    // one-CTA path for 0 < n_c <= kSmallNc, 4-CTA cluster for n_c <= kClusNc
+    // (the kernels exit otherwise)
+    a.small_lim = kClusNc;
     ProfScope ps(PROF_CHOL, s);
     k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
     k_small_x<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
     k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
     k_small_v<<<1, kST, kSmallSmemV, s>>>(a);
-    count_launch(4);
+    {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kCl);
+      cfg.blockDim = dim3(kST);
+      cfg.dynamicSmemBytes = kClusSmem;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kCl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_clus_v, a);
+      if (e != cudaSuccess) return e;
+    }
+    count_launch(5);
   }
   void* args[] = {&a};
   const int grid = std::max(1, num_sms);
@@ -917,5 +1308,6 @@ namespace fsim {
 void set_reduced_smem_limits() {
   cudaFuncSetAttribute(k_small_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemS);
   cudaFuncSetAttribute(k_small_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemV);
+  cudaFuncSetAttribute(k_clus_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusSmem);
 }
 }  // namespace fsim

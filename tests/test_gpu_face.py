@@ -90,11 +90,13 @@ def test_face_contact_set_and_local_step(face):
     assert abs(E - OF.elastic_energy(F, Po, pr.w)) <= 1e-10 * E
 
 
-def test_face_global_step_backward_error(face):
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-4)])
+def test_face_global_step_backward_error(face, prec, tol):
     mesh, m, pr = face["mesh"], face["m"], face["pr"]
     x, _ = face["fp64"]
-    # a contact state between converged frames: half-way to a harder actuation
-    dx = m.eval_global_step(x, precision=0)
+    # the converged contact state of frame 30 (n_c there exercises the
+    # multi-CTA reduced solve of the mixed form)
+    dx = m.eval_global_step(x, precision=prec)
     ev = pr.evaluate(x)
     assert ev["C"][0].size > 0
     g = pr.gradient(x, ev).ravel()[pr.free_dofs]
@@ -103,5 +105,7 @@ def test_face_global_step_backward_error(face):
     # cond(H) of the face is ~1.6e3, but stiff contact pairs make the low-rank
     # correction z2 = u - Sigma^-1 Q^T v a difference of two large terms, so
     # the backward error of this (not backward-stable) route is well above
-    # eps; measured 1.9e-7.  The outer loop's float64 gradient absorbs it.
-    assert res <= 1e-6, res
+    # eps; measured 1.9e-7 in float64.  The mixed form's float32 solves of
+    # K11 and Sigma bound it near 1e-5 (same bound as the slab test).  The
+    # outer loop's float64 gradient absorbs either.
+    assert res <= tol, res
