@@ -84,6 +84,12 @@ typedef struct {
                                max(2^16, 16 * proxy triangles), at most
                                contact_capacity.  More pairs than either
                                capacity return FSIM_ECONTACT_OVERFLOW         */
+  double skin;              /* width of the contact candidate list: pairs within
+                               d0 + skin are kept and the all-pairs sweep is
+                               repeated only after proxy vertices moved about
+                               skin / 2 (results are the same as sweeping
+                               every time); <= 0 selects max(10 d0, a quarter
+                               of the mean proxy edge length at rest)        */
 } fsim_params;
 
 /* Per-frame statistics filled by fsim_solve_frame. */
@@ -105,8 +111,8 @@ typedef struct {
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
- * coop_ctas 0, contact_capacity and active_capacity auto.  dhat must still
- * be set by the caller. */
+ * coop_ctas 0, contact_capacity, active_capacity and skin auto.  dhat must
+ * still be set by the caller. */
 fsim_status fsim_default_params(fsim_params* p);
 
 /* Create a context on CUDA device `device`; it owns one CUDA stream and all

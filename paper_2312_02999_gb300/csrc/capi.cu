@@ -154,6 +154,7 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.sf, 3 * Ns, bytes));
   TRY(dalloc(al, &m.dsf, 3 * Ns, bytes));
   TRY(dalloc(al, &m.counters, kCounters, bytes));
+  CK(cudaMemset(m.counters, 0, sizeof(int) * kCounters));   // skin list starts invalid
   TRY(dalloc(al, &m.scal, kScal, bytes));
   TRY(dalloc(al, &m.partials, (size_t)m.n_partials, bytes));
   TRY(dalloc(al, &m.y1, 3 * (size_t)std::max(m.n1, 1), bytes));
@@ -165,6 +166,8 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.pairs, (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.cand, (size_t)m.cap, bytes));
   TRY(dalloc(al, &m.nearl, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.vlist, (size_t)m.cap, bytes));
+  TRY(dalloc(al, &m.sb, 3 * Ns, bytes));
   TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.x2mark, (size_t)std::max(m.n2, 1), bytes));
@@ -435,6 +438,7 @@ fsim_status fsim_default_params(fsim_params* p) {
   p->accd_max_iters = 2000;
   p->contact_capacity = 0;
   p->active_capacity = 0;
+  p->skin = 0.0;
   return FSIM_OK;
 }
 
@@ -568,6 +572,21 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
     double mx = 0.0;
     for (int64_t k = 0; k < 3 * n; ++k) mx = std::max(mx, std::fabs(rest_xyz[k]));
     m.coord_scale = 2.0 * std::max(mx, 1e-30);
+    // mean proxy edge length at rest (the default skin of the contact list)
+    std::vector<double> sr(3 * (size_t)std::max<int64_t>(Ns, 1), 0.0);
+    for (int64_t r = 0; r < Ns; ++r)
+      for (int64_t e = W_rowptr[r]; e < W_rowptr[r + 1]; ++e)
+        for (int d = 0; d < 3; ++d) sr[3 * r + d] += W_val[e] * rest_xyz[3 * (int64_t)W_col[e] + d];
+    double sum = 0.0;
+    for (size_t k = 0; k < ed.size(); ++k) {
+      double l2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double q = sr[3 * ed[k].first + d] - sr[3 * ed[k].second + d];
+        l2 += q * q;
+      }
+      sum += std::sqrt(l2);
+    }
+    ms.mean_edge = ed.empty() ? 0.0 : sum / (double)ed.size();
   }
   m.n_partials = std::max(elastic_blocks(m.T), gnorm_blocks(m.n)) + 16;
   CK(cudaStreamSynchronize(s));
@@ -668,6 +687,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   }
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
                                   : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
+  m.skin = p->skin > 0.0 ? p->skin : std::max(10.0 * p->dhat, 0.25 * ms.mean_edge);
   m.cap_act = p->active_capacity > 0 ? p->active_capacity
                                      : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));
   m.cap_act = std::min(m.cap_act, m.cap);

@@ -582,13 +582,16 @@ struct SweepArgs {
   int* count;
   int* overflow;
   int64_t cap;
+  const int* gate;              // if set, the sweep runs only when *gate != 0
 };
 
 // MODE 0: pairs whose float32 distance is within `near` (a superset of the
 // d < dhat pairs; decided in float64 by k_near_pairs).  MODE 1: CCD
 // candidates, whose swept boxes (+dhat) overlap by the exact float64 test.
+// (The skin list is built with MODE 0 and a wider `near`.)
 template <int MODE>
 __global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
+  if (a.gate && *a.gate == 0) return;
   __shared__ float tb[kTile][6];
   __shared__ int tid3[kTile][3];
   __shared__ unsigned long long tk[MODE == 1 ? kTile : 1][6];
@@ -637,6 +640,7 @@ __global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
 template <int MODE>
 __global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
   if (blockIdx.y < blockIdx.x) return;        // tiles with j-tile >= i-tile
+  if (a.gate && *a.gate == 0) return;
   __shared__ float eb[kTile][6];
   __shared__ int eid[kTile][2];
   __shared__ unsigned long long ek[MODE == 1 ? kTile : 1][6];
@@ -759,6 +763,105 @@ __global__ void k_accd_list(const int* __restrict__ cand_count, int64_t cap,
 }
 
 // ---------------------------------------------------------------------------
+// Skin (Verlet) list.  The all-pairs sweep runs only when proxy vertices
+// have moved far since the last build: the list holds every pair whose
+// float32 distance at the build positions sb was within dhat + skin.  A
+// pair's distance changes by at most the sum of its two largest vertex
+// displacements, so while 2 max|s - sb| <= skin - margin every pair with
+// d(s) < dhat is in the list (the constraint set is unchanged), and while
+// 2 (max|s - sb| + max|ds|) <= 0.4 skin no pair outside it can come within
+// s_ccd d0 of contact during the step (the CCD bound is unchanged).
+// counters: [10] list length, [11] rebuild now, [12] list valid,
+// [13] CCD needs the full sweep, [14] list overflow.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_max_d(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;   // valid in thread 0
+}
+
+// one CTA: decide whether the skin list must be rebuilt (detection) or the
+// CCD step needs the full sweep (ds != nullptr); a rebuild records sb = s
+__global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __restrict__ sb,
+                             const double* __restrict__ ds, double skin, double margin,
+                             int* counters) {
+  double dmax = 0.0, smax = 0.0;
+  for (int v = threadIdx.x; v < Ns; v += blockDim.x) {
+    double d2 = 0.0, q2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double e = s[3 * v + d] - sb[3 * v + d];
+      d2 += e * e;
+      if (ds) q2 += ds[3 * v + d] * ds[3 * v + d];
+    }
+    dmax = fmax(dmax, sqrt(d2));
+    smax = fmax(smax, sqrt(q2));
+  }
+  dmax = block_max_d(dmax);
+  __syncthreads();
+  smax = block_max_d(smax);
+  __shared__ int rebuild;
+  if (threadIdx.x == 0) {
+    const bool valid = counters[12] == 1 && counters[14] == 0;
+    if (ds) {
+      counters[13] = (valid && 2.0 * (dmax + smax) <= 0.4 * skin) ? 0 : 1;
+      rebuild = 0;
+    } else {
+      rebuild = (valid && 2.0 * dmax <= skin - margin) ? 0 : 1;
+      counters[11] = rebuild;
+      if (rebuild) { counters[10] = 0; counters[12] = 1; counters[14] = 0; }
+    }
+  }
+  __syncthreads();
+  if (rebuild)
+    for (int e = threadIdx.x; e < 3 * Ns; e += blockDim.x) sb[e] = s[e];
+}
+
+// near list from the skin list: float32 distance at the current positions
+__global__ void k_skin_near(const int* __restrict__ counters, int64_t cap,
+                            const unsigned long long* __restrict__ vlist, const float* __restrict__ sf,
+                            const int* __restrict__ tris, const int* __restrict__ edges, float near,
+                            unsigned long long* __restrict__ nearl, int* count, int* overflow) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && counters[14]) atomicOr(overflow, 1);   // list incomplete
+  int64_t n = counters[10];
+  n = n < cap ? n : cap;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int type, i, j;
+    unpack_key(vlist[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    float X[4][3];
+    gather_Xf(sf, V, X);
+    if (pair_distance_f(type, X) <= near) append(vlist[p], nearl, count, overflow, cap);
+  }
+}
+
+// CCD candidates from the skin list (when counters[13] == 0): the exact
+// float64 swept-box test of the full sweep
+__global__ void k_skin_cand(int* counters, int64_t cap, const unsigned long long* __restrict__ vlist,
+                            const unsigned long long* __restrict__ key, int Ns, int Nt,
+                            unsigned long long* __restrict__ cand) {
+  if (counters[13] != 0) return;
+  int64_t n = counters[10];
+  n = n < cap ? n : cap;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int type, i, j;
+    unpack_key(vlist[p], type, i, j);
+    const unsigned long long* ka = key + 12 * (size_t)(type == 0 ? i : Ns + Nt + i);
+    const unsigned long long* kb = key + 12 * (size_t)(type == 0 ? Ns + j : Ns + Nt + j) + 6;
+    if (ov64(ka, kb)) append(vlist[p], cand, counters + 1, counters + 9, cap);
+  }
+}
+
+// ---------------------------------------------------------------------------
 void launch_proxy(cudaStream_t st, const DevMesh& m, const double* x, double* sp) {
   k_proxy<<<(m.Ns + 255) / 256, 256, 0, st>>>(m.Ns, m.Wptr, m.Wcol, m.Wval, x, sp);
   count_launch();
@@ -766,11 +869,13 @@ void launch_proxy(cudaStream_t st, const DevMesh& m, const double* x, double* sp
 
 namespace {
 int nprim(const DevMesh& m) { return m.Ns + m.Nt + m.Ne; }
+// float32 rounding allowance of the skin tests (as for the CCD early-out)
+double skin_margin(const DevMesh& m, double dhat) { return fmax(0.01 * dhat, 1e-5 * m.coord_scale); }
 
 void launch_sweeps(cudaStream_t st, const DevMesh& m, int mode, unsigned long long* out, int* count,
-                   int* overflow, float nearf) {
+                   int* overflow, float nearf, const int* gate) {
   SweepArgs a{m.Ns, m.Nt, m.Ne, m.pbox, m.pkey, m.sf, m.tris, m.edges, nearf, out, count, overflow,
-              m.cap};
+              m.cap, gate};
   if (m.Ns > 0 && m.Nt > 0) {
     dim3 gpt((m.Ns + kTile - 1) / kTile, (m.Nt + kTile - 1) / kTile);
     if (mode == 0) k_sweep_pt<0><<<gpt, kTile, 0, st>>>(a);
@@ -793,13 +898,20 @@ void launch_detect(cudaStream_t st, const DevMesh& m, const double* sp, double d
   ProfScope ps(PROF_DETECT, st);
   const int np = nprim(m);
   if (np == 0) return;
-  k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, nullptr, m.tris, m.edges, dhat,
+  // boxes inflated for a skin-list build (used only when it runs)
+  const double pad = dhat + m.skin;
+  const float margin = (float)skin_margin(m, dhat);
+  k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, nullptr, m.tris, m.edges, pad,
                                                 m.pbox, m.pkey, m.sf, nullptr);
-  launch_sweeps(st, m, 0, m.nearl, m.counters + 8, m.counters + 2, 2.0f * (float)dhat);
+  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, nullptr, m.skin, margin, m.counters);
+  launch_sweeps(st, m, 0, m.vlist, m.counters + 10, m.counters + 14, (float)pad + margin,
+                m.counters + 11);
+  k_skin_near<<<2 * 152, 128, 0, st>>>(m.counters, m.cap, m.vlist, m.sf, m.tris, m.edges,
+                                       2.0f * (float)dhat, m.nearl, m.counters + 8, m.counters + 2);
   k_near_pairs<<<2 * 152, 128, 0, st>>>(m.counters + 8, m.cap, m.cap_act, m.nearl, sp, m.tris,
                                         m.edges, dhat,
                                         kappa, m.pairs, m.counters, m.scal);
-  count_launch(2);
+  count_launch(4);
 }
 
 // CCD candidates of the step sp -> sp + dsp into m.cand ([1] length, [9]
@@ -811,7 +923,12 @@ void launch_ccd(cudaStream_t st, const DevMesh& m, const double* sp, const doubl
   if (np == 0) return;
   k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, dsp, m.tris, m.edges, dhat,
                                                 m.pbox, m.pkey, m.sf, m.dsf);
-  launch_sweeps(st, m, 1, m.cand, m.counters + 1, m.counters + 9, 0.0f);
+  // candidates from the skin list when it still covers the step, else the
+  // full sweep
+  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, dsp, m.skin, 0.0, m.counters);
+  k_skin_cand<<<2 * 152, 128, 0, st>>>(m.counters, m.cap, m.vlist, m.pkey, m.Ns, m.Nt, m.cand);
+  launch_sweeps(st, m, 1, m.cand, m.counters + 1, m.counters + 9, 0.0f, m.counters + 13);
+  count_launch(2);
   // float32 coordinates round by ~6e-8 of their magnitude; the early-out
   // slack (1e-5 of twice the largest rest coordinate, at least 1% of dhat)
   // stays two orders of magnitude above that rounding

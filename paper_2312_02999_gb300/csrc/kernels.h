@@ -39,6 +39,9 @@ struct DevMesh {
   float* sf = nullptr;        // 3 Ns float32 proxy positions
   float* dsf = nullptr;       // 3 Ns float32 proxy step
   unsigned long long* nearl = nullptr;  // pairs within 2 dhat in float32 (cap)
+  unsigned long long* vlist = nullptr;  // skin list: pairs within dhat + skin at sb (cap)
+  double* sb = nullptr;       // 3 Ns proxy positions of the last skin-list build
+  double skin = 0.0;          // skin width of the list (length)
   double coord_scale = 1.0;   // 2 x largest |rest coordinate|
   // solver ordering
   int* perm = nullptr;        // nf: position -> vertex
@@ -75,6 +78,7 @@ struct DevMesh {
   unsigned long long* cand = nullptr;     // CCD candidates
   int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite [5] touching
                               // [6..7] Cholesky info [8] near pairs [9] CCD overflow
+                              // [10..14] skin list (k_contact.cu)
   double* scal = nullptr;     // [0] barrier energy [1] alpha [2] elastic energy [3] gnorm2 ...
   double* partials = nullptr; // block partial sums
   int n_partials = 0;

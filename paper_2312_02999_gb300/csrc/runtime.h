@@ -26,6 +26,7 @@ struct MeshState {
   int64_t factor_nnz = 0;
   std::vector<void*> allocs;     // device buffers owned by this mesh
   size_t ws_bytes = 0;           // bytes of one per-solve workspace
+  double mean_edge = 0.0;        // mean proxy edge length at rest
   // host copies kept for the prefactor
   std::vector<double> rest;
   std::vector<int32_t> tets;

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
-                ("active_capacity", C.c_int64)]
+                ("active_capacity", C.c_int64), ("skin", C.c_double)]
 
 
 class FrameStats(C.Structure):

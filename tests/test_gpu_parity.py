@@ -122,6 +122,25 @@ def test_constraint_set_and_barrier_energy(fsim, slab_small):
         assert keys.tolist() == sorted(keys.tolist())
 
 
+def test_constraint_set_reuses_the_skin_list(fsim, ctx):
+    # consecutive evaluations at nearby positions reuse the candidate list
+    # built at the first one; the constraint set must stay exact
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    rng = np.random.default_rng(21)
+    x = _contact_x(mesh, 3e-4, seed=3, gap_shift=0.0035)
+    free = mesh.pinned == 0
+    for step in range(4):
+        keys, B = m.eval_contacts(x)
+        s = pr.W @ x
+        ora = OC.constraint_set(s, pr.tris, pr.edges, mesh.dhat)
+        n, nd = _check_contact_sets(keys, ora, s, pr, mesh.dhat)
+        assert n > 0 and nd == 0
+        x = x.copy()
+        x[free] += 1e-4 * rng.standard_normal((int(free.sum()), 3))
+
+
 def test_barrier_gradient_and_reduced_block(fsim, slab_small):
     mesh, act, m, pr = slab_small
     x = _contact_x(mesh, 3e-4, seed=7, gap_shift=0.0035)
