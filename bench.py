@@ -48,8 +48,10 @@ def parse():
                     help="concurrent frame sequences (server workers)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the float64 served leg and the host-buffer leg")
-    ap.add_argument("--legs", choices=["all", "single"], default="all",
-                    help="single: only the single-sequence legs (profiling runs)")
+    ap.add_argument("--legs", choices=["all", "single", "compare"], default="all",
+                    help="single: only the single-sequence legs (profiling runs); compare: "
+                         "global step by Schur + Woodbury vs PD-preconditioned CG, at kappa and "
+                         "10 kappa (the paper's solver comparison), float64")
     ap.add_argument("--first-frame", type=int, default=20,
                     help="first frame of each sequence (solved from rest, untimed)")
     return ap.parse_args()
@@ -222,6 +224,72 @@ def stream_actuations(I, field, first, n_frames, seed):
     coeffs = I.keyframe_coeffs(seed=seed)
     return [I.bump_actuation(field, coeffs[min(first + f - 1, len(coeffs) - 1)])
             for f in range(n_frames + 1)]
+
+
+def run_compare(args):
+    """Per-iteration global-step time of the paper's method (Schur + Woodbury,
+    Eq. 8-11) against its comparison configuration (CG preconditioned with H),
+    at the automatic kappa and at 10 kappa, on the same face frames (float64)."""
+    import numpy as np
+    import torch
+    from paper_2312_02999_gb300 import build
+    build.build()
+    from paper_2312_02999_gb300 import fsim
+    from paper_2312_02999_gb300 import inputs as I
+    F0, K = args.first_frame, max(1, min(args.steps, 2))
+    mesh = I.face_shell(n_target=args.n_target)
+    field = I.bump_field(mesh, seed=2)
+    acts = stream_actuations(I, field, F0, K + 1, seed=3)
+    cls = fsim.PROF_CLASSES
+    gstep = ["trsv_fwd", "trsv_bwd", "sigma_gemv", "reduced"]
+    out = {}
+    with fsim.Context(0) as ctx:
+        kappa0 = None
+        for solver, name in ((fsim.SOLVER_WOODBURY, "woodbury"), (fsim.SOLVER_PCG, "pcg")):
+            for kmul in (1.0, 10.0):
+                m = ctx.upload(mesh)
+                p = fsim.params_for(mesh, solver=solver)
+                if kappa0 is not None:
+                    p.kappa = kmul * kappa0
+                m.prefactor(p)
+                if kappa0 is None:
+                    kappa0 = m.info()["kappa"]
+                    if kmul != 1.0:
+                        raise RuntimeError("first run must use the automatic kappa")
+                m.set_actuation(acts[1].fiber, acts[1].stretch)
+                m.solve_frame(mesh.rest, precision=fsim.FP64, check=True)
+                ctx.profile((1 << len(cls)) - 1)
+                ctx.profile_reset()
+                it, cg, t_ms = 0, 0, 0.0
+                for f in range(2, K + 2):
+                    m.set_actuation(acts[f].fiber, acts[f].stretch)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    stream = torch.cuda.ExternalStream(ctx.stream_ptr())
+                    e0.record(stream)
+                    rc, st = m.solve_frame(None, precision=fsim.FP64, check=False)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if rc != 0:
+                        raise RuntimeError(f"{name} frame {f}: {fsim.STATUS_NAMES.get(rc, rc)}")
+                    it += st["iterations"]
+                    cg += st["cg_iterations"]
+                    t_ms += e0.elapsed_time(e1)
+                prof = {c: ctx.profile_read(i)[1] for i, c in enumerate(cls)}
+                ctx.profile(0)
+                g_ms = prof["pcg"] if solver == fsim.SOLVER_PCG else sum(prof[c] for c in gstep)
+                out[f"{name}_kappa_x{int(kmul)}"] = {
+                    "global_step_ms_per_iter": g_ms / max(it, 1), "frame_ms": t_ms / K,
+                    "iterations": it, "cg_iterations": cg}
+    w1, c1 = out["woodbury_kappa_x1"], out["pcg_kappa_x1"]
+    w10, c10 = out["woodbury_kappa_x10"], out["pcg_kappa_x10"]
+    line = {"comparison": "global step, Schur + Woodbury (Eq. 8-11) vs PD-preconditioned CG",
+            "workload": "face_shell_30k", "frames": f"{F0 + 1}..{F0 + K}", "precision": "float64",
+            "results": out,
+            "pcg_over_woodbury_gstep": c1["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
+            "kappa_x10_cost_ratio": {
+                "woodbury": w10["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
+                "pcg": c10["global_step_ms_per_iter"] / c1["global_step_ms_per_iter"]}}
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
@@ -426,7 +494,8 @@ def run_ours(args):
         "warmup": W, "ms_per_step": srv_m["total_ms"] / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
         "config": dict(bench_config(args, world), n=int(info["n"]), tets=int(info["T"]),
-                       n1=int(info["n1"]), n2=int(info["n2"])),
+                       n1=int(info["n1"]), n2=int(info["n2"]),
+                       workspace_bytes=int(info["workspace_bytes"])),
         "latency_ms": {"p50": percentile(srv_m["lat"], 50), "p99": percentile(srv_m["lat"], 99)},
         "iterations_mean": statistics.mean(iters),
         "n_c_max": max(st["n_c_max"] for st in srv_m["stats"]),
@@ -472,7 +541,8 @@ def roofline_entry(cls_name, info, prof, stats):
         flops = 13.83 * sum(st["sum_nc3"] for st in stats)
         ach = flops / (ms * 1e-3) / 1e12
         base.update({"bound": "alu", "achieved": ach, "peak": FP32_TFLOPS_PEAK, "unit": "TFLOP/s",
-                     "frac": ach / FP32_TFLOPS_PEAK, "kernel": "k_reduced<float>",
+                     "frac": ach / FP32_TFLOPS_PEAK,
+                     "kernel": "reduced-system kernels (k_small_s/x/n/v, k_clus_v, k_reduced<float>)",
                      "work": "13.83 n_c^3 float32 flop per launch (two Cholesky factorisations "
                              "and the N product), summed over the timed global steps",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"})
@@ -501,6 +571,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.legs == "compare":
+        if dist_env()[0] == 0:
+            run_compare(args)
         return
     run_ours(args)
 

@@ -90,7 +90,15 @@ typedef struct {
                                skin / 2 (results are the same as sweeping
                                every time); <= 0 selects max(10 d0, a quarter
                                of the mean proxy edge length at rest)        */
+  int32_t solver;           /* global step: FSIM_SOLVER_WOODBURY (Eq. 8-11, the
+                               paper's method) or FSIM_SOLVER_PCG (conjugate
+                               gradients preconditioned with H, the paper's
+                               comparison configuration; float64)             */
+  int32_t cg_max_iters;     /* CG iteration cap per global step                */
+  double cg_tol;            /* CG stop: ||r|| <= cg_tol ||g-hat||              */
 } fsim_params;
+#define FSIM_SOLVER_WOODBURY 0
+#define FSIM_SOLVER_PCG 1
 
 /* Per-frame statistics filled by fsim_solve_frame. */
 typedef struct {
@@ -107,12 +115,14 @@ typedef struct {
   double alpha_min;       /* smallest accepted step of the frame                  */
   double sum_nc3;         /* sum of n_c^3 over the frame's global steps (the
                              reduced system's work scales with it)            */
+  int64_t cg_iterations;  /* CG iterations of the frame (FSIM_SOLVER_PCG)       */
 } fsim_frame_stats;
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
- * coop_ctas 0, contact_capacity, active_capacity and skin auto.  dhat must
- * still be set by the caller. */
+ * coop_ctas 0, contact_capacity, active_capacity and skin auto, solver
+ * Woodbury, cg_max_iters 2000, cg_tol 1e-8.  dhat must still be set by the
+ * caller. */
 fsim_status fsim_default_params(fsim_params* p);
 
 /* Create a context on CUDA device `device`; it owns one CUDA stream and all

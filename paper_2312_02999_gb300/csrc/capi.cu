@@ -167,6 +167,14 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.cand, (size_t)m.cap, bytes));
   TRY(dalloc(al, &m.nearl, (size_t)m.cap, bytes));
   TRY(dalloc(al, &m.vlist, (size_t)m.cap, bytes));
+  if (ms.p.solver == FSIM_SOLVER_PCG) {
+    TRY(dalloc(al, &m.cg_r, 3 * n, bytes));
+    TRY(dalloc(al, &m.cg_z, 3 * n, bytes));
+    TRY(dalloc(al, &m.cg_p, 3 * n, bytes));
+    TRY(dalloc(al, &m.cg_q, 3 * n, bytes));
+    TRY(dalloc(al, &m.cg_tmp, 3 * n, bytes));
+    TRY(dalloc(al, &m.cg_red, 2, bytes));
+  }
   TRY(dalloc(al, &m.sb, 3 * Ns, bytes));
   TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap_act, bytes));
@@ -340,12 +348,21 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     st.n_c_max = std::max(st.n_c_max, nc);
     if (gn <= tol) break;
     if (st.iterations >= p.max_iters) { rc = FSIM_ENOT_CONVERGED; break; }
-    // global step (Eq. 4 via Eq. 8-11)
-    TRY(with_graph(ex, m, prec, m.g, prec, m.red_gen, [&]() -> int {
+    // global step (Eq. 4 via Eq. 8-11, or the CG comparison configuration)
+    if (p.solver == FSIM_SOLVER_PCG) {
       CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-      CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone));
-      return FSIM_OK;
-    }));
+      int cg_it = 0;
+      if (pcg_global_step(s, m, m.g, m.dx, p.cg_tol, p.cg_max_iters, m.counters + 6, ex.coop_ctas,
+                          ex.h_scal + 6, &cg_it) != 0)
+        return FSIM_ECUDA;
+      st.cg_iterations += cg_it;
+    } else {
+      TRY(with_graph(ex, m, prec, m.g, prec, m.red_gen, [&]() -> int {
+        CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
+        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone));
+        return FSIM_OK;
+      }));
+    }
     st.sum_nc3 += (double)nc * nc * nc;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
@@ -439,6 +456,9 @@ fsim_status fsim_default_params(fsim_params* p) {
   p->contact_capacity = 0;
   p->active_capacity = 0;
   p->skin = 0.0;
+  p->solver = FSIM_SOLVER_WOODBURY;
+  p->cg_max_iters = 2000;
+  p->cg_tol = 1e-8;
   return FSIM_OK;
 }
 
@@ -599,7 +619,8 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   MeshState* msp = get_mesh(ctx, mesh_id);
   if (!msp || !p || !(p->dhat > 0.0) || !(p->weight_scale > 0.0) || p->max_iters < 0 ||
       p->max_ls < 0 || !(p->ccd_s > 0.0 && p->ccd_s < 1.0) || p->accd_max_iters <= 0 ||
-      p->coop_ctas < 0)
+      p->coop_ctas < 0 || (p->solver != FSIM_SOLVER_WOODBURY && p->solver != FSIM_SOLVER_PCG) ||
+      (p->solver == FSIM_SOLVER_PCG && (p->cg_max_iters <= 0 || !(p->cg_tol > 0.0))))
     return FSIM_EINVAL;
   if (msp->prefactored) return FSIM_EINVAL;
   cudaSetDevice(ctx->device);
@@ -687,6 +708,26 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   }
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
                                   : std::max<int64_t>(1 << 20, 256 * (int64_t)std::max(m.Nt, 1));
+  {   // K in vertex order for the CG operator (rows of pinned vertices empty)
+    std::vector<int> kp(m.n + 1, 0), kc;
+    std::vector<double> kv;
+    std::vector<int> rowlen(m.n, 0);
+    for (int q = 0; q < m.nf; ++q) rowlen[f.perm[q]] = f.k_ptr[q + 1] - f.k_ptr[q];
+    for (int v = 0; v < m.n; ++v) kp[v + 1] = kp[v] + rowlen[v];
+    kc.resize(kp[m.n]);
+    kv.resize(kp[m.n]);
+    for (int q = 0; q < m.nf; ++q) {
+      int o = kp[f.perm[q]];
+      for (int e = f.k_ptr[q]; e < f.k_ptr[q + 1]; ++e, ++o) {
+        kc[o] = f.perm[f.k_col[e]];
+        kv[o] = f.k_val[e];
+      }
+    }
+    TRY(upload(ms, s, &m.kv_ptr, kp.data(), kp.size()));
+    TRY(upload(ms, s, &m.kv_col, kc.data(), kc.size()));
+    TRY(upload(ms, s, &m.kv_val, kv.data(), kv.size()));
+    CK(cudaStreamSynchronize(s));
+  }
   m.skin = p->skin > 0.0 ? p->skin : std::max(10.0 * p->dhat, 0.25 * ms.mean_edge);
   m.cap_act = p->active_capacity > 0 ? p->active_capacity
                                      : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));
@@ -957,7 +998,14 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   double gn2 = 0.0;
   TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
   CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-  CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone));
+  if (ms->p.solver == FSIM_SOLVER_PCG) {
+    int cg_it = 0;
+    if (pcg_global_step(s, m, ms->gtmp, ms->dxtmp, ms->p.cg_tol, ms->p.cg_max_iters, m.counters + 6,
+                        ex.coop_ctas, ex.h_scal + 6, &cg_it) != 0)
+      return FSIM_ECUDA;
+  } else {
+    CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone));
+  }
   TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
   CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));

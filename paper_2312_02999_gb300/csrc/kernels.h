@@ -40,6 +40,12 @@ struct DevMesh {
   float* dsf = nullptr;       // 3 Ns float32 proxy step
   unsigned long long* nearl = nullptr;  // pairs within 2 dhat in float32 (cap)
   unsigned long long* vlist = nullptr;  // skin list: pairs within dhat + skin at sb (cap)
+  double* cg_r = nullptr;     // CG work vectors (3n each) and 2 device scalars
+  double* cg_z = nullptr;
+  double* cg_p = nullptr;
+  double* cg_q = nullptr;
+  double* cg_tmp = nullptr;
+  double* cg_red = nullptr;
   double* sb = nullptr;       // 3 Ns proxy positions of the last skin-list build
   double skin = 0.0;          // skin width of the list (length)
   double coord_scale = 1.0;   // 2 x largest |rest coordinate|
@@ -65,6 +71,9 @@ struct DevMesh {
   double* y1 = nullptr;       // n1*3 forward-solve scratch
   float* y1f = nullptr;
   double* Sinv = nullptr;     // n2 x n2 Schur-complement inverse (Sec. 3.2)
+  int* kv_ptr = nullptr;      // K in vertex order (CSR over free vertices), for the CG operator
+  int* kv_col = nullptr;
+  double* kv_val = nullptr;
   float* Sinvf = nullptr;
   // global-step work (solver positions, AoS 3)
   double* r = nullptr;        // nf*3
@@ -145,6 +154,11 @@ void launch_ccd_reset(cudaStream_t s, const DevMesh& m);
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
                         int* info_dev, int num_sms, bool alone);
 int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
+// Global step by CG preconditioned with H (k_pcg.cu): dx for (H + W^T B W) dx = -g
+// to a relative residual rel_tol; h_scal2 is 2 pinned host doubles.  Returns 0
+// or -1 on a CUDA error; *iters_out receives the CG iterations.
+int pcg_global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, double rel_tol,
+                    int max_iters, int* info_dev, int num_sms, double* h_scal2, int* iters_out);
 // z2 = u - Sigma^-1 Q^T v with the push-through reduced system (k_reduced.cu);
 // precision 0: float64 factors, 1: float32 factors + float64 refinement.
 // y2 (double for precision 0, float for 1) is the Schur right-hand side with
@@ -169,7 +183,7 @@ void count_launch(int k = 1);
 // Optional CUDA-event timing of kernel classes (see fsim_profile in fsim.h).
 enum ProfClass {
   PROF_ELASTIC = 0, PROF_DETECT = 1, PROF_TRSV_FWD = 2, PROF_TRSV_BWD = 3, PROF_CHOL = 4,
-  PROF_BARRIER = 5, PROF_CCD = 6, PROF_GEMV = 7, PROF_REDUCED = 8, PROF_NCLASS = 9
+  PROF_BARRIER = 5, PROF_CCD = 6, PROF_GEMV = 7, PROF_REDUCED = 8, PROF_PCG = 9, PROF_NCLASS = 10
 };
 struct ProfScope {
   ProfScope(int cls, cudaStream_t s);

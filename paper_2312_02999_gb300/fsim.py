@@ -44,14 +44,16 @@ class Params(C.Structure):
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int32),
                 ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
-                ("active_capacity", C.c_int64), ("skin", C.c_double)]
+                ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
+                ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double)]
 
 
 class FrameStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("ls_trials", C.c_int32),
                 ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("reserved0", C.c_int32),
                 ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
-                ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double)]
+                ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double),
+                ("cg_iterations", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -136,7 +138,9 @@ _SIGS = {
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
-                "sigma_gemv", "reduced"]
+                "sigma_gemv", "reduced", "pcg"]
+SOLVER_WOODBURY = 0
+SOLVER_PCG = 1
 
 _lib = None
 

@@ -191,6 +191,42 @@ def test_global_step_matches_direct_solve(fsim, slab_small, prec, state, res_tol
     assert np.all(dx[mesh.pinned == 1] == 0.0)
 
 
+@pytest.mark.parametrize("state,res_tol", [("mild", 1e-9), ("stiff", 1e-6)])
+def test_pcg_global_step_matches_direct_solve(fsim, ctx, state, res_tol):
+    # the paper's comparison configuration: CG preconditioned with H.  CG's
+    # recurrence residual drifts from the true one by about cond(H-hat) * eps
+    # (cond ~ 4.8e6 at the stiff state), so the true-residual bounds are those
+    # of the float64 direct route in test_global_step_matches_direct_solve
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    m, pr = _pair(fsim, ctx, mesh, act, solver=fsim.SOLVER_PCG, cg_tol=1e-11, cg_max_iters=5000)
+    if state == "mild":
+        x = _contact_x(mesh, 1e-4, seed=9, gap_shift=0.0033)
+    else:
+        x = _contact_x(mesh, 3e-4, seed=9, gap_shift=0.0035)
+    dx = m.eval_global_step(x, precision=0)
+    ev = pr.evaluate(x)
+    assert ev["C"][0].size > 0
+    g = pr.gradient(x, ev).ravel()[pr.free_dofs]
+    Hh = pr.H + pr.free_part(pr.barrier_hessian(ev))
+    res = np.linalg.norm(Hh @ dx.ravel()[pr.free_dofs] + g) / np.linalg.norm(g)
+    assert res <= res_tol, res
+    assert np.all(dx[mesh.pinned == 1] == 0.0)
+
+
+def test_pcg_frame_matches_woodbury_frame(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, seed=1)
+    mw, pr = _pair(fsim, ctx, mesh, act)
+    mc, _ = _pair(fsim, ctx, mesh, act, solver=fsim.SOLVER_PCG, cg_tol=1e-12, cg_max_iters=5000)
+    rc, sw = mw.solve_frame(x_init=mesh.rest)
+    assert rc == 0
+    rc, sc = mc.solve_frame(x_init=mesh.rest)
+    assert rc == 0 and sc["cg_iterations"] > 0
+    assert sc["iterations"] == sw["iterations"]
+    assert np.abs(mc.positions() - mw.positions()).max() <= 1e-9 * _diag(mesh)
+
+
 def test_global_step_without_contact(fsim, ctx):
     mesh = I.two_slabs(3, 3, 2, gap=0.3)
     act = I.slab_actuation(mesh, seed=2)
