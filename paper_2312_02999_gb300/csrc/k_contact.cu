@@ -108,13 +108,13 @@ __device__ __forceinline__ void append(unsigned long long key, unsigned long lon
   else atomicOr(overflow, 1);
 }
 
-// MODE 0: constraint set (d < dhat) + barrier energy;  MODE 1: CCD candidates
-// (swept boxes, exact float64 overlap test)
-template <int MODE>
+// CCD candidates of caller-owned buffers (fsim_ccd_noalloc): point-triangle
+// and edge-edge pairs whose swept boxes (inflated by dhat) overlap by the
+// exact float64 test, after a float32 box prefilter.
 __global__ void __launch_bounds__(kTile)
-k_pairs_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restrict__ ds,
-           const int* __restrict__ tris, double dhat, double kappa,
-           unsigned long long* __restrict__ out, int* counters, int64_t cap, double* scal) {
+k_cand_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restrict__ ds,
+          const int* __restrict__ tris, double dhat, unsigned long long* __restrict__ out,
+          int* counters, int64_t cap) {
   __shared__ Box32 tb[kTile];
   __shared__ int tid3[kTile][3];
   const int t0 = blockIdx.y * kTile;
@@ -123,7 +123,7 @@ k_pairs_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restric
     if (t < Nt) {
       int ids[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
       double lo[3], hi[3];
-      prim_box<3>(s, MODE == 1 ? ds : nullptr, ids, lo, hi);
+      prim_box<3>(s, ds, ids, lo, hi);
       tb[k] = to_box32(lo, hi, 0.0);
       tid3[k][0] = ids[0]; tid3[k][1] = ids[1]; tid3[k][2] = ids[2];
     } else {
@@ -134,44 +134,25 @@ k_pairs_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restric
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= Ns) return;
   double vlo[3], vhi[3];
-  prim_box<1>(s, MODE == 1 ? ds : nullptr, &v, vlo, vhi);
+  prim_box<1>(s, ds, &v, vlo, vhi);
   const Box32 vb = to_box32(vlo, vhi, dhat);
   const int nt = min(kTile, Nt - t0);
-  double esum = 0.0;
   for (int k = 0; k < nt; ++k) {
     if (!box_overlap32(vb, tb[k])) continue;
     const int a = tid3[k][0], b = tid3[k][1], c = tid3[k][2];
     if (a == v || b == v || c == v) continue;
-    const int t = t0 + k;
-    if (MODE == 1) {
-      double tlo[3], thi[3];
-      int ids[3] = {a, b, c};
-      prim_box<3>(s, ds, ids, tlo, thi);
-      if (box_overlap64(vlo, vhi, tlo, thi, dhat))
-        append(pack_key(0, v, t), out, counters + 1, counters + 2, cap);
-    } else {
-      const int V[4] = {v, a, b, c};
-      double X[4][3];
-      gather_X(s, V, X);
-      float Xf[4][3];
-      to_rel_f(X, Xf);
-      if (pair_distance_f(0, Xf) > 2.0f * (float)dhat) continue;   // far: skip float64 work
-      const double d = pair_distance(0, X);
-      if (d < dhat) {
-        append(pack_key(0, v, t), out, counters + 0, counters + 2, cap);
-        esum += barrier_value(d, dhat);
-        if (!(d > 0.0)) atomicOr(counters + 5, 1);
-      }
-    }
+    double tlo[3], thi[3];
+    int ids[3] = {a, b, c};
+    prim_box<3>(s, ds, ids, tlo, thi);
+    if (box_overlap64(vlo, vhi, tlo, thi, dhat))
+      append(pack_key(0, v, t0 + k), out, counters + 1, counters + 2, cap);
   }
-  if (MODE == 0 && esum != 0.0) atomicAdd(scal + 0, kappa * esum);
 }
 
-template <int MODE>
 __global__ void __launch_bounds__(kTile)
-k_pairs_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
-           const int* __restrict__ edges, double dhat, double kappa,
-           unsigned long long* __restrict__ out, int* counters, int64_t cap, double* scal) {
+k_cand_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
+          const int* __restrict__ edges, double dhat, unsigned long long* __restrict__ out,
+          int* counters, int64_t cap) {
   if (blockIdx.y < blockIdx.x) return;        // tiles with j-tile >= i-tile
   __shared__ Box32 eb[kTile];
   __shared__ int eid[kTile][2];
@@ -181,7 +162,7 @@ k_pairs_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
     if (e < Ne) {
       int ids[2] = {edges[2 * e], edges[2 * e + 1]};
       double lo[3], hi[3];
-      prim_box<2>(s, MODE == 1 ? ds : nullptr, ids, lo, hi);
+      prim_box<2>(s, ds, ids, lo, hi);
       eb[k] = to_box32(lo, hi, 0.0);
       eid[k][0] = ids[0]; eid[k][1] = ids[1];
     }
@@ -191,38 +172,21 @@ k_pairs_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
   if (i >= Ne) return;
   const int ia[2] = {edges[2 * i], edges[2 * i + 1]};
   double ilo[3], ihi[3];
-  prim_box<2>(s, MODE == 1 ? ds : nullptr, ia, ilo, ihi);
+  prim_box<2>(s, ds, ia, ilo, ihi);
   const Box32 ib = to_box32(ilo, ihi, dhat);
   const int ne = min(kTile, Ne - j0);
-  double esum = 0.0;
   for (int k = 0; k < ne; ++k) {
     const int j = j0 + k;
     if (j <= i) continue;
     if (!box_overlap32(ib, eb[k])) continue;
     const int b0 = eid[k][0], b1 = eid[k][1];
     if (b0 == ia[0] || b0 == ia[1] || b1 == ia[0] || b1 == ia[1]) continue;
-    if (MODE == 1) {
-      double jlo[3], jhi[3];
-      int ids[2] = {b0, b1};
-      prim_box<2>(s, ds, ids, jlo, jhi);
-      if (box_overlap64(ilo, ihi, jlo, jhi, dhat))
-        append(pack_key(1, i, j), out, counters + 1, counters + 2, cap);
-    } else {
-      const int V[4] = {ia[0], ia[1], b0, b1};
-      double X[4][3];
-      gather_X(s, V, X);
-      float Xf[4][3];
-      to_rel_f(X, Xf);
-      if (pair_distance_f(1, Xf) > 2.0f * (float)dhat) continue;   // far: skip float64 work
-      const double d = pair_distance(1, X);
-      if (d < dhat) {
-        append(pack_key(1, i, j), out, counters + 0, counters + 2, cap);
-        esum += barrier_value(d, dhat);
-        if (!(d > 0.0)) atomicOr(counters + 5, 1);
-      }
-    }
+    double jlo[3], jhi[3];
+    int ids[2] = {b0, b1};
+    prim_box<2>(s, ds, ids, jlo, jhi);
+    if (box_overlap64(ilo, ihi, jlo, jhi, dhat))
+      append(pack_key(1, i, j), out, counters + 1, counters + 2, cap);
   }
-  if (MODE == 0 && esum != 0.0) atomicAdd(scal + 0, kappa * esum);
 }
 
 // Pass A: per-pair gradient and PSD Hessian blocks (PositiveDefinite of
@@ -231,7 +195,10 @@ k_pairs_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
 // Jacobi rotation updates its rows, columns and eigenvectors lane-parallel,
 // and the 144 block entries of the lift are spread over the lanes.  ET is the
 // type of the small eigen-solve (float64, or float32 in the mixed form).
-constexpr int kPairWarps = 4;
+// One pair-warp per CTA: the float64 geometry of a pair is a long chain of
+// float64 instructions, and an SM's float64 pipe is narrow on this part, so
+// the pairs are spread over as many SMs as possible.
+constexpr int kPairWarps = 1;
 
 template <typename ET>
 __global__ void __launch_bounds__(32 * kPairWarps)
@@ -472,24 +439,6 @@ __device__ double accd_toi(int type, double X[4][3], double dX[4][3], double s_r
     step = 0.9 * d / lp;
   }
   return fmin(t, 1.0);
-}
-
-__global__ void k_accd(int64_t nc, const unsigned long long* __restrict__ cand,
-                       const double* __restrict__ s, const double* __restrict__ ds,
-                       const int* __restrict__ tris, const int* __restrict__ edges,
-                       double s_ratio, int max_iters, double* __restrict__ alpha) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= nc) return;
-  int type, i, j;
-  unpack_key(cand[p], type, i, j);
-  int V[4];
-  load_pair(type, i, j, tris, edges, V);
-  double X[4][3], dX[4][3];
-  gather_X(s, V, X);
-  gather_X(ds, V, dX);
-  const double toi = accd_toi(type, X, dX, s_ratio, max_iters);
-  if (toi < 1.0)
-    atomicMin(reinterpret_cast<unsigned long long*>(alpha), (unsigned long long)__double_as_longlong(toi));
 }
 
 // ---------------------------------------------------------------------------
@@ -1074,13 +1023,13 @@ extern "C" fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_de
   k_set_one<<<1, 1, 0, st>>>(alpha_dev);
   if (Ns > 0 && Nt > 0) {
     dim3 gpt((unsigned)((Ns + kTile - 1) / kTile), (unsigned)((Nt + kTile - 1) / kTile));
-    k_pairs_pt<1><<<gpt, kTile, 0, st>>>((int)Ns, (int)Nt, s_dev, ds_dev, tris_dev, dhat, 0.0, keys,
-                                         counters, kNoallocCandidates, nullptr);
+    k_cand_pt<<<gpt, kTile, 0, st>>>((int)Ns, (int)Nt, s_dev, ds_dev, tris_dev, dhat, keys, counters,
+                                     kNoallocCandidates);
   }
   if (Ne > 1) {
     const unsigned ne = (unsigned)((Ne + kTile - 1) / kTile);
-    k_pairs_ee<1><<<dim3(ne, ne), kTile, 0, st>>>((int)Ne, s_dev, ds_dev, edges_dev, dhat, 0.0, keys,
-                                                  counters, kNoallocCandidates, nullptr);
+    k_cand_ee<<<dim3(ne, ne), kTile, 0, st>>>((int)Ne, s_dev, ds_dev, edges_dev, dhat, keys, counters,
+                                              kNoallocCandidates);
   }
   k_accd_count<<<256, 128, 0, st>>>(counters, kNoallocCandidates, keys, s_dev, ds_dev, tris_dev,
                                     edges_dev, ccd_s, accd_max_iters, alpha_dev);
