@@ -96,6 +96,13 @@ typedef struct {
                                comparison configuration; float64)             */
   int32_t cg_max_iters;     /* CG iteration cap per global step                */
   double cg_tol;            /* CG stop: ||r|| <= cg_tol ||g-hat||              */
+  int32_t adaptive_kappa;   /* nonzero: IPC's adaptive barrier stiffness, as the
+                               paper uses it: within a frame kappa doubles
+                               when the smallest active pair distance is below
+                               0.1 d0 and smaller than at the previous iterate,
+                               up to 100 times its start value; every frame
+                               starts from the mesh's kappa                   */
+  int32_t reserved1;
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1
@@ -107,7 +114,7 @@ typedef struct {
   int32_t ls_trials;      /* energy evaluations spent in line searches           */
   int32_t n_c;            /* contact-affected vertices at the last iteration     */
   int32_t n_c_max;        /* largest n_c over the frame                          */
-  int32_t reserved0;
+  int32_t kappa_doublings; /* adaptive_kappa: times kappa doubled in the frame    */
   int64_t contacts;       /* |C| at the returned positions                       */
   double grad_norm;       /* ||g-hat_free||_2 at the returned positions           */
   double grad_norm0;      /* ||g-hat_free||_2 at x_t                              */
@@ -121,8 +128,8 @@ typedef struct {
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
  * coop_ctas 0, contact_capacity, active_capacity and skin auto, solver
- * Woodbury, cg_max_iters 2000, cg_tol 1e-8.  dhat must still be set by the
- * caller. */
+ * Woodbury, cg_max_iters 2000, cg_tol 1e-8, adaptive_kappa off.  dhat must
+ * still be set by the caller. */
 fsim_status fsim_default_params(fsim_params* p);
 
 /* Create a context on CUDA device `device`; it owns one CUDA stream and all

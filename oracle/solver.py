@@ -54,12 +54,25 @@ class Params:
     max_ls: int = 40
     ccd_s: float = 0.1
     weight_scale: float = 1e3
+    # IPC's adaptive stiffness, as the paper uses it (Sec. 4: kappa is
+    # initialised from the soft body's average stiffness and adapted): each
+    # iteration of a frame doubles kappa when the smallest active distance is
+    # below KAPPA_GROW_BELOW * dhat and smaller than at the previous iterate,
+    # up to KAPPA_MAX_RATIO times its initial value; every frame starts from
+    # the initial value
+    adaptive_kappa: bool = False
+
+
+KAPPA_GROW_BELOW = 0.1
+KAPPA_MAX_RATIO = 100.0
 
 
 @dataclass
 class FrameStats:
     status: int = STATUS_OK
     iterations: int = 0
+    kappa_doublings: int = 0
+    d_mins: list = field(default_factory=list)       # smallest active distance per iterate
     grad_norms: list = field(default_factory=list)
     energies: list = field(default_factory=list)
     alphas: list = field(default_factory=list)
@@ -93,6 +106,7 @@ class Problem:
         self.H = H_all[self.free_dofs][:, self.free_dofs].tocsr()
         self.kappa = (float(self.H.diagonal().mean()) if params.kappa is None
                       else float(params.kappa))
+        self.kappa0 = self.kappa
         # collision-aware set x2 (Sec. 3.1: x2 embeds s): the free support of
         # W, plus the marked region when one is given
         x2 = np.zeros(self.n, dtype=bool)
@@ -180,8 +194,20 @@ class Problem:
         x = np.array(x_t, dtype=np.float64, copy=True)
         x[self.pinned] = self.rest[self.pinned]
         tol = None
+        self.kappa = self.kappa0
+        d_prev = np.inf
         while True:
             ev = self.evaluate(x)                          # GetProjection, C
+            d_min = float(ev["C"][3].min()) if ev["C"][3].size else np.inf
+            if record:
+                st.d_mins.append(d_min)
+            if p.adaptive_kappa:
+                if (d_min < KAPPA_GROW_BELOW * p.dhat and d_min < d_prev
+                        and 2.0 * self.kappa <= KAPPA_MAX_RATIO * self.kappa0):
+                    ev["B"] *= 2.0                          # B is linear in kappa
+                    self.kappa *= 2.0
+                    st.kappa_doublings += 1
+                d_prev = d_min
             g_all = self.gradient(x, ev)                   # g-hat
             g = g_all.ravel()[self.free_dofs]
             gn = float(np.linalg.norm(g))

@@ -264,7 +264,7 @@ int graph_slot(const DevMesh& m, int first, int count, const void* key, int key2
 // Leaves E in scal[2], B in scal[0], |C| in counters[0].
 // ---------------------------------------------------------------------------
 int evaluate(const Exec& ex, const MeshState& ms, const DevMesh& m, const double* xb, double* sb,
-             double* tetf, double* proj, int prec) {
+             double* tetf, double* proj, int prec, double kappa) {
   cudaStream_t s = ex.stream;
   CK(cudaMemsetAsync(m.counters, 0, sizeof(int) * 3, s));       // |C|, candidates, overflow
   CK(cudaMemsetAsync(m.counters + 5, 0, sizeof(int), s));       // touching pair
@@ -273,7 +273,7 @@ int evaluate(const Exec& ex, const MeshState& ms, const DevMesh& m, const double
   launch_elastic(s, m, xb, tetf, proj, m.partials, prec);
   launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
   launch_proxy(s, m, xb, sb);
-  launch_detect(s, m, sb, ms.p.dhat, ms.kappa);
+  launch_detect(s, m, sb, ms.p.dhat, kappa);
   CK(cudaGetLastError());
   return FSIM_OK;
 }
@@ -283,11 +283,11 @@ int evaluate(const Exec& ex, const MeshState& ms, const DevMesh& m, const double
 // Requires counters[0] (|C|) already on the host in npairs.
 int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const double* sb,
                          const double* tetf, double* gout, int64_t npairs, int prec, int* nc_out,
-                         double* gn2_out) {
+                         double* gn2_out, double kappa) {
   cudaStream_t s = ex.stream;
   launch_gather_forces(s, m, tetf, gout);
   CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
-  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, ms.kappa, prec);
+  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, kappa, prec);
   if (m.n2 > 0) launch_mark_scan(s, m);
   else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
   TRY(sync_read(ex, m));
@@ -307,6 +307,9 @@ int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const 
   return FSIM_OK;
 }
 
+constexpr double kKappaGrowBelow = 0.1;   // adaptive kappa: grow below 0.1 dhat ...
+constexpr double kKappaMaxRatio = 100.0;   // ... up to 100 times the start value
+
 int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                      bool init_is_dev, int prec, fsim_frame_stats* stats) {
   cudaStream_t s = ex.stream;
@@ -320,10 +323,27 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
   launch_reset_pinned(s, m, m.x);
   CK(cudaMemsetAsync(m.counters + 4, 0, sizeof(int), s));
   launch_check_finite(s, 3 * m.n, m.x, m.counters + 4);
+  // barrier stiffness of this frame: starts at the mesh's kappa; with
+  // adaptive_kappa it doubles when the smallest active distance falls below
+  // kKappaGrowBelow dhat and keeps shrinking (IPC's rule, as the paper uses
+  // it), up to kKappaMaxRatio times the start value
+  double kappa = ms.kappa;
+  int kgen = 0;
+  double d_prev = INFINITY;
+  auto adapt_kappa = [&](double d_min, double* E_barrier) {
+    if (!p.adaptive_kappa) return;
+    if (d_min < kKappaGrowBelow * p.dhat && d_min < d_prev && 2.0 * kappa <= kKappaMaxRatio * ms.kappa) {
+      kappa *= 2.0;
+      *E_barrier *= 2.0;          // B is linear in kappa
+      ++kgen;
+      st.kappa_doublings++;
+    }
+    d_prev = d_min;
+  };
   auto eval_at = [&](double* xb, double* sb, double* tetf) -> int {
     const int slot = graph_slot(m, 2, 4, xb, prec);
-    return with_graph(ex, m, slot, xb, prec, 0,
-                      [&] { return evaluate(ex, ms, m, xb, sb, tetf, nullptr, prec); });
+    return with_graph(ex, m, slot, xb, prec, kgen,
+                      [&] { return evaluate(ex, ms, m, xb, sb, tetf, nullptr, prec, kappa); });
   };
   TRY(eval_at(m.x, m.s, m.tetf));
   TRY(sync_read(ex, m));
@@ -332,12 +352,14 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
   else if (ex.h_counters[5]) rc = FSIM_EINTERSECTING;
   else if (ex.h_counters[2]) rc = FSIM_ECONTACT_OVERFLOW;
   int64_t npairs = ex.h_counters[0];
-  double E = ex.h_scal[2] + ex.h_scal[0];
+  double Eb = ex.h_scal[0];
+  adapt_kappa(ex.h_scal[4], &Eb);
+  double E = ex.h_scal[2] + Eb;
   double gn = 0.0, tol = 0.0;
   int nc = 0;
   if (rc == FSIM_OK) {
     double gn2;
-    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
+    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2, kappa));
     gn = std::sqrt(gn2);
     st.grad_norm0 = gn;
     tol = std::max(p.tol_abs, p.tol_rel * gn);
@@ -399,11 +421,15 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     std::swap(m.x, m.xt);
     std::swap(m.s, m.st);
     std::swap(m.tetf, m.tetf_t);
-    E = Et;
+    {
+      double Ebt = ex.h_scal[0];
+      adapt_kappa(ex.h_scal[4], &Ebt);
+      E = ex.h_scal[2] + Ebt;
+    }
     npairs = np_t;
     st.iterations++;
     double gn2;
-    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2));
+    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2, kappa));
     gn = std::sqrt(gn2);
     if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
   }
@@ -459,6 +485,7 @@ fsim_status fsim_default_params(fsim_params* p) {
   p->solver = FSIM_SOLVER_WOODBURY;
   p->cg_max_iters = 2000;
   p->cg_tol = 1e-8;
+  p->adaptive_kappa = 0;
   return FSIM_OK;
 }
 
@@ -885,7 +912,7 @@ fsim_status fsim_read_contacts(fsim_ctx_t ctx, int mesh_id, int32_t* keys, int64
   cudaSetDevice(ctx->device);
   DevMesh& m = ms->d;
   const Exec ex = ctx_exec(ctx, *ms);
-  TRY(evaluate(ex, *ms, m, m.x, m.st, m.tetf_t, nullptr, 0));
+  TRY(evaluate(ex, *ms, m, m.x, m.st, m.tetf_t, nullptr, 0, ms->kappa));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   return copy_keys(ctx, *ms, ctx->h_counters[0], keys, cap, count);
@@ -942,7 +969,7 @@ fsim_status fsim_eval_contacts(fsim_ctx_t ctx, int mesh_id, const double* x, int
   DevMesh& m = ms->d;
   TRY(stage_x(ctx, *ms, x));
   const Exec ex = ctx_exec(ctx, *ms);
-  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0, ms->kappa));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   if (barrier_energy_out) *barrier_energy_out = ctx->h_scal[0];
@@ -959,7 +986,7 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
   cudaStream_t s = ctx->stream;
   TRY(stage_x(ctx, *ms, x));
   const Exec ex = ctx_exec(ctx, *ms);
-  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0));
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, 0, ms->kappa));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const int64_t np = ctx->h_counters[0];
@@ -967,7 +994,7 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
   CK(cudaMemsetAsync(m.tetf_t, 0, sizeof(double) * 12 * (size_t)m.T, s));
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2, ms->kappa));
   if (n_c) *n_c = nc;
   if (grad_out)
     CK(cudaMemcpy(grad_out, ms->gtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
@@ -990,13 +1017,13 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   cudaStream_t s = ctx->stream;
   TRY(stage_x(ctx, *ms, x));
   const Exec ex = ctx_exec(ctx, *ms);
-  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision, ms->kappa));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, precision, &nc, &gn2, ms->kappa));
   CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
   if (ms->p.solver == FSIM_SOLVER_PCG) {
     int cg_it = 0;
@@ -1041,14 +1068,14 @@ fsim_status fsim_eval_energy(fsim_ctx_t ctx, int mesh_id, const double* x, int p
   DevMesh& m = ms->d;
   TRY(stage_x(ctx, *ms, x));
   const Exec ex = ctx_exec(ctx, *ms);
-  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision));
+  TRY(evaluate(ex, *ms, m, m.xt, m.st, m.tetf_t, nullptr, precision, ms->kappa));
   TRY(sync_read(ex, m));
   if (ctx->h_counters[2]) return FSIM_ECONTACT_OVERFLOW;
   const double E = ctx->h_scal[2] + ctx->h_scal[0];
   const int64_t np = ctx->h_counters[0];
   int nc = 0;
   double gn2 = 0.0;
-  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2));
+  TRY(gradient_and_hessian(ex, *ms, m, m.st, m.tetf_t, ms->gtmp, np, 0, &nc, &gn2, ms->kappa));
   if (energy_out) *energy_out = E;
   if (grad_norm_out) *grad_norm_out = std::sqrt(gn2);
   return FSIM_OK;

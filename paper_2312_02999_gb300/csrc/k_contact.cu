@@ -663,6 +663,8 @@ __global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, in
       append(pack_key(type, i, j), pairs, counters + 0, counters + 2, cap_act);
       esum += barrier_value(d, dhat);
       if (!(d > 0.0)) atomicOr(counters + 5, 1);
+      else   // smallest active distance (positive doubles order like their bits)
+        atomicMin(reinterpret_cast<unsigned long long*>(scal + 4), (unsigned long long)__double_as_longlong(d));
     }
   }
   if (esum != 0.0) atomicAdd(scal + 0, kappa * esum);
@@ -739,7 +741,8 @@ __device__ __forceinline__ double block_max_d(double v) {
 // CCD step needs the full sweep (ds != nullptr); a rebuild records sb = s
 __global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __restrict__ sb,
                              const double* __restrict__ ds, double skin, double margin,
-                             int* counters) {
+                             int* counters, double* scal) {
+  if (ds == nullptr && threadIdx.x == 0) scal[4] = __longlong_as_double(0x7ff0000000000000LL);  // d_min = inf
   double dmax = 0.0, smax = 0.0;
   for (int v = threadIdx.x; v < Ns; v += blockDim.x) {
     double d2 = 0.0, q2 = 0.0;
@@ -852,7 +855,7 @@ void launch_detect(cudaStream_t st, const DevMesh& m, const double* sp, double d
   const float margin = (float)skin_margin(m, dhat);
   k_prim_prep<<<(np + 255) / 256, 256, 0, st>>>(m.Ns, m.Nt, m.Ne, sp, nullptr, m.tris, m.edges, pad,
                                                 m.pbox, m.pkey, m.sf, nullptr);
-  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, nullptr, m.skin, margin, m.counters);
+  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, nullptr, m.skin, margin, m.counters, m.scal);
   launch_sweeps(st, m, 0, m.vlist, m.counters + 10, m.counters + 14, (float)pad + margin,
                 m.counters + 11);
   k_skin_near<<<2 * 152, 128, 0, st>>>(m.counters, m.cap, m.vlist, m.sf, m.tris, m.edges,
@@ -874,7 +877,7 @@ void launch_ccd(cudaStream_t st, const DevMesh& m, const double* sp, const doubl
                                                 m.pbox, m.pkey, m.sf, m.dsf);
   // candidates from the skin list when it still covers the step, else the
   // full sweep
-  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, dsp, m.skin, 0.0, m.counters);
+  k_skin_check<<<1, 512, 0, st>>>(m.Ns, sp, m.sb, dsp, m.skin, 0.0, m.counters, m.scal);
   k_skin_cand<<<2 * 152, 128, 0, st>>>(m.counters, m.cap, m.vlist, m.pkey, m.Ns, m.Nt, m.cand);
   launch_sweeps(st, m, 1, m.cand, m.counters + 1, m.counters + 9, 0.0f, m.counters + 13);
   count_launch(2);

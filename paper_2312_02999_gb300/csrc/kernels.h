@@ -88,7 +88,8 @@ struct DevMesh {
   int* counters = nullptr;    // [0] pairs [1] cand [2] overflow [3] nc [4] nonfinite [5] touching
                               // [6..7] Cholesky info [8] near pairs [9] CCD overflow
                               // [10..14] skin list (k_contact.cu)
-  double* scal = nullptr;     // [0] barrier energy [1] alpha [2] elastic energy [3] gnorm2 ...
+  double* scal = nullptr;     // [0] barrier energy [1] alpha [2] elastic energy [3] gnorm2
+                              // [4] smallest active pair distance
   double* partials = nullptr; // block partial sums
   int n_partials = 0;
   double* pair_grad = nullptr;   // cap * 12

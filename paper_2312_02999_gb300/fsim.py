@@ -45,12 +45,13 @@ class Params(C.Structure):
                 ("max_ls", C.c_int32), ("ccd_s", C.c_double), ("accd_max_iters", C.c_int32),
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
                 ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
-                ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double)]
+                ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double), ("adaptive_kappa", C.c_int32),
+                ("reserved1", C.c_int32)]
 
 
 class FrameStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("ls_trials", C.c_int32),
-                ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("reserved0", C.c_int32),
+                ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("kappa_doublings", C.c_int32),
                 ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
                 ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double),
                 ("cg_iterations", C.c_int64)]

@@ -227,6 +227,27 @@ def test_pcg_frame_matches_woodbury_frame(fsim, ctx):
     assert np.abs(mc.positions() - mw.positions()).max() <= 1e-9 * _diag(mesh)
 
 
+def test_adaptive_kappa_frame_matches_oracle(fsim, ctx):
+    # IPC's adaptive stiffness: from a start with one pair at ~0.003 dhat the
+    # oracle doubles kappa once; the GPU frame must take the same decisions
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    m, _ = _pair(fsim, ctx, mesh, act, adaptive_kappa=1)
+    kappa = m.info()["kappa"]
+    pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr, mesh.W_col,
+                   mesh.W_val, S.Params(dhat=mesh.dhat, kappa=kappa, adaptive_kappa=True,
+                                        tol_abs=mesh.tol_abs, tol_rel=mesh.tol_rel,
+                                        weight_scale=mesh.weight_scale), region=mesh.region)
+    pr.set_actuation(act.fiber, act.stretch)
+    x0 = _contact_x(mesh, 3e-4, seed=9, gap_shift=0.0035)
+    xo, so = pr.solve_frame(x0)
+    rc, st = m.solve_frame(x_init=x0)
+    assert rc == 0 and so.status == 0
+    assert st["kappa_doublings"] == so.kappa_doublings >= 1
+    assert st["iterations"] == so.iterations
+    assert np.abs(m.positions() - xo).max() <= 1e-9 * _diag(mesh)
+
+
 def test_global_step_without_contact(fsim, ctx):
     mesh = I.two_slabs(3, 3, 2, gap=0.3)
     act = I.slab_actuation(mesh, seed=2)

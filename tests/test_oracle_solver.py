@@ -135,3 +135,44 @@ def test_direct_solver_step_is_independent_of_kappa_scaling_of_h():
         dx = pr.global_step_direct(g, k * B)
         res = (pr.H + k * B) @ dx + g
         assert np.linalg.norm(res) <= 1e-11 * np.linalg.norm(g)
+
+
+def _near_contact_slab(adaptive):
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr, mesh.W_col,
+                   mesh.W_val, S.Params(dhat=mesh.dhat, adaptive_kappa=adaptive,
+                                        weight_scale=mesh.weight_scale), region=mesh.region)
+    pr.set_actuation(act.fiber, act.stretch)
+    rng = np.random.default_rng(9)
+    x = mesh.rest.copy()
+    free = mesh.pinned == 0
+    x[free] += 3e-4 * rng.standard_normal((int(free.sum()), 3))
+    top = mesh.rest[:, 2] > mesh.rest[:, 2].mean()
+    x[top & free, 2] -= 0.0035           # one pair at ~0.003 dhat
+    return mesh, pr, x
+
+
+def test_adaptive_kappa_follows_its_rule():
+    # IPC's adaptive stiffness (Sec. 4): kappa doubles at an iterate whose
+    # smallest active distance is below 0.1 dhat and below the previous
+    # iterate's, never beyond 100 kappa_0, and restarts every frame
+    mesh, pr, x0 = _near_contact_slab(True)
+    x, st = pr.solve_frame(x0)
+    assert st.status == S.STATUS_OK
+    expect, prev, kap = 0, np.inf, 1.0
+    for d in st.d_mins:
+        if d < S.KAPPA_GROW_BELOW * mesh.dhat and d < prev and 2 * kap <= S.KAPPA_MAX_RATIO:
+            expect += 1
+            kap *= 2
+        prev = d
+    assert st.kappa_doublings == expect >= 1
+    assert pr.kappa == pr.kappa0 * 2 ** expect
+    assert min(st.d_mins) > 0.0
+    # the next frame starts from kappa_0 again
+    x2, st2 = pr.solve_frame(x)
+    assert st2.kappa_doublings == 0 and pr.kappa == pr.kappa0
+    # without adaptation the same start converges with kappa_0 throughout
+    _, pr0, _ = _near_contact_slab(False)
+    _, st0 = pr0.solve_frame(x0)
+    assert st0.status == S.STATUS_OK and st0.kappa_doublings == 0 and pr0.kappa == pr0.kappa0
