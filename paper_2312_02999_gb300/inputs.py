@@ -16,6 +16,8 @@ whose collision proxy is the mouth region, n2 about a tenth of n1 or less):
                      3 cm thick, inner surface pinned as the skull, with a thin
                      mouth slit that separates two lip lobes; the proxy is the
                      boundary surface around the mouth.
+* ``embed_finer_surface`` -- turns a selection proxy into a finer surface
+                     embedded in the tets (barycentric rows of W).
 * ``bump_actuation`` -- stretch field from a sum of seeded Gaussian bumps.
 """
 from __future__ import annotations
@@ -265,6 +267,97 @@ def face_shell(n_target: int = 30000, nr: int = 7, thickness: float = 0.03,
                      grid={"nphi": nphi, "ntheta": ntheta, "nr": nr, "jm": jm,
                            "gi": gi_, "gj": gj_, "gk": gk_,
                            "theta_mouth": theta_mouth})
+
+
+# ----------------------------------------------------------------------------
+# embedded finer proxy surface (general barycentric rows of W)
+# ----------------------------------------------------------------------------
+def embed_finer_surface(mesh: MeshInput, levels: int = 2, relief: float = 0.15,
+                        seed: int = 7) -> MeshInput:
+    """Replace a selection proxy by a finer surface embedded in the tet mesh.
+
+    Sec. 3.1 lets the collision proxy be a surface finer than the simulation
+    mesh, each proxy vertex interpolated from the tet that contains it (s = W x
+    with barycentric rows).  Every proxy triangle (a boundary face of one tet)
+    is split 4^levels ways on the lattice of step 1/2^levels.  Lattice points
+    on the face's corners and edges stay on the face (rows of 1 and 2 entries,
+    shared by the neighbouring faces); interior lattice points are pulled into
+    the owning tet towards its fourth vertex by a seeded fraction
+    mu ~ U[0, relief] of the way (rows of 4 entries), which gives the finer
+    surface its own small relief below the coarse one.
+    """
+    if not np.all(np.diff(mesh.W_rowptr) == 1) or not np.all(mesh.W_val == 1.0):
+        raise ValueError("embed_finer_surface expects a selection proxy")
+    if levels < 1:
+        raise ValueError("levels must be >= 1")
+    N = 1 << levels
+    faces = mesh.W_col[mesh.W_rowptr[:-1]][mesh.proxy_tris].astype(np.int64)   # mesh ids
+    # owning tet of each face and its fourth vertex
+    tets = mesh.tets.astype(np.int64)
+    owner = {}
+    for t in range(tets.shape[0]):
+        q = tets[t]
+        for drop in range(4):
+            f = tuple(sorted(np.delete(q, drop).tolist()))
+            owner.setdefault(f, []).append((t, int(q[drop])))
+    apex = np.empty(faces.shape[0], dtype=np.int64)
+    for k in range(faces.shape[0]):
+        own = owner[tuple(sorted(faces[k].tolist()))]
+        if len(own) != 1:
+            raise ValueError("proxy face is not a boundary face")
+        apex[k] = own[0][1]
+    rng = np.random.default_rng(seed)
+    points = {}      # lattice key -> proxy id
+    rows = []        # proxy id -> {mesh vertex: weight}
+
+    def point(k, i, j):
+        a, b, c = (int(v) for v in faces[k])
+        lam = {a: (N - i - j) / N, b: i / N, c: j / N}
+        nz = [v for v in (a, b, c) if lam[v] != 0.0]
+        if len(nz) == 1:
+            key = ("v", nz[0])
+        elif len(nz) == 2:
+            lo, hi = min(nz), max(nz)
+            key = ("e", lo, hi, round(lam[hi] * N))
+        else:
+            key = ("f", k, i, j)
+        pid = points.get(key)
+        if pid is not None:
+            return pid
+        row = {v: lam[v] for v in nz}
+        if len(nz) == 3:
+            mu = relief * rng.uniform()
+            row = {v: (1.0 - mu) * w for v, w in row.items()}
+            row[int(apex[k])] = mu
+        pid = len(rows)
+        points[key] = pid
+        rows.append(row)
+        return pid
+
+    tris = []
+    for k in range(faces.shape[0]):
+        idx = {}
+        for i in range(N + 1):
+            for j in range(N + 1 - i):
+                idx[i, j] = point(k, i, j)
+        for i in range(N):
+            for j in range(N - i):
+                tris.append((idx[i, j], idx[i + 1, j], idx[i, j + 1]))
+                if i + j <= N - 2:
+                    tris.append((idx[i + 1, j], idx[i + 1, j + 1], idx[i, j + 1]))
+    rowptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    col, val = [], []
+    for r, row in enumerate(rows):
+        for v in sorted(row):
+            col.append(v)
+            val.append(row[v])
+        rowptr[r + 1] = len(col)
+    return MeshInput(name=f"{mesh.name}_embedded{levels}", rest=mesh.rest, tets=mesh.tets,
+                     pinned=mesh.pinned, proxy_tris=np.asarray(tris, dtype=np.int32),
+                     W_rowptr=rowptr, W_col=np.asarray(col, dtype=np.int32),
+                     W_val=np.asarray(val, dtype=np.float64), region=mesh.region,
+                     dhat=mesh.dhat, weight_scale=mesh.weight_scale, tol_abs=mesh.tol_abs,
+                     tol_rel=mesh.tol_rel, grid=mesh.grid)
 
 
 @dataclass
