@@ -245,7 +245,8 @@ def run_compare(args):
     out = {}
     with fsim.Context(0) as ctx:
         kappa0 = None
-        for solver, name in ((fsim.SOLVER_WOODBURY, "woodbury"), (fsim.SOLVER_PCG, "pcg")):
+        for solver, name in ((fsim.SOLVER_WOODBURY, "woodbury"), (fsim.SOLVER_PCG, "pcg"),
+                             (fsim.SOLVER_SCHUR, "schur")):
             for kmul in (1.0, 10.0):
                 m = ctx.upload(mesh)
                 p = fsim.params_for(mesh, solver=solver)
@@ -276,18 +277,26 @@ def run_compare(args):
                     t_ms += e0.elapsed_time(e1)
                 prof = {c: ctx.profile_read(i)[1] for i, c in enumerate(cls)}
                 ctx.profile(0)
-                g_ms = prof["pcg"] if solver == fsim.SOLVER_PCG else sum(prof[c] for c in gstep)
+                if solver == fsim.SOLVER_PCG:
+                    g_ms = prof["pcg"]
+                elif solver == fsim.SOLVER_SCHUR:
+                    g_ms = prof["trsv_fwd"] + prof["trsv_bwd"] + prof["schur"]
+                else:
+                    g_ms = sum(prof[c] for c in gstep)
                 out[f"{name}_kappa_x{int(kmul)}"] = {
                     "global_step_ms_per_iter": g_ms / max(it, 1), "frame_ms": t_ms / K,
                     "iterations": it, "cg_iterations": cg}
-    w1, c1 = out["woodbury_kappa_x1"], out["pcg_kappa_x1"]
-    w10, c10 = out["woodbury_kappa_x10"], out["pcg_kappa_x10"]
-    line = {"comparison": "global step, Schur + Woodbury (Eq. 8-11) vs PD-preconditioned CG",
+    w1, c1, s1 = out["woodbury_kappa_x1"], out["pcg_kappa_x1"], out["schur_kappa_x1"]
+    w10, c10, s10 = out["woodbury_kappa_x10"], out["pcg_kappa_x10"], out["schur_kappa_x10"]
+    line = {"comparison": "global step, Schur + Woodbury (Eq. 8-11) vs Schur only (dense Sigma-hat, "
+                          "Sec. 3.1) vs PD-preconditioned CG",
             "workload": "face_shell_30k", "frames": f"{F0 + 1}..{F0 + K}", "precision": "float64",
             "results": out,
             "pcg_over_woodbury_gstep": c1["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
+            "schur_over_woodbury_gstep": s1["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
             "kappa_x10_cost_ratio": {
                 "woodbury": w10["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
+                "schur": s10["global_step_ms_per_iter"] / s1["global_step_ms_per_iter"],
                 "pcg": c10["global_step_ms_per_iter"] / c1["global_step_ms_per_iter"]}}
     print(json.dumps(line), flush=True)
 

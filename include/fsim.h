@@ -91,9 +91,15 @@ typedef struct {
                                every time); <= 0 selects max(10 d0, a quarter
                                of the mean proxy edge length at rest)        */
   int32_t solver;           /* global step: FSIM_SOLVER_WOODBURY (Eq. 8-11, the
-                               paper's method) or FSIM_SOLVER_PCG (conjugate
+                               paper's method), FSIM_SOLVER_PCG (conjugate
                                gradients preconditioned with H, the paper's
-                               comparison configuration; float64)             */
+                               comparison configuration; float64) or
+                               FSIM_SOLVER_SCHUR (Sec. 3.1 alone: the dense
+                               3 n2 x 3 n2 Sigma-hat of Eq. 9 assembled and
+                               Cholesky-factored every iteration; float64, or
+                               a float32 factor with two float64 refinement
+                               steps in the mixed precision; needs
+                               108 n2^2 bytes more workspace per slot)        */
   int32_t cg_max_iters;     /* CG iteration cap per global step                */
   double cg_tol;            /* CG stop: ||r|| <= cg_tol ||g-hat||              */
   int32_t adaptive_kappa;   /* nonzero: IPC's adaptive barrier stiffness, as the
@@ -106,6 +112,7 @@ typedef struct {
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1
+#define FSIM_SOLVER_SCHUR 2
 
 /* Per-frame statistics filled by fsim_solve_frame. */
 typedef struct {

@@ -175,6 +175,14 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
     TRY(dalloc(al, &m.cg_tmp, 3 * n, bytes));
     TRY(dalloc(al, &m.cg_red, 2, bytes));
   }
+  if (ms.p.solver == FSIM_SOLVER_SCHUR && m.n2 > 0) {
+    const size_t N = 3 * (size_t)m.n2;
+    TRY(dalloc(al, &m.sh_A, N * N, bytes));
+    TRY(dalloc(al, &m.sh_Af, N * N, bytes));
+    TRY(dalloc(al, &m.sh_y, N, bytes));
+    TRY(dalloc(al, &m.sh_r, N, bytes));
+    TRY(dalloc(al, &m.sh_df, N, bytes));
+  }
   TRY(dalloc(al, &m.sb, 3 * Ns, bytes));
   TRY(dalloc(al, &m.pair_grad, 12 * (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.pair_hess, 144 * (size_t)m.cap_act, bytes));
@@ -381,7 +389,8 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     } else {
       TRY(with_graph(ex, m, prec, m.g, prec, m.red_gen, [&]() -> int {
         CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone));
+        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone,
+                       p.solver == FSIM_SOLVER_SCHUR));
         return FSIM_OK;
       }));
     }
@@ -514,6 +523,7 @@ fsim_status fsim_create(fsim_ctx_t* out, int device) {
   }
   set_solver_smem_limits(200 * 1024);
   set_reduced_smem_limits();
+  set_schur_smem_limits();
   *out = c;
   return FSIM_OK;
 }
@@ -646,7 +656,8 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   MeshState* msp = get_mesh(ctx, mesh_id);
   if (!msp || !p || !(p->dhat > 0.0) || !(p->weight_scale > 0.0) || p->max_iters < 0 ||
       p->max_ls < 0 || !(p->ccd_s > 0.0 && p->ccd_s < 1.0) || p->accd_max_iters <= 0 ||
-      p->coop_ctas < 0 || (p->solver != FSIM_SOLVER_WOODBURY && p->solver != FSIM_SOLVER_PCG) ||
+      p->coop_ctas < 0 || (p->solver != FSIM_SOLVER_WOODBURY && p->solver != FSIM_SOLVER_PCG &&
+       p->solver != FSIM_SOLVER_SCHUR) ||
       (p->solver == FSIM_SOLVER_PCG && (p->cg_max_iters <= 0 || !(p->cg_tol > 0.0))))
     return FSIM_EINVAL;
   if (msp->prefactored) return FSIM_EINVAL;
@@ -728,6 +739,8 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   TRY(upload(ms, s, &m.fwd_items, fwd.data(), fwd.size()));
   TRY(upload(ms, s, &m.bwd_items, bwd.data(), bwd.size()));
   TRY(upload(ms, s, &m.Sinv, f.sigma_inv.data(), f.sigma_inv.size()));
+  if (p->solver == FSIM_SOLVER_SCHUR && !f.sigma.empty())
+    TRY(upload(ms, s, &m.Sig, f.sigma.data(), f.sigma.size()));
   {
     std::vector<float> sf(f.sigma_inv.begin(), f.sigma_inv.end());
     TRY(upload(ms, s, &m.Sinvf, sf.data(), sf.size()));
@@ -1031,7 +1044,8 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
                         ex.coop_ctas, ex.h_scal + 6, &cg_it) != 0)
       return FSIM_ECUDA;
   } else {
-    CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone));
+    CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone,
+                   ms->p.solver == FSIM_SOLVER_SCHUR));
   }
   TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;

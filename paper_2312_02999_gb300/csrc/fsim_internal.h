@@ -36,6 +36,7 @@ struct HostFactor {
   // full free-DOF K (solver positions) for residual checks / refinement
   std::vector<int> k_ptr, k_col; std::vector<double> k_val;
   std::vector<double> sigma_inv;  // n2 x n2 dense, row-major (symmetric)
+  std::vector<double> sigma;      // n2 x n2 Sigma, row-major (symmetric)
   double kappa_auto = 0.0;        // mean diag(H) over free DOFs
   int64_t factor_nnz = 0;
 };

@@ -252,7 +252,7 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
 //   upper:    dx1 = L1^-T (z1 - L21^T dx2)             (one backward pass)
 template <typename T>
 cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int* info,
-                          int num_sms, bool wide) {
+                          int num_sms, bool wide, bool dense_schur) {
   const int nf = m.nf, n1 = m.n1, n2 = m.n2;
   const bool f64 = std::is_same<T, double>::value;
   double* r = m.r;                                  // float64 work (nf * 3)
@@ -266,19 +266,23 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
     T* y2 = b + 3 * (size_t)n1;
     double* u = m.u;
     double* z2 = r + 3 * (size_t)n1;                // float64 dx2
-    {
-      ProfScope psg(PROF_GEMV, s);
-      if (f64) {
-        k_gemv3<double><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinv, (const double*)y2, u);
-        count_launch();
-      } else {
-        float* uf = m.uf;
-        k_gemv3<float><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinvf, (const float*)y2, uf);
-        k_convert<float, double><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, uf, u);
-        count_launch(2);
+    if (dense_schur) {
+      // Schur-only configuration: Sigma-hat factored densely (k_schur.cu)
+      const cudaError_t e = sigma_hat_solve(s, m, y2, z2, info, f64 ? 0 : 1);
+      if (e != cudaSuccess) return e;
+    } else {
+      {
+        ProfScope psg(PROF_GEMV, s);
+        if (f64) {
+          k_gemv3<double><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinv, (const double*)y2, u);
+          count_launch();
+        } else {
+          float* uf = m.uf;
+          k_gemv3<float><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinvf, (const float*)y2, uf);
+          k_convert<float, double><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, uf, u);
+          count_launch(2);
+        }
       }
-    }
-    {
       // The reduced system carries the barrier stiffness (cond ~ kappa b''):
       // float64 factors, or float32 factors refined with float64 residuals.
       // n_c is read on the device (z2 = u when it is 0).
@@ -317,10 +321,10 @@ void set_solver_smem_limits(int max_bytes) {
 }
 
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
-                        int* info_dev, int num_sms, bool alone) {
+                        int* info_dev, int num_sms, bool alone, bool dense_schur) {
   // 32-warp solve items only for a float32 solve that has the GPU to itself
-  if (precision == 0) return global_step_t<double>(s, m, g, dx, info_dev, num_sms, false);
-  return global_step_t<float>(s, m, g, dx, info_dev, num_sms, alone);
+  if (precision == 0) return global_step_t<double>(s, m, g, dx, info_dev, num_sms, false, dense_schur);
+  return global_step_t<float>(s, m, g, dx, info_dev, num_sms, alone, dense_schur);
 }
 
 }  // namespace fsim

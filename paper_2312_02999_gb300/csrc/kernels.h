@@ -75,6 +75,12 @@ struct DevMesh {
   int* kv_col = nullptr;
   double* kv_val = nullptr;
   float* Sinvf = nullptr;
+  double* Sig = nullptr;      // n2 x n2 Sigma itself (the Schur-only global step)
+  double* sh_A = nullptr;     // (3 n2)^2 Sigma-hat, float64 (Schur-only global step)
+  float* sh_Af = nullptr;     // (3 n2)^2 Sigma-hat, float32 factor (mixed)
+  double* sh_y = nullptr;     // 3 n2 refinement vectors
+  double* sh_r = nullptr;
+  float* sh_df = nullptr;
   // global-step work (solver positions, AoS 3)
   double* r = nullptr;        // nf*3
   double* u = nullptr;        // n2*3
@@ -153,7 +159,13 @@ void launch_ccd_reset(cudaStream_t s, const DevMesh& m);
 // count of the cooperative reduced-system launch; alone = no other solve
 // shares the GPU (selects wider triangular-solve work items).
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
-                        int* info_dev, int num_sms, bool alone);
+                        int* info_dev, int num_sms, bool alone, bool dense_schur = false);
+// Schur-only variant of the x2 block (k_schur.cu): z2 = Sigma-hat^-1 y2 with
+// Sigma-hat = Sigma (x) I_3 + B-check assembled densely and factored by
+// Cholesky (float64, or float32 + two float64 refinement steps).
+cudaError_t sigma_hat_solve(cudaStream_t s, const DevMesh& m, const void* y2, double* z2, int* info,
+                            int precision);
+void set_schur_smem_limits();
 int64_t reduced_workspace_elems(int nc);   // doubles (or floats) needed by the reduced solve
 // Global step by CG preconditioned with H (k_pcg.cu): dx for (H + W^T B W) dx = -g
 // to a relative residual rel_tol; h_scal2 is 2 pinned host doubles.  Returns 0
@@ -184,7 +196,8 @@ void count_launch(int k = 1);
 // Optional CUDA-event timing of kernel classes (see fsim_profile in fsim.h).
 enum ProfClass {
   PROF_ELASTIC = 0, PROF_DETECT = 1, PROF_TRSV_FWD = 2, PROF_TRSV_BWD = 3, PROF_CHOL = 4,
-  PROF_BARRIER = 5, PROF_CCD = 6, PROF_GEMV = 7, PROF_REDUCED = 8, PROF_PCG = 9, PROF_NCLASS = 10
+  PROF_BARRIER = 5, PROF_CCD = 6, PROF_GEMV = 7, PROF_REDUCED = 8, PROF_PCG = 9,
+  PROF_SCHUR = 10, PROF_NCLASS = 11
 };
 struct ProfScope {
   ProfScope(int cls, cudaStream_t s);

@@ -450,6 +450,7 @@ int build_factor(int64_t n, const double* rest, const int32_t* tets, int64_t T,
     }
     // accumulated updates were subtracted as F22 - L L^T (U holds F22-LL^T of the
     // children's K entries only), so S already equals the Schur complement.
+    f.sigma = S;                                   // Sigma itself (Schur-only step)
     if (!potrf_lower(S.data(), n2, n2)) return FSIM_ENOT_SPD;
     std::vector<double> Li((size_t)n2 * n2);
     // triangular inverse, columns in parallel

@@ -139,9 +139,10 @@ _SIGS = {
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
-                "sigma_gemv", "reduced", "pcg"]
+                "sigma_gemv", "reduced", "pcg", "schur"]
 SOLVER_WOODBURY = 0
 SOLVER_PCG = 1
+SOLVER_SCHUR = 2
 
 _lib = None
 

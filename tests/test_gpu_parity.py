@@ -389,3 +389,96 @@ def test_config1_two_slabs_frame_parity(fsim, ctx):
             xo, so = pr.solve_frame(mesh.rest)
         err = np.abs(x - xo).max() / _diag(mesh)
         assert err <= tol, (prec, err)
+
+
+# ---- a finer proxy embedded in the tets (barycentric rows of W, Sec. 3.1) ----
+@pytest.fixture(scope="module")
+def slab_embedded(fsim, ctx):
+    mesh = I.embed_finer_surface(I.two_slabs(3, 3, 2, gap=0.004), levels=2, relief=0.02)
+    act = I.slab_actuation(mesh, seed=11)
+    return (mesh, act) + _pair(fsim, ctx, mesh, act)
+
+
+def test_embedded_proxy_barrier_and_global_step(fsim, slab_embedded):
+    # proxy rows of 1, 2 and 4 weights: s, the mapped gradient W^T grad B,
+    # the reduced block B-check over x2 (now holding interior vertices) and
+    # the global step, each against the oracle at 1e-9 (float64)
+    mesh, act, m, pr = slab_embedded
+    assert set(np.unique(np.diff(mesh.W_rowptr)).tolist()) == {1, 2, 4}
+    x = _contact_x(mesh, 2e-4, seed=7, gap_shift=0.0035)
+    s = m.eval_proxy(x)
+    assert _rel(s, pr.W @ x) <= 1e-15
+    g, clist, Bc = m.eval_barrier(x)
+    ev = pr.evaluate(x)
+    assert ev["C"][0].size > 0
+    V, gp, _ = pr._pair_terms(ev, project=False)
+    nnz = np.diff(mesh.W_rowptr)
+    assert (nnz[np.unique(V)] == 4).any()
+    gs = np.zeros((pr.W.shape[0], 3))
+    np.add.at(gs, V.ravel(), gp.reshape(-1, 3))
+    assert _rel(g, pr.W.T @ gs) <= 1e-9
+    Bfull = pr.barrier_hessian(ev, project=True).toarray()
+    cv = np.nonzero(pr.x2_mask)[0][clist]
+    idx = (3 * cv[:, None] + np.arange(3)).ravel()
+    assert _rel(Bc, Bfull[np.ix_(idx, idx)]) <= 1e-8
+    dx = m.eval_global_step(x, precision=0)
+    gfree = pr.gradient(x, ev).ravel()[pr.free_dofs]
+    Bf = pr.free_part(pr.barrier_hessian(ev))
+    res = np.linalg.norm((pr.H + Bf) @ dx.ravel()[pr.free_dofs] + gfree) / np.linalg.norm(gfree)
+    assert res <= 1e-8, res
+
+
+def test_embedded_frame_parity(fsim, ctx):
+    mesh = I.embed_finer_surface(I.two_slabs(3, 3, 2), levels=2, relief=0.02)
+    act = I.slab_actuation(mesh, seed=5)
+    m, pr = _pair(fsim, ctx, mesh, act)
+    xo, so = pr.solve_frame(mesh.rest)
+    assert so.status == 0
+    for prec, tol in ((fsim.FP64, 1e-9), (fsim.MIXED, 1e-6)):
+        rc, st = m.solve_frame(x_init=mesh.rest, precision=prec)
+        assert rc == 0 and st["contacts"] > 0
+        err = np.abs(m.positions() - xo).max() / _diag(mesh)
+        assert err <= tol, (prec, err, st["iterations"], so.iterations)
+        if prec == fsim.FP64:
+            x = m.positions()
+            _check_contact_sets(m.contacts(), OC.constraint_set(pr.W @ x, pr.tris, pr.edges,
+                                                                mesh.dhat), pr.W @ x, pr, mesh.dhat)
+
+
+# ---- Schur-only global step (dense Sigma-hat of Eq. 9, Sec. 3.1) --------------
+@pytest.mark.parametrize("prec,state,res_tol", [
+    (0, "mild", 1e-9), (0, "stiff", 1e-6), (1, "mild", 1e-6)])
+def test_schur_only_global_step_matches_direct_solve(fsim, ctx, prec, state, res_tol):
+    # the dense factorisation of Sigma-hat is backward stable (Cholesky), so
+    # float64 residuals sit at eps * cond(H-hat); mixed: a float32 factor and
+    # two float64 refinement steps (cond ~ 1.6e4 at the mild state)
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    m, pr = _pair(fsim, ctx, mesh, act, solver=fsim.SOLVER_SCHUR)
+    if state == "mild":
+        x = _contact_x(mesh, 1e-4, seed=9, gap_shift=0.0033)
+    else:
+        x = _contact_x(mesh, 3e-4, seed=9, gap_shift=0.0035)
+    dx = m.eval_global_step(x, precision=prec)
+    ev = pr.evaluate(x)
+    assert ev["C"][0].size > 0
+    g = pr.gradient(x, ev).ravel()[pr.free_dofs]
+    Bf = pr.free_part(pr.barrier_hessian(ev))
+    Hh = pr.H + Bf
+    res = np.linalg.norm(Hh @ dx.ravel()[pr.free_dofs] + g) / np.linalg.norm(g)
+    assert res <= res_tol, res
+    assert np.all(dx[mesh.pinned == 1] == 0.0)
+
+
+def test_schur_only_frame_matches_woodbury_frame(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, seed=1)
+    mw, _ = _pair(fsim, ctx, mesh, act)
+    ms, _ = _pair(fsim, ctx, mesh, act, solver=fsim.SOLVER_SCHUR)
+    for prec, tol in ((fsim.FP64, 1e-9), (fsim.MIXED, 1e-6)):
+        rc, sw = mw.solve_frame(x_init=mesh.rest, precision=prec)
+        assert rc == 0
+        xw = mw.positions()
+        rc, ss = ms.solve_frame(x_init=mesh.rest, precision=prec)
+        assert rc == 0 and ss["contacts"] > 0
+        assert np.abs(ms.positions() - xw).max() <= tol * _diag(mesh), prec
