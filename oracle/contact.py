@@ -18,6 +18,10 @@ Readings where the paper is silent:
   share no vertex; every pair is its own term.
 * PositiveDefinite: each pair's 12x12 Hessian in s-space is projected onto
   the PSD cone by clamping negative eigenvalues to zero.
+* optional EE mollifier (the paper uses IPC; IPC multiplies each edge-edge
+  term by a mollifier of the squared edge cross product, Li et al. 2020,
+  "Incremental Potential Contact"): m(c) = (2 - c/eps) c/eps below
+  eps = 1e-3 |E_a|^2 |E_b|^2 (rest edges), else 1.
 * CCD: additive CCD (Li, Kaufman & Jiang 2021, "Codimensional Incremental
   Potential Contact") with gap ratio s = 0.1 and zero thickness, on every pair
   whose swept boxes (over the step), inflated by dhat, overlap; the step bound
@@ -29,6 +33,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import distance as D
 from .distance import Hd, distance, distance_hd
 
 ACCD_MAX_ITERS = 2000
@@ -131,10 +136,63 @@ def constraint_set(s: np.ndarray, tris: np.ndarray, edges: np.ndarray, dhat: flo
     return typ[order], i[order], j[order], d[order]
 
 
-def barrier_energy(s, tris, edges, dhat, kappa) -> float:
-    """B = kappa * sum over C of b(d_k) at proxy positions s (Eq. 3)."""
-    _, _, _, d = constraint_set(s, tris, edges, dhat)
-    return float(kappa * barrier(d, dhat).sum())
+def barrier_energy(s, tris, edges, dhat, kappa, s_rest=None) -> float:
+    """B = kappa * sum over C of b(d_k) at proxy positions s (Eq. 3); with
+    s_rest, EE terms carry the mollifier m(c_k)."""
+    typ, i, j, d = constraint_set(s, tris, edges, dhat)
+    return float(kappa * pair_barrier_values(s, typ, i, j, d, tris, edges, dhat, s_rest).sum())
+
+
+# ---------------------------------------------------------------------------
+# edge-edge mollifier (IPC's treatment of nearly parallel edges; optional)
+# ---------------------------------------------------------------------------
+# For an edge-edge pair with edges e_a, e_b let c = |e_a x e_b|^2.  Below the
+# threshold eps_x = MOLLIFIER_EPS_SCALE |E_a|^2 |E_b|^2 (rest edge vectors E)
+# the pair's barrier is multiplied by m(c) = (2 - c/eps_x) c/eps_x, which is 0
+# for parallel edges, 1 with zero slope at c = eps_x, and 1 beyond; so the
+# pair's term kappa m(c) b(d) stays C^1 where the closest features of two
+# edges jump as they turn parallel.
+MOLLIFIER_EPS_SCALE = 1e-3
+
+
+def ee_mollifier_eps(s_rest: np.ndarray, edges: np.ndarray, i: np.ndarray, j: np.ndarray):
+    """eps_x of EE pairs (edge i, edge j) from the rest proxy positions."""
+    ea = s_rest[edges[i, 1]] - s_rest[edges[i, 0]]
+    eb = s_rest[edges[j, 1]] - s_rest[edges[j, 0]]
+    return MOLLIFIER_EPS_SCALE * np.einsum("ij,ij->i", ea, ea) * np.einsum("ij,ij->i", eb, eb)
+
+
+def edge_cross_sq(X: np.ndarray) -> np.ndarray:
+    """c = |(a1 - a0) x (b1 - b0)|^2 for EE pairs X (P,4,3) = (a0, a1, b0, b1)."""
+    w = np.cross(X[:, 1] - X[:, 0], X[:, 3] - X[:, 2])
+    return np.einsum("ij,ij->i", w, w)
+
+
+def mollifier(c: np.ndarray, eps: np.ndarray) -> np.ndarray:
+    q = c / eps
+    return np.where(c < eps, (2.0 - q) * q, 1.0)
+
+
+def mollifier_hd(X: np.ndarray, eps: np.ndarray) -> Hd:
+    """m(c) with gradient and Hessian in the pair's 12 coordinates."""
+    a0, a1, b0, b1 = (D._vec(X, k) for k in range(4))
+    w = D._cross3(D._sub3(a1, a0), D._sub3(b1, b0))
+    c = D._dot3(w, w)
+    q = c * (1.0 / eps)
+    m = (2.0 - q) * q
+    one = Hd(np.ones(X.shape[0]), np.zeros_like(m.g), np.zeros_like(m.h))
+    return m.select(c.v < eps, one)
+
+
+def pair_barrier_values(s, typ, i, j, d, tris, edges, dhat, s_rest=None) -> np.ndarray:
+    """b(d_k), times m(c_k) for EE pairs when s_rest (mollifier) is given."""
+    b = barrier(d, dhat)
+    if s_rest is not None:
+        ee = np.nonzero(typ == 1)[0]
+        if ee.size:
+            V = pair_vertices(typ[ee], i[ee], j[ee], tris, edges)
+            b[ee] *= mollifier(edge_cross_sq(s[V]), ee_mollifier_eps(s_rest, edges, i[ee], j[ee]))
+    return b
 
 
 # ---------------------------------------------------------------------------
@@ -147,11 +205,18 @@ def psd_project(Hs: np.ndarray) -> np.ndarray:
     return np.einsum("pik,pk,pjk->pij", Q, lam, Q)
 
 
-def pair_barrier_derivatives(s, typ, i, j, tris, edges, dhat, kappa, project=True):
-    """Per-pair kappa*b(d) gradient (P,12) and (PSD) Hessian (P,12,12)."""
+def pair_barrier_derivatives(s, typ, i, j, tris, edges, dhat, kappa, project=True, s_rest=None):
+    """Per-pair kappa*b(d) gradient (P,12) and (PSD) Hessian (P,12,12); with
+    s_rest, EE pairs take kappa*m(c)*b(d) (the mollified term)."""
     V = pair_vertices(typ, i, j, tris, edges)
     d = distance_hd(s[V], typ == 1)
     b = barrier_hd(d, dhat)
+    if s_rest is not None:
+        ee = np.nonzero(typ == 1)[0]
+        if ee.size:
+            m = mollifier_hd(s[V[ee]], ee_mollifier_eps(s_rest, edges, i[ee], j[ee]))
+            be = Hd(b.v[ee], b.g[ee], b.h[ee]) * m
+            b.v[ee], b.g[ee], b.h[ee] = be.v, be.g, be.h
     g = kappa * b.g
     h = kappa * b.h
     if project:

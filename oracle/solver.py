@@ -61,6 +61,9 @@ class Params:
     # up to KAPPA_MAX_RATIO times its initial value; every frame starts from
     # the initial value
     adaptive_kappa: bool = False
+    # IPC's edge-edge mollifier (contact.mollifier): EE terms become
+    # kappa m(c) b(d) with eps from the rest proxy (off: plain b(d))
+    ee_mollifier: bool = False
 
 
 KAPPA_GROW_BELOW = 0.1
@@ -115,6 +118,7 @@ class Problem:
             x2 |= np.asarray(region).astype(bool)
         x2 &= ~self.pinned
         self.x2_mask = x2
+        self.s_rest = (self.W @ self.rest) if params.ee_mollifier else None
         self.A = None
 
     # -- actuation ---------------------------------------------------------
@@ -132,7 +136,8 @@ class Problem:
         E = fem.elastic_energy(F, P, self.w)
         s = self.proxy(x)
         typ, i, j, d = C.constraint_set(s, self.tris, self.edges, self.p.dhat)
-        B = float(self.kappa * C.barrier(d, self.p.dhat).sum())
+        B = float(self.kappa * C.pair_barrier_values(s, typ, i, j, d, self.tris, self.edges,
+                                                     self.p.dhat, self.s_rest).sum())
         return {"F": F, "R": R, "P": P, "E": E, "s": s, "C": (typ, i, j, d), "B": B}
 
     def energy(self, x):
@@ -142,7 +147,8 @@ class Problem:
     def _pair_terms(self, ev, project=True):
         typ, i, j, _ = ev["C"]
         return C.pair_barrier_derivatives(ev["s"], typ, i, j, self.tris, self.edges,
-                                          self.p.dhat, self.kappa, project=project)
+                                          self.p.dhat, self.kappa, project=project,
+                                          s_rest=self.s_rest)
 
     def gradient(self, x, ev):
         """g-hat over all vertices (n,3): elastic term + W^T grad B(s)."""
