@@ -108,7 +108,11 @@ typedef struct {
                                0.1 d0 and smaller than at the previous iterate,
                                up to 100 times its start value; every frame
                                starts from the mesh's kappa                   */
-  int32_t reserved1;
+  int32_t ee_mollifier;     /* nonzero: IPC's edge-edge mollifier -- each EE
+                               term becomes kappa m(c) b(d) with c = |e_a x
+                               e_b|^2, m(c) = (2 - c/eps) c/eps below
+                               eps = 1e-3 |E_a|^2 |E_b|^2 (rest proxy edges),
+                               1 above; 0 (default): plain b(d)              */
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1

@@ -635,15 +635,18 @@ fsim_status fsim_mesh_upload(fsim_ctx_t ctx, int* mesh_id, const double* rest_xy
       for (int64_t e = W_rowptr[r]; e < W_rowptr[r + 1]; ++e)
         for (int d = 0; d < 3; ++d) sr[3 * r + d] += W_val[e] * rest_xyz[3 * (int64_t)W_col[e] + d];
     double sum = 0.0;
+    std::vector<double> el2(std::max<size_t>(ed.size(), 1), 0.0);
     for (size_t k = 0; k < ed.size(); ++k) {
       double l2 = 0.0;
       for (int d = 0; d < 3; ++d) {
         const double q = sr[3 * ed[k].first + d] - sr[3 * ed[k].second + d];
         l2 += q * q;
       }
+      el2[k] = l2;
       sum += std::sqrt(l2);
     }
     ms.mean_edge = ed.empty() ? 0.0 : sum / (double)ed.size();
+    TRY(upload(ms, s, &m.elen2, el2.data(), el2.size()));
   }
   m.n_partials = std::max(elastic_blocks(m.T), gnorm_blocks(m.n)) + 16;
   CK(cudaStreamSynchronize(s));
@@ -769,6 +772,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
     CK(cudaStreamSynchronize(s));
   }
   m.skin = p->skin > 0.0 ? p->skin : std::max(10.0 * p->dhat, 0.25 * ms.mean_edge);
+  m.ee_moll = p->ee_mollifier ? 1 : 0;
   m.cap_act = p->active_capacity > 0 ? p->active_capacity
                                      : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));
   m.cap_act = std::min(m.cap_act, m.cap);

@@ -354,4 +354,58 @@ __device__ void pair_reduced(int type, const double X[4][3], double dhat, double
     }
 }
 
+// ---------------------------------------------------------------------------
+// Edge-edge mollifier (optional; IPC's treatment of nearly parallel edges):
+// with c = |e_a x e_b|^2 and eps = 1e-3 |E_a|^2 |E_b|^2 at rest, the EE term
+// becomes kappa m(c) b(d), m(c) = (2 - c/eps) c/eps for c < eps, else 1.
+// ---------------------------------------------------------------------------
+#define FSIM_MOLLIFIER_EPS_SCALE 1e-3
+
+struct EdgeCross {
+  double ea[3], eb[3];   // a1 - a0, b1 - b0
+  double aa, bb, ab;     // ea.ea, eb.eb, ea.eb
+  double c;              // |ea x eb|^2
+};
+
+__device__ __forceinline__ void edge_cross(const double X[4][3], EdgeCross& e) {
+  for (int d = 0; d < 3; ++d) {
+    e.ea[d] = X[1][d] - X[0][d];
+    e.eb[d] = X[3][d] - X[2][d];
+  }
+  const double w0 = e.ea[1] * e.eb[2] - e.ea[2] * e.eb[1];
+  const double w1 = e.ea[2] * e.eb[0] - e.ea[0] * e.eb[2];
+  const double w2 = e.ea[0] * e.eb[1] - e.ea[1] * e.eb[0];
+  e.c = w0 * w0 + w1 * w1 + w2 * w2;
+  e.aa = dot3(e.ea, e.ea);
+  e.bb = dot3(e.eb, e.eb);
+  e.ab = dot3(e.ea, e.eb);
+}
+
+__device__ __forceinline__ double mollifier_value(double c, double eps) {
+  if (!(c < eps)) return 1.0;
+  const double q = c / eps;
+  return (2.0 - q) * q;
+}
+
+// d c / d X[I][al] (vertices a0, a1, b0, b1)
+__device__ __forceinline__ double edge_cross_grad(const EdgeCross& e, int I, int al) {
+  const double ga = 2.0 * (e.ea[al] * e.bb - e.ab * e.eb[al]);
+  const double gb = 2.0 * (e.eb[al] * e.aa - e.ab * e.ea[al]);
+  const double g = (I < 2) ? ga : gb;
+  return (I == 0 || I == 2) ? -g : g;
+}
+
+// d^2 c / d X[I][al] d X[J][be]
+__device__ __forceinline__ double edge_cross_hess(const EdgeCross& e, int I, int al, int J, int be) {
+  const double dl = (al == be) ? 1.0 : 0.0;
+  const int ei = I >> 1, ej = J >> 1;     // 0: edge a, 1: edge b
+  double h;
+  if (ei == 0 && ej == 0) h = 2.0 * e.bb * dl - 2.0 * e.eb[al] * e.eb[be];
+  else if (ei == 1 && ej == 1) h = 2.0 * e.aa * dl - 2.0 * e.ea[al] * e.ea[be];
+  else if (ei == 0) h = 4.0 * e.ea[al] * e.eb[be] - 2.0 * e.eb[al] * e.ea[be] - 2.0 * e.ab * dl;
+  else h = 4.0 * e.ea[be] * e.eb[al] - 2.0 * e.eb[be] * e.ea[al] - 2.0 * e.ab * dl;
+  const double si = (I == 0 || I == 2) ? -1.0 : 1.0, sj = (J == 0 || J == 2) ? -1.0 : 1.0;
+  return si * sj * h;
+}
+
 }  // namespace fsim

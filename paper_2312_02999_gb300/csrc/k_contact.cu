@@ -317,6 +317,122 @@ k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long 
   }
 }
 
+// Edge-edge mollifier (optional): for EE pairs with c = |e_a x e_b|^2 below
+// eps = 1e-3 |E_a|^2 |E_b|^2 the pair term is kappa m(c) b(d); this pass
+// overwrites those pairs' gradient and Hessian blocks written by
+// k_barrier_pairs.  The 12 x 12 Hessian
+//   m H_b + kappa b (m'' grad c grad c^T + m' hess c) + m' (grad c G^T + G grad c^T)
+// (H_b, G: kappa b's Hessian and gradient, lifted from the reduced basis) is
+// projected onto the PSD cone by a cyclic Jacobi eigen-solve in float64 (one
+// warp per pair, lane-parallel rotations), whatever the precision.
+__global__ void __launch_bounds__(32) k_mollify_ee(const int* __restrict__ count, int64_t cap,
+                                                   const unsigned long long* __restrict__ pairs,
+                                                   const double* __restrict__ s,
+                                                   const int* __restrict__ edges,
+                                                   const double* __restrict__ elen2, double dhat,
+                                                   double kappa, double* __restrict__ pgrad,
+                                                   double* __restrict__ phess) {
+  __shared__ double As[12][13];
+  __shared__ double Qs[12][13];
+  __shared__ double gcs[12], Gs[12];
+  const int lane = threadIdx.x;
+  int64_t np = *count;
+  np = np < cap ? np : cap;
+  for (int64_t p = blockIdx.x; p < np; p += gridDim.x) {
+    int type, i, j;
+    unpack_key(pairs[p], type, i, j);
+    if (type != 1) continue;
+    const double eps = FSIM_MOLLIFIER_EPS_SCALE * elen2[i] * elen2[j];
+    int V[4];
+    load_pair(type, i, j, nullptr, edges, V);
+    double X[4][3];
+    gather_X(s, V, X);
+    EdgeCross ec;
+    edge_cross(X, ec);
+    if (!(ec.c < eps)) continue;                  // warp-uniform
+    PairReduced r;
+    pair_reduced(1, X, dhat, kappa, r);
+    const double u = r.d - dhat;
+    const double kb = kappa * (-u * u * log(r.d / dhat));
+    const double q = ec.c / eps;
+    const double m0 = (2.0 - q) * q, m1 = (2.0 - 2.0 * q) / eps, m2 = -2.0 / (eps * eps);
+    if (lane < 12) {
+      const int I = lane / 3, al = lane % 3;
+      gcs[lane] = edge_cross_grad(ec, I, al);
+      Gs[lane] = r.gfac * r.c[I] * r.vh[al];
+    }
+    __syncwarp();
+    if (lane < 12) pgrad[p * 12 + lane] = m0 * Gs[lane] + kb * m1 * gcs[lane];
+    for (int e = lane; e < 144; e += 32) {
+      const int a = e / 12, b = e % 12;
+      const int I = a / 3, al = a % 3, J = b / 3, be = b % 3;
+      double bp[5], bq[5];
+      for (int t = 0; t < 3; ++t) {
+        bp[t] = (al == t) ? r.ch[I] : 0.0;
+        bq[t] = (be == t) ? r.ch[J] : 0.0;
+      }
+      for (int t = 0; t < 2; ++t) {
+        bp[3 + t] = r.q[t][I] * r.vh[al];
+        bq[3 + t] = r.q[t][J] * r.vh[be];
+      }
+      double hb = 0.0;
+      for (int x = 0; x < r.n; ++x)
+        for (int y = 0; y < r.n; ++y) hb += bp[x] * r.A[x][y] * bq[y];
+      As[a][b] = m0 * hb + kb * (m2 * gcs[a] * gcs[b] + m1 * edge_cross_hess(ec, I, al, J, be)) +
+                 m1 * (gcs[a] * Gs[b] + Gs[a] * gcs[b]);
+      Qs[a][b] = (a == b) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      double off = 0.0, dia = 0.0;
+      for (int a = 0; a < 12; ++a) {
+        dia += As[a][a] * As[a][a];
+        for (int b = a + 1; b < 12; ++b) off += As[a][b] * As[a][b];
+      }
+      if (!(off > 1e-30 * dia)) break;
+      for (int pp = 0; pp < 11; ++pp)
+        for (int qq = pp + 1; qq < 12; ++qq) {
+          const double apq = As[pp][qq];
+          if (!(fabs(apq) > 1e-300)) continue;
+          const double app = As[pp][pp], aqq = As[qq][qq];
+          const double th = (aqq - app) / (2.0 * apq);
+          const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+          const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+          double x0 = 0.0, x1 = 0.0;
+          const bool rowl = lane < 12 && lane != pp && lane != qq;
+          const bool qlan = lane >= 16 && lane < 28;
+          if (rowl) { x0 = As[lane][pp]; x1 = As[lane][qq]; }
+          if (qlan) { x0 = Qs[lane - 16][pp]; x1 = Qs[lane - 16][qq]; }
+          __syncwarp();
+          if (rowl) {
+            const double np_ = c * x0 - sn * x1, nq = sn * x0 + c * x1;
+            As[lane][pp] = np_; As[pp][lane] = np_;
+            As[lane][qq] = nq; As[qq][lane] = nq;
+          }
+          if (qlan) {
+            Qs[lane - 16][pp] = c * x0 - sn * x1;
+            Qs[lane - 16][qq] = sn * x0 + c * x1;
+          }
+          if (lane == 12) As[pp][pp] = app - t * apq;
+          if (lane == 13) As[qq][qq] = aqq + t * apq;
+          if (lane == 14) { As[pp][qq] = 0.0; As[qq][pp] = 0.0; }
+          __syncwarp();
+        }
+    }
+    for (int e = lane; e < 144; e += 32) {
+      const int a = e / 12, b = e % 12;
+      double acc = 0.0;
+      for (int l = 0; l < 12; ++l) {
+        const double lam = As[l][l];
+        if (lam > 0.0) acc += Qs[a][l] * lam * Qs[b][l];
+      }
+      const int I = a / 3, al = a % 3, J = b / 3, be = b % 3;
+      phess[p * 144 + (I * 4 + J) * 9 + al * 3 + be] = acc;
+    }
+    __syncwarp();
+  }
+}
+
 // x2mark (0/1 flags) -> x2mark[q] = c position + 1 (0 if untouched); clist; nc.
 __global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ clist,
                             int* __restrict__ counters) {
@@ -645,6 +761,7 @@ __global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, in
                              const unsigned long long* __restrict__ nearl,
                              const double* __restrict__ s, const int* __restrict__ tris,
                              const int* __restrict__ edges, double dhat, double kappa,
+                             const double* __restrict__ elen2,
                              unsigned long long* __restrict__ pairs, int* counters,
                              double* __restrict__ scal) {
   int64_t n = *near_count;
@@ -661,7 +778,13 @@ __global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, in
     const double d = pair_distance(type, X);
     if (d < dhat) {
       append(pack_key(type, i, j), pairs, counters + 0, counters + 2, cap_act);
-      esum += barrier_value(d, dhat);
+      double bv = barrier_value(d, dhat);
+      if (elen2 != nullptr && type == 1) {     // edge-edge mollifier
+        EdgeCross ec;
+        edge_cross(X, ec);
+        bv *= mollifier_value(ec.c, FSIM_MOLLIFIER_EPS_SCALE * elen2[i] * elen2[j]);
+      }
+      esum += bv;
       if (!(d > 0.0)) atomicOr(counters + 5, 1);
       else   // smallest active distance (positive doubles order like their bits)
         atomicMin(reinterpret_cast<unsigned long long*>(scal + 4), (unsigned long long)__double_as_longlong(d));
@@ -861,8 +984,8 @@ void launch_detect(cudaStream_t st, const DevMesh& m, const double* sp, double d
   k_skin_near<<<2 * 152, 128, 0, st>>>(m.counters, m.cap, m.vlist, m.sf, m.tris, m.edges,
                                        2.0f * (float)dhat, m.nearl, m.counters + 8, m.counters + 2);
   k_near_pairs<<<2 * 152, 128, 0, st>>>(m.counters + 8, m.cap, m.cap_act, m.nearl, sp, m.tris,
-                                        m.edges, dhat,
-                                        kappa, m.pairs, m.counters, m.scal);
+                                        m.edges, dhat, kappa, m.ee_moll ? m.elen2 : nullptr,
+                                        m.pairs, m.counters, m.scal);
   count_launch(4);
 }
 
@@ -906,6 +1029,11 @@ void launch_barrier_pairs(cudaStream_t st, const DevMesh& m, int64_t np, const d
         m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);
   count_launch();
+  if (m.ee_moll) {
+    k_mollify_ee<<<grid, 32, 0, st>>>(m.counters, m.cap_act, m.pairs, sp, m.edges, m.elen2, dhat,
+                                      kappa, m.pair_grad, m.pair_hess);
+    count_launch();
+  }
 }
 
 void launch_mark_scan(cudaStream_t st, const DevMesh& m) {

@@ -776,13 +776,58 @@ __global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
 }
 
 // q = (L_s (x) I_3)^T p (float; L_s packed plain, in shared memory)
+// (one warp per entry)
 __device__ void cta_lt_apply_f(const float* Lp, int nc, const double* p, float* q) {
-  for (int e = threadIdx.x; e < 3 * nc; e += kST) {
+  const int lane = threadIdx.x & 31;
+  for (int e = threadIdx.x >> 5; e < 3 * nc; e += kSW) {
     const int i = e / 3, ax = e % 3;
     float acc = 0.f;
-    for (int j = i; j < nc; ++j) acc += Lp[prow(j) + i] * (float)p[3 * j + ax];
-    q[e] = acc;
+    for (int j = i + lane; j < nc; j += 32) acc += Lp[prow(j) + i] * (float)p[3 * j + ax];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) q[e] = acc;
   }
+}
+
+// Refinement products in float64, one warp per row (warp w of nw):
+// w = S v with S = Sigma^-1[c, c] (x) I_3 (gathered into S64 by k_small_s)
+__device__ void refine_sv(const RedArgs<float>& a, int nc, int w, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int e = w; e < 3 * nc; e += nw) {
+    const int i = e / 3, ax = e % 3;
+    const double* srow = a.S64 + (size_t)i * nc;
+    double acc = 0.0;
+    for (int j = lane; j < nc; j += 32) acc += srow[j] * a.v[3 * j + ax];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.w[e] = acc;
+  }
+}
+
+// rho = y - v - B w over the block-row lists of B; returns this lane's share
+// of |rho|^2 (lane 0 of each warp holds it)
+__device__ double refine_rho(const RedArgs<float>& a, int nc, int w, int nw) {
+  const int lane = threadIdx.x & 31, n3 = 3 * nc;
+  double r2 = 0.0;
+  for (int row = w; row < n3; row += nw) {
+    const int i = row / 3;
+    const double* brow = a.Bc + (size_t)row * n3;
+    const int* li = a.list + (size_t)i * nc;
+    double acc = 0.0;
+    for (int e = lane; e < a.cnt[i]; e += 32) {
+      const int j = li[e];
+      acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
+             brow[3 * j + 2] * a.w[3 * j + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double rr = a.y[row] - a.v[row] - acc;
+      a.rho[row] = rr;
+      r2 += rr * rr;
+    }
+  }
+  return r2;
 }
 
 // k_small_v (1 CTA): L_N in shared memory, v = (L_s (x) I)^-T N^-1 (L_s (x) I)^T y
@@ -821,33 +866,9 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   double prev = -1.0;
   for (int it = 0; it < a.refine; ++it) {
     // w = S v with S = Sigma^-1[c, c] (x) I_3 in float64 (S gathered by k_small_s)
-    for (int e = tid; e < n3; e += kST) {
-      const int i = e / 3, ax = e % 3;
-      const double* srow = a.S64 + (size_t)i * nc;
-      double acc0 = 0.0, acc1 = 0.0;
-      int j = 0;
-      for (; j + 1 < nc; j += 2) {
-        acc0 += srow[j] * a.v[3 * j + ax];
-        acc1 += srow[j + 1] * a.v[3 * j + 3 + ax];
-      }
-      if (j < nc) acc0 += srow[j] * a.v[3 * j + ax];
-      a.w[e] = acc0 + acc1;
-    }
+    refine_sv(a, nc, tid >> 5, kSW);
     __syncthreads();
-    double r2 = 0.0;
-    for (int row = tid; row < n3; row += kST) {
-      const int i = row / 3;
-      const double* brow = a.Bc + (size_t)row * n3;
-      double acc = 0.0;
-      for (int e = 0; e < a.cnt[i]; ++e) {
-        const int j = a.list[(size_t)i * nc + e];
-        acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
-               brow[3 * j + 2] * a.w[3 * j + 2];
-      }
-      const double rr = a.y[row] - a.v[row] - acc;
-      a.rho[row] = rr;
-      r2 += rr * rr;
-    }
+    double r2 = refine_rho(a, nc, tid >> 5, kSW);
     r2 = block_sum_d(r2, red);
     const double ys = __ldcg(a.nrm + 2);
     if (!(r2 > 1e-14 * ys)) break;
@@ -1178,16 +1199,17 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
     cl.sync();
   };
   // t = (L_s (x) I_3)^T p on own rows
-  auto lt_own = [&](const double* p) {
-    for (int b = rank; b < nblk; b += kCl)
-      for (int e = tid; e < 32; e += kST) {
-        const int r = 32 * b + e;
-        if (r >= n3) continue;
-        const int i = r / 3, ax = r % 3;
-        float acc = 0.f;
-        for (int j = i; j < nc; ++j) acc += Ls[prow(j) + i] * (float)p[3 * j + ax];
-        t[r] = acc;
-      }
+  auto lt_own = [&](const double* p) {     // one warp per own row
+    for (int idx = wid; idx < kClusRowsMax; idx += kSW) {
+      const int r = 32 * (((idx >> 5) * kCl) + rank) + (idx & 31);
+      if (r >= n3) continue;
+      const int i = r / 3, ax = r % 3;
+      float acc = 0.f;
+      for (int j = i + lane; j < nc; j += 32) acc += Ls[prow(j) + i] * (float)p[3 * j + ax];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) t[r] = acc;
+    }
     __syncthreads();
   };
   lt_own(a.y);
@@ -1196,29 +1218,11 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
 
   // ---- float64 refinement, rows split over the cluster ----------------------
   double prev = -1.0;
+  const int gw = rank * kSW + wid;                 // one warp per row, rows split over the cluster
   for (int it = 0; it < a.refine; ++it) {
-    for (int e = rank * kST + tid; e < n3; e += kCl * kST) {
-      const int i = e / 3, ax = e % 3;
-      const double* srow = a.S64 + (size_t)i * nc;
-      double acc = 0.0;
-      for (int j = 0; j < nc; ++j) acc += srow[j] * a.v[3 * j + ax];
-      a.w[e] = acc;
-    }
+    refine_sv(a, nc, gw, kCl * kSW);
     cl.sync();
-    double r2 = 0.0;
-    for (int row = rank * kST + tid; row < n3; row += kCl * kST) {
-      const int i = row / 3;
-      const double* brow = a.Bc + (size_t)row * n3;
-      double acc = 0.0;
-      for (int e = 0; e < a.cnt[i]; ++e) {
-        const int j = a.list[(size_t)i * nc + e];
-        acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
-               brow[3 * j + 2] * a.w[3 * j + 2];
-      }
-      const double rr = a.y[row] - a.v[row] - acc;
-      a.rho[row] = rr;
-      r2 += rr * rr;
-    }
+    double r2 = refine_rho(a, nc, gw, kCl * kSW);
     r2 = block_sum_d(r2, red);
     if (tid < kCl) cl.map_shared_rank(&nrm_parts[0], tid)[rank] = r2;
     cl.sync();

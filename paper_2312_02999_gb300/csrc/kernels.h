@@ -47,6 +47,8 @@ struct DevMesh {
   double* cg_tmp = nullptr;
   double* cg_red = nullptr;
   double* sb = nullptr;       // 3 Ns proxy positions of the last skin-list build
+  double* elen2 = nullptr;    // Ne squared rest lengths of the proxy edges (EE mollifier)
+  int ee_moll = 0;            // 1: edge-edge terms carry IPC's mollifier
   double skin = 0.0;          // skin width of the list (length)
   double coord_scale = 1.0;   // 2 x largest |rest coordinate|
   // solver ordering

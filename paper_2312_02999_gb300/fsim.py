@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
                 ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
                 ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double), ("adaptive_kappa", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("ee_mollifier", C.c_int32)]
 
 
 class FrameStats(C.Structure):

@@ -482,3 +482,60 @@ def test_schur_only_frame_matches_woodbury_frame(fsim, ctx):
         rc, ss = ms.solve_frame(x_init=mesh.rest, precision=prec)
         assert rc == 0 and ss["contacts"] > 0
         assert np.abs(ms.positions() - xw).max() <= tol * _diag(mesh), prec
+
+
+# ---- IPC's edge-edge mollifier (optional) -------------------------------------
+def _moll_pair(fsim, ctx, mesh, act):
+    m = ctx.upload(mesh)
+    p = fsim.params_for(mesh, ee_mollifier=1)
+    m.prefactor(p)
+    m.set_actuation(act.fiber, act.stretch)
+    k = m.info()["kappa"]
+    pr = S.Problem(mesh.rest, mesh.tets, mesh.pinned, mesh.proxy_tris, mesh.W_rowptr, mesh.W_col,
+                   mesh.W_val, S.Params(dhat=mesh.dhat, tol_abs=p.tol_abs, tol_rel=p.tol_rel,
+                                        kappa=k, max_iters=p.max_iters,
+                                        weight_scale=mesh.weight_scale, ee_mollifier=True),
+                   region=mesh.region)
+    pr.set_actuation(act.fiber, act.stretch)
+    return m, pr
+
+
+def test_mollified_energy_gradient_and_block(fsim, ctx):
+    # the slabs' facing grid edges are parallel at rest, so after a small
+    # perturbation many active EE pairs have c far below eps
+    mesh = I.two_slabs(4, 4, 2, gap=0.004)
+    act = I.slab_actuation(mesh, seed=11)
+    m, pr = _moll_pair(fsim, ctx, mesh, act)
+    x = _contact_x(mesh, 3e-4, seed=7, gap_shift=0.0035)
+    ev = pr.evaluate(x)
+    typ, i, j, _ = ev["C"]
+    ee = typ == 1
+    V = OC.pair_vertices(typ[ee], i[ee], j[ee], pr.tris, pr.edges)
+    moll = OC.edge_cross_sq(ev["s"][V]) < OC.ee_mollifier_eps(pr.s_rest, pr.edges, i[ee], j[ee])
+    assert moll.sum() >= 5
+    keys, B = m.eval_contacts(x)
+    assert abs(B - ev["B"]) <= 1e-10 * abs(ev["B"])
+    g, clist, Bc = m.eval_barrier(x)
+    Vp, gp, _ = pr._pair_terms(ev, project=False)
+    gs = np.zeros((pr.W.shape[0], 3))
+    np.add.at(gs, Vp.ravel(), gp.reshape(-1, 3))
+    assert _rel(g, pr.W.T @ gs) <= 1e-9
+    Bfull = pr.barrier_hessian(ev, project=True).toarray()
+    cv = np.nonzero(pr.x2_mask)[0][clist]
+    idx = (3 * cv[:, None] + np.arange(3)).ravel()
+    assert _rel(Bc, Bfull[np.ix_(idx, idx)]) <= 1e-8
+    E, gn = m.eval_energy(x)
+    assert abs(E - (ev["E"] + ev["B"])) <= 1e-10 * abs(ev["E"] + ev["B"])
+
+
+def test_mollified_frame_parity(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    act = I.slab_actuation(mesh, seed=5)
+    m, pr = _moll_pair(fsim, ctx, mesh, act)
+    xo, so = pr.solve_frame(mesh.rest)
+    assert so.status == 0
+    for prec, tol in ((fsim.FP64, 1e-9), (fsim.MIXED, 1e-6)):
+        rc, st = m.solve_frame(x_init=mesh.rest, precision=prec)
+        assert rc == 0 and st["contacts"] > 0
+        err = np.abs(m.positions() - xo).max() / _diag(mesh)
+        assert err <= tol, (prec, err, st["iterations"], so.iterations)
