@@ -254,8 +254,9 @@ int with_graph(const Exec& ex, DevMesh& m, int slot, const void* key, int key2, 
   return FSIM_OK;
 }
 
-// graph slots: 0-1 global step (by precision), 2-5 evaluation (by position
-// buffer and precision), 6-7 CCD (by proxy-position buffer)
+// graph slots: 0-5 global step (by precision and reduced-system path), 6-9
+// evaluation (by position buffer and precision), 10-11 CCD (by proxy-position
+// buffer)
 int graph_slot(const DevMesh& m, int first, int count, const void* key, int key2) {
   for (int k = first; k < first + count; ++k)
     if (m.graphs[k].exec && m.graphs[k].key == key && m.graphs[k].key2 == key2) return k;
@@ -349,7 +350,7 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     d_prev = d_min;
   };
   auto eval_at = [&](double* xb, double* sb, double* tetf) -> int {
-    const int slot = graph_slot(m, 2, 4, xb, prec);
+    const int slot = graph_slot(m, 6, 4, xb, prec);
     return with_graph(ex, m, slot, xb, prec, kgen,
                       [&] { return evaluate(ex, ms, m, xb, sb, tetf, nullptr, prec, kappa); });
   };
@@ -387,17 +388,19 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
         return FSIM_ECUDA;
       st.cg_iterations += cg_it;
     } else {
-      TRY(with_graph(ex, m, prec, m.g, prec, m.red_gen, [&]() -> int {
+      // one graph per precision and reduced-system path (n_c decides the path)
+      const bool schur = p.solver == FSIM_SOLVER_SCHUR;
+      const int gkey = 8 * prec + (schur ? 4 : reduced_path(nc, prec));
+      TRY(with_graph(ex, m, graph_slot(m, 0, 6, m.g, gkey), m.g, gkey, m.red_gen, [&]() -> int {
         CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone,
-                       p.solver == FSIM_SOLVER_SCHUR));
+        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone, schur, nc));
         return FSIM_OK;
       }));
     }
     st.sum_nc3 += (double)nc * nc * nc;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
-    TRY(with_graph(ex, m, graph_slot(m, 6, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
+    TRY(with_graph(ex, m, graph_slot(m, 10, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
       launch_proxy(s, m, m.dx, m.ds);
       launch_ccd_reset(s, m);
       launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
@@ -1049,7 +1052,7 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
       return FSIM_ECUDA;
   } else {
     CK(global_step(s, m, ms->gtmp, ms->dxtmp, precision, m.counters + 6, ex.coop_ctas, ex.alone,
-                   ms->p.solver == FSIM_SOLVER_SCHUR));
+                   ms->p.solver == FSIM_SOLVER_SCHUR, nc));
   }
   TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;

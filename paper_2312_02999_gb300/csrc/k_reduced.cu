@@ -271,6 +271,45 @@ __device__ void cta_lt_apply(const FT* L, int nc, const VT* p, FT* q) {
   }
 }
 
+// z2 = u - (Sigma^-1[:, c] (x) I_3) v, one warp per row (warp w of nw)
+template <typename FT>
+__device__ void z2_update(const RedArgs<FT>& a, int nc, int w, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int q = w; q < a.n2; q += nw) {
+    const double* srow = a.Sinv + (size_t)q * a.n2;
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int m = lane; m < nc; m += 32) {
+      const double sv = srow[a.clist[m]];
+      a0 += sv * a.v[3 * m]; a1 += sv * a.v[3 * m + 1]; a2 += sv * a.v[3 * m + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+      a.z2[3 * q] = a.u[3 * q] - a0;
+      a.z2[3 * q + 1] = a.u[3 * q + 1] - a1;
+      a.z2[3 * q + 2] = a.u[3 * q + 2] - a2;
+    }
+  }
+}
+
+// The z2 update alone (plain launch) after the one-CTA or cluster path; with
+// n_c = 0 it copies z2 = u.
+__global__ void __launch_bounds__(256) k_z2_update(RedArgs<float> a) {
+  const int nc = *a.nc_dev;
+  if (nc == 0) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * a.n2; e += gridDim.x * blockDim.x)
+      a.z2[e] = a.u[e];
+    return;
+  }
+  if (nc > a.small_lim) return;         // the cooperative kernel owns larger n_c
+  red_layout(a, nc);
+  z2_update(a, nc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
 template <typename FT>
 __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
   cg::grid_group grid = cg::this_grid();
@@ -414,26 +453,8 @@ __global__ void __launch_bounds__(kRT) k_reduced(RedArgs<FT> a) {
       grid.sync();
     }
   }
-  // 8. z2 = u - (Sigma^-1[:, c] (x) I_3) v, one warp per row
-  for (int q = gwarp; q < a.n2; q += nwarps) {
-    const double* srow = a.Sinv + (size_t)q * a.n2;
-    double a0 = 0, a1 = 0, a2 = 0;
-    for (int m = lane; m < nc; m += 32) {
-      const double sv = srow[a.clist[m]];
-      a0 += sv * a.v[3 * m]; a1 += sv * a.v[3 * m + 1]; a2 += sv * a.v[3 * m + 2];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    if (lane == 0) {
-      a.z2[3 * q] = a.u[3 * q] - a0;
-      a.z2[3 * q + 1] = a.u[3 * q + 1] - a1;
-      a.z2[3 * q + 2] = a.u[3 * q + 2] - a2;
-    }
-  }
+  // 8. z2 = u - (Sigma^-1[:, c] (x) I_3) v
+  z2_update(a, nc, gwarp, nwarps);
 }
 
 // ---------------------------------------------------------------------------
@@ -692,6 +713,7 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
   if (tid == 0) a.nrm[2] = 0.0;
   for (int i = wid; i < nc; i += kSW) {
     const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
+#pragma unroll 4
     for (int j = lane; j < nc; j += 32) {
       const double sv = srow[a.clist[j]];
       a.S64[(size_t)i * nc + j] = sv;
@@ -699,12 +721,17 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
     }
   }
   for (int i = wid; i < nc; i += kSW) {
+    bool f[kClusNc / 32];                 // all occupancy flags of the row first
+#pragma unroll
+    for (int q = 0; q < kClusNc / 32; ++q) {
+      const int j = 32 * q + lane;
+      f[q] = j < nc && a.bocc[(size_t)i * nc + j] != 0;
+    }
     int base = 0;
-    for (int j0 = 0; j0 < nc; j0 += 32) {
-      const int j = j0 + lane;
-      const bool f = j < nc && a.bocc[(size_t)i * nc + j] != 0;
-      const unsigned msk = __ballot_sync(0xffffffffu, f);
-      if (f) a.list[(size_t)i * nc + base + __popc(msk & ((1u << lane) - 1u))] = j;
+#pragma unroll
+    for (int q = 0; q < kClusNc / 32; ++q) {
+      const unsigned msk = __ballot_sync(0xffffffffu, f[q]);
+      if (f[q]) a.list[(size_t)i * nc + base + __popc(msk & ((1u << lane) - 1u))] = 32 * q + lane;
       base += __popc(msk);
     }
     if (lane == 0) a.cnt[i] = base;
@@ -732,7 +759,9 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
     const int i = row / 3;
     const double* brow = a.Bc + (size_t)row * n3;
     double acc = 0.0;
-    for (int e = 0; e < a.cnt[i]; ++e) {
+    const int ci = a.cnt[i];
+#pragma unroll 4
+    for (int e = 0; e < ci; ++e) {
       const int j = a.list[(size_t)i * nc + e];
       const double* uj = a.u + 3 * (size_t)a.clist[j];
       acc += brow[3 * j] * uj[0] + brow[3 * j + 1] * uj[1] + brow[3 * j + 2] * uj[2];
@@ -750,7 +779,9 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
     const int i = row / 3, k = colx / 3, b = colx % 3;
     const double* brow = a.Bc + (size_t)row * n3;
     float acc = 0.f;
-    for (int q = 0; q < a.cnt[i]; ++q) {
+    const int ci = a.cnt[i];
+#pragma unroll 4
+    for (int q = 0; q < ci; ++q) {
       const int j = a.list[(size_t)i * nc + q];
       if (j >= k) acc += (float)brow[3 * j + b] * a.S[(size_t)j * nc + k];
     }
@@ -770,6 +801,7 @@ __global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
     if (col > row) continue;
     const int i = row / 3, ax = row % 3;
     float acc = (row == col) ? 1.f : 0.f;
+#pragma unroll 8
     for (int j = i; j < nc; ++j) acc += a.S[(size_t)j * nc + i] * a.X[(size_t)(3 * j + ax) * n3 + col];
     a.N[prow(row) + col] = acc;        // packed lower, the layout k_small_v factors in
   }
@@ -782,6 +814,7 @@ __device__ void cta_lt_apply_f(const float* Lp, int nc, const double* p, float* 
   for (int e = threadIdx.x >> 5; e < 3 * nc; e += kSW) {
     const int i = e / 3, ax = e % 3;
     float acc = 0.f;
+#pragma unroll 4
     for (int j = i + lane; j < nc; j += 32) acc += Lp[prow(j) + i] * (float)p[3 * j + ax];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -797,6 +830,7 @@ __device__ void refine_sv(const RedArgs<float>& a, int nc, int w, int nw) {
     const int i = e / 3, ax = e % 3;
     const double* srow = a.S64 + (size_t)i * nc;
     double acc = 0.0;
+#pragma unroll 4
     for (int j = lane; j < nc; j += 32) acc += srow[j] * a.v[3 * j + ax];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -814,7 +848,9 @@ __device__ double refine_rho(const RedArgs<float>& a, int nc, int w, int nw) {
     const double* brow = a.Bc + (size_t)row * n3;
     const int* li = a.list + (size_t)i * nc;
     double acc = 0.0;
-    for (int e = lane; e < a.cnt[i]; e += 32) {
+    const int ci = a.cnt[i];
+#pragma unroll 4
+    for (int e = lane; e < ci; e += 32) {
       const int j = li[e];
       acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
              brow[3 * j + 2] * a.w[3 * j + 2];
@@ -847,6 +883,7 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   {   // packed N (padding included: prow(n3) is a multiple of 4)
     const float4* src = reinterpret_cast<const float4*>(a.N);
     float4* dst = reinterpret_cast<float4*>(A);
+#pragma unroll 4
     for (int e = tid; e < prow(n3) / 4; e += kST) dst[e] = src[e];
   }
   __syncthreads();
@@ -854,6 +891,7 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   // L_s (packed plain + inverted diagonal blocks) into the panel scratch
   float* Ls = Pt;
   const float* LsDI = Pt + prow(nc);
+#pragma unroll 4
   for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
   __syncthreads();
   cta_lt_apply_f(Ls, nc, a.y, t);
@@ -952,11 +990,13 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
   auto Ael = [&](int r, int c) -> float& { return A[loff[lrow(r)] + c]; };
   // load own rows of the packed N and L_s
   for (int b = rank; b < nblk; b += kCl)
+#pragma unroll 4
     for (int e = tid; e < 32 * 32 * (b + 1); e += kST) {
       const int rr = e / (32 * (b + 1)), c = e % (32 * (b + 1));
       const int r = b * 32 + rr;
       if (r < n3 && c <= r) Ael(r, c) = a.N[prow(r) + c];
     }
+#pragma unroll 4
   for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
   __syncthreads();
 
@@ -1022,6 +1062,7 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
       const float* rD = cl.map_shared_rank(&Ds[0][0], owner);
       const float* rL = cl.map_shared_rank(&Li[0][0], owner);
       const float* rv = cl.map_shared_rank(&dv[0], owner);
+#pragma unroll
       for (int e = tid; e < 32 * 33; e += kST) {
         (&Ds[0][0])[e] = rD[e];
         (&Li[0][0])[e] = rL[e];
@@ -1060,6 +1101,7 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
       for (int b = q; b < nblk; b += kCl) {
         if (b <= k) continue;
         const int rows = min(32, n3 - 32 * b);
+#pragma unroll 4
         for (int e = tid; e < 32 * rows; e += kST) {
           const int l = e / rows, rr = 32 * b + e % rows - k1;
           Pt[l * kClusN3 + rr] = rP[l * kClusN3 + rr];
@@ -1205,6 +1247,7 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
       if (r >= n3) continue;
       const int i = r / 3, ax = r % 3;
       float acc = 0.f;
+#pragma unroll 4
       for (int j = i + lane; j < nc; j += 32) acc += Ls[prow(j) + i] * (float)p[3 * j + ax];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1243,7 +1286,7 @@ constexpr size_t kSmallSmemV = sizeof(float) * ((size_t)prow(kSmallN3) + 32 * kP
 
 template <typename FT>
 cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, const FT* y2,
-                             double* z2, int* info, int num_sms, int refine) {
+                             double* z2, int* info, int num_sms, int refine, int nc_host) {
   RedArgs<FT> a{};
   a.n2 = m.n2; a.refine = refine;
   a.nc_dev = m.counters + 3;
@@ -1256,14 +1299,30 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
   a.small_lim = 0;
   if constexpr (std::is_same<FT, float>::value) {
     // one-CTA path for 0 < n_c <= kSmallNc, 4-CTA cluster for n_c <= kClusNc
-    // (the kernels exit otherwise)
+    // (every kernel reads n_c on the device and exits when it is not its
+    // range).  With n_c known on the host (nc_host >= 0) only the kernels of
+    // its path are launched and the z2 update runs as a plain launch, so
+    // n_c <= kClusNc needs no cooperative launch (whose grid must find all of
+    // its SMs free at once when other solves share the GPU).
     a.small_lim = kClusNc;
     ProfScope ps(PROF_CHOL, s);
+    const int zgrid = std::max(1, std::min(2 * std::max(1, num_sms), (m.n2 + 7) / 8));
+    if (nc_host == 0) {
+      k_z2_update<<<zgrid, 256, 0, s>>>(a);
+      count_launch();
+      return cudaGetLastError();
+    }
+    const bool known = nc_host > 0 && nc_host <= kClusNc;
+    const bool want_small = !known || nc_host <= kSmallNc, want_clus = !known || nc_host > kSmallNc;
     k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
     k_small_x<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
     k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
-    k_small_v<<<1, kST, kSmallSmemV, s>>>(a);
-    {
+    count_launch(3);
+    if (want_small) {
+      k_small_v<<<1, kST, kSmallSmemV, s>>>(a);
+      count_launch();
+    }
+    if (want_clus) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(kCl);
       cfg.blockDim = dim3(kST);
@@ -1278,8 +1337,13 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
       cfg.numAttrs = 1;
       const cudaError_t e = cudaLaunchKernelEx(&cfg, k_clus_v, a);
       if (e != cudaSuccess) return e;
+      count_launch();
     }
-    count_launch(5);
+    if (known) {
+      k_z2_update<<<zgrid, 256, 0, s>>>(a);
+      count_launch();
+      return cudaGetLastError();
+    }
   }
   void* args[] = {&a};
   const int grid = std::max(1, num_sms);
@@ -1299,11 +1363,17 @@ int64_t reduced_workspace_elems(int nc) {
          (prow(nc) + 1024 * ((int64_t)nc + 31) / 32 + 16) + 4 * n3 + (int64_t)nc * nc + 128;
 }
 
+int reduced_path(int nc_host, int precision) {
+  if (precision == 0 || nc_host < 0 || nc_host > kClusNc) return 0;   // cooperative kernel
+  if (nc_host == 0) return 1;
+  return nc_host <= kSmallNc ? 2 : 3;
+}
+
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
-                          double* z2, int* info, int num_sms, int precision) {
+                          double* z2, int* info, int num_sms, int precision, int nc_host) {
   if (precision == 0)
-    return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0);
-  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4);
+    return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0, nc_host);
+  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4, nc_host);
 }
 
 }  // namespace fsim

@@ -252,7 +252,7 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
 //   upper:    dx1 = L1^-T (z1 - L21^T dx2)             (one backward pass)
 template <typename T>
 cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int* info,
-                          int num_sms, bool wide, bool dense_schur) {
+                          int num_sms, bool wide, bool dense_schur, int nc_host) {
   const int nf = m.nf, n1 = m.n1, n2 = m.n2;
   const bool f64 = std::is_same<T, double>::value;
   double* r = m.r;                                  // float64 work (nf * 3)
@@ -287,7 +287,7 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
       // float64 factors, or float32 factors refined with float64 residuals.
       // n_c is read on the device (z2 = u when it is 0).
       ProfScope psr(PROF_REDUCED, s);
-      const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, f64 ? 0 : 1);
+      const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, f64 ? 0 : 1, nc_host);
       if (e != cudaSuccess) return e;
     }
     if (!f64) {
@@ -321,10 +321,11 @@ void set_solver_smem_limits(int max_bytes) {
 }
 
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
-                        int* info_dev, int num_sms, bool alone, bool dense_schur) {
+                        int* info_dev, int num_sms, bool alone, bool dense_schur, int nc_host) {
   // 32-warp solve items only for a float32 solve that has the GPU to itself
-  if (precision == 0) return global_step_t<double>(s, m, g, dx, info_dev, num_sms, false, dense_schur);
-  return global_step_t<float>(s, m, g, dx, info_dev, num_sms, alone, dense_schur);
+  if (precision == 0)
+    return global_step_t<double>(s, m, g, dx, info_dev, num_sms, false, dense_schur, nc_host);
+  return global_step_t<float>(s, m, g, dx, info_dev, num_sms, alone, dense_schur, nc_host);
 }
 
 }  // namespace fsim

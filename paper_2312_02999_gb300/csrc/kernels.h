@@ -121,7 +121,7 @@ struct DevMesh {
     int64_t kernels = 0;        // kernel nodes (counted as launches per replay)
     bool failed = false;        // capture unsupported: launch directly
   };
-  static constexpr int kGraphs = 8;
+  static constexpr int kGraphs = 12;
   Graph graphs[kGraphs];
   int red_gen = 0;            // bumped whenever the reduced buffers move
 };
@@ -160,8 +160,13 @@ void launch_ccd_reset(cudaStream_t s, const DevMesh& m);
 // per workspace and can be captured in a CUDA graph).  num_sms is the CTA
 // count of the cooperative reduced-system launch; alone = no other solve
 // shares the GPU (selects wider triangular-solve work items).
+// nc_host: n_c as read back by the host (selects the reduced-system path
+// and skips the launches of the others), or -1 when the host does not know it.
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,
-                        int* info_dev, int num_sms, bool alone, bool dense_schur = false);
+                        int* info_dev, int num_sms, bool alone, bool dense_schur = false,
+                        int nc_host = -1);
+// Reduced-system path a global step takes for this n_c and precision (graph key).
+int reduced_path(int nc_host, int precision);
 // Schur-only variant of the x2 block (k_schur.cu): z2 = Sigma-hat^-1 y2 with
 // Sigma-hat = Sigma (x) I_3 + B-check assembled densely and factored by
 // Cholesky (float64, or float32 + two float64 refinement steps).
@@ -179,7 +184,7 @@ int pcg_global_step(cudaStream_t s, const DevMesh& m, const double* g, double* d
 // y2 (double for precision 0, float for 1) is the Schur right-hand side with
 // u = Sigma^-1 y2; it scales the refinement's stopping test.
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
-                          double* z2, int* info, int num_sms, int precision);
+                          double* z2, int* info, int num_sms, int precision, int nc_host = -1);
 void set_solver_smem_limits(int max_bytes);
 void set_reduced_smem_limits();
 
