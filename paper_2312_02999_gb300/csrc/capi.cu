@@ -144,6 +144,7 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.dx, 3 * n, bytes));
   TRY(dalloc(al, &m.g, 3 * n, bytes));
   TRY(dalloc(al, &m.act, 6 * T, bytes));
+  TRY(dalloc(al, &m.act_df, 6 * T, bytes));
   TRY(dalloc(al, &m.tetf, 12 * T, bytes));
   TRY(dalloc(al, &m.tetf_t, 12 * T, bytes));
   TRY(dalloc(al, &m.s, 3 * Ns, bytes));
@@ -684,6 +685,14 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   ms.factor_nnz = f.factor_nnz;
   m.nf = f.n_free; m.n1 = f.n1; m.n2 = f.n2;
   TRY(upload(ms, s, &m.dminv, dminv.data(), dminv.size()));
+  {   // Dm^-1 as float pairs (hi, lo) for the mixed local step
+    std::vector<float2> dd(dminv.size());
+    for (size_t k = 0; k < dminv.size(); ++k) {
+      const float h = (float)dminv[k];
+      dd[k] = make_float2(h, (float)(dminv[k] - (double)h));
+    }
+    TRY(upload(ms, s, &m.dminv_df, dd.data(), dd.size()));
+  }
   TRY(upload(ms, s, &m.w, w.data(), w.size()));
   TRY(upload(ms, s, &m.perm, f.perm.data(), f.perm.size()));
   TRY(upload(ms, s, &m.pos, f.pos.data(), f.pos.size()));
@@ -811,7 +820,7 @@ fsim_status fsim_set_actuation(fsim_ctx_t ctx, int mesh_id, const double* fiber,
   // staging: fiber into tetf (>= 3T doubles), stretch into tetf_t
   CK(cudaMemcpyAsync(m.tetf, fiber, sizeof(double) * 3 * (size_t)T, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(m.tetf_t, stretch, sizeof(double) * (size_t)T, cudaMemcpyHostToDevice, s));
-  launch_actuation(s, T, m.tetf, m.tetf_t, m.act);
+  launch_actuation(s, T, m.tetf, m.tetf_t, m.act, m.act_df);
   CK(cudaStreamSynchronize(s));
   msp->actuated = true;
   return FSIM_OK;
@@ -823,7 +832,7 @@ fsim_status fsim_set_actuation_dev(fsim_ctx_t ctx, int mesh_id, const double* fi
   if (!msp || !fiber_dev || !stretch_dev) return FSIM_EINVAL;
   if (!msp->prefactored) return FSIM_ENOT_READY;
   cudaSetDevice(ctx->device);
-  launch_actuation(ctx->stream, msp->d.T, fiber_dev, stretch_dev, msp->d.act);
+  launch_actuation(ctx->stream, msp->d.T, fiber_dev, stretch_dev, msp->d.act, msp->d.act_df);
   CK(cudaGetLastError());
   msp->actuated = true;
   return FSIM_OK;

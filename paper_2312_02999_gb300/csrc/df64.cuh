@@ -1,0 +1,76 @@
+// Double-float arithmetic (an unevaluated sum hi + lo of two float32 values,
+// about 48 significant bits) for the mixed-precision local step.  On GB300 a
+// float64 FMA costs about as much issue time as 60 float32 operations, while
+// a double-float multiply-add is about 25, so the float64-accurate parts of
+// the per-tet local step run several times faster in this form.
+//
+// The building blocks are the classical error-free transformations: Knuth's
+// two-sum (the rounding error of a + b), Dekker's fast two-sum for
+// |a| >= |b|, and the FMA two-product (the rounding error of a * b is
+// fma(a, b, -a*b) exactly).  The additions and products use the _rn
+// intrinsics, which the compiler never fuses into FMAs or reorders, so the
+// transformations stay error-free whatever the contraction flags.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fsim {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_from_double(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(__dsub_rn(v, (double)h))};
+}
+
+__device__ __forceinline__ df df_from_float(float v) { return {v, 0.f}; }
+
+__device__ __forceinline__ double df_to_double(df a) { return __dadd_rn((double)a.hi, (double)a.lo); }
+
+// a + b with both parts' errors carried (exact-cancellation safe)
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  const df t = df_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = df_two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return df_fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = df_two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return df_fast_two_sum(p.hi, p.lo);
+}
+
+// a * b + c
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+
+}  // namespace fsim

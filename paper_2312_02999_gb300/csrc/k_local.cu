@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "df64.cuh"
 #include "mat3.cuh"
 
 namespace fsim {
@@ -123,7 +124,8 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 __global__ void k_actuation(int T, const double* __restrict__ fiber,
-                            const double* __restrict__ stretch, double* __restrict__ act) {
+                            const double* __restrict__ stretch, double* __restrict__ act,
+                            float2* __restrict__ act_df) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
   double f0 = fiber[3 * t], f1 = fiber[3 * t + 1], f2 = fiber[3 * t + 2];
@@ -138,6 +140,14 @@ __global__ void k_actuation(int T, const double* __restrict__ fiber,
   act[3 * T + t] = b + k * f1 * f1;
   act[4 * T + t] = k * f1 * f2;
   act[5 * T + t] = b + k * f2 * f2;
+  if (act_df) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double v = act[c * T + t];
+      const float h = __double2float_rn(v);
+      act_df[(size_t)c * T + t] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+  }
 }
 
 template <int PREC>
@@ -226,6 +236,185 @@ k_elastic(int T, const int4* __restrict__ tets, const double* __restrict__ dminv
   if (threadIdx.x == 0) partials[blockIdx.x] = bs;
 }
 
+// Mixed-precision local step in double-float arithmetic (df64.cuh): the
+// same quantities as k_elastic<1> (float32 rotation refined to float64
+// accuracy, then p, D, energy and forces) with the float64-accurate parts
+// carried as float pairs, which GB300 executes several times faster than
+// float64.  The refinement follows polar_refine with its small terms in
+// float32: R1 = R0 + R0 D with D = (I - R0^T R0) / 2 (about 1e-7), the
+// skew part of S = R1^T M kept in double-float, w = ((tr S) I - S)^-1 2 a
+// in float32, and R = R1 exp([w]) = R0 + C with C = R0 D + R0 (E - I) +
+// R0 D (E - I) (all about 1e-7, so float32 products suffice).  Inputs and
+// outputs stay float64; Dm^-1 and A come as float pairs.
+__global__ void __launch_bounds__(kElasticThreads)
+k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dminv_df,
+             const double* __restrict__ w, const float2* __restrict__ act_df,
+             const double* __restrict__ x, double* __restrict__ tetf,
+             double* __restrict__ proj, double* __restrict__ partials) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (t < T) {
+    const int4 tv = tets[t];
+    const double* x0 = x + 3 * (size_t)tv.x;
+    const double* x1 = x + 3 * (size_t)tv.y;
+    const double* x2 = x + 3 * (size_t)tv.z;
+    const double* x3 = x + 3 * (size_t)tv.w;
+    df Ds[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double o = x0[d];
+      Ds[d][0] = df_from_double(x1[d] - o);
+      Ds[d][1] = df_from_double(x2[d] - o);
+      Ds[d][2] = df_from_double(x3[d] - o);
+    }
+    df Di[3][3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float2 v = dminv_df[(size_t)k * T + t];
+      Di[k / 3][k % 3] = {v.x, v.y};
+    }
+    df A[3][3];
+    {
+      const float2 a00 = act_df[0 * (size_t)T + t], a01 = act_df[1 * (size_t)T + t],
+                   a02 = act_df[2 * (size_t)T + t], a11 = act_df[3 * (size_t)T + t],
+                   a12 = act_df[4 * (size_t)T + t], a22 = act_df[5 * (size_t)T + t];
+      A[0][0] = {a00.x, a00.y};
+      A[0][1] = A[1][0] = {a01.x, a01.y};
+      A[0][2] = A[2][0] = {a02.x, a02.y};
+      A[1][1] = {a11.x, a11.y};
+      A[1][2] = A[2][1] = {a12.x, a12.y};
+      A[2][2] = {a22.x, a22.y};
+    }
+    df F[3][3], M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        F[i][j] = df_add(df_add(df_mul(Ds[i][0], Di[0][j]), df_mul(Ds[i][1], Di[1][j])),
+                         df_mul(Ds[i][2], Di[2][j]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        M[i][j] = df_add(df_add(df_mul(F[i][0], A[0][j]), df_mul(F[i][1], A[1][j])),
+                         df_mul(F[i][2], A[2][j]));
+    float R0[3][3];
+    {
+      float Mf[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mf[i][j] = M[i][j].hi;
+      polar_rotation<float, 6>(Mf, R0);
+    }
+    // D = (I - R0^T R0) / 2 from exact float products summed in double-float
+    float Dm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        df g = df_add(df_add(df_two_prod(R0[0][i], R0[0][j]), df_two_prod(R0[1][i], R0[1][j])),
+                      df_two_prod(R0[2][i], R0[2][j]));
+        const df r = df_sub(df_from_float(i == j ? 1.f : 0.f), g);
+        Dm[i][j] = Dm[j][i] = 0.5f * (r.hi + r.lo);
+      }
+    float R1c[3][3];
+    matmul(R0, Dm, R1c);
+    // S = R1^T M = R0^T M (double-float) + R1c^T M (float)
+    df S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        df acc = df_add(df_add(df_mul_f(M[0][j], R0[0][i]), df_mul_f(M[1][j], R0[1][i])),
+                        df_mul_f(M[2][j], R0[2][i]));
+        const float c = R1c[0][i] * M[0][j].hi + R1c[1][i] * M[1][j].hi + R1c[2][i] * M[2][j].hi;
+        S[i][j] = df_add(acc, df_from_float(c));
+      }
+    float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
+    {
+      const df d0 = df_sub(S[2][1], S[1][2]), d1 = df_sub(S[0][2], S[2][0]), d2 = df_sub(S[1][0], S[0][1]);
+      const float a0 = 0.5f * (d0.hi + d0.lo), a1 = 0.5f * (d1.hi + d1.lo), a2 = 0.5f * (d2.hi + d2.lo);
+      const float s00 = S[0][0].hi, s11 = S[1][1].hi, s22 = S[2][2].hi;
+      const float s01 = 0.5f * (S[0][1].hi + S[1][0].hi);
+      const float s02 = 0.5f * (S[0][2].hi + S[2][0].hi);
+      const float s12 = 0.5f * (S[1][2].hi + S[2][1].hi);
+      const float tr = s00 + s11 + s22;
+      const float A00 = tr - s00, A11 = tr - s11, A22 = tr - s22;
+      const float A01 = -s01, A02 = -s02, A12 = -s12;
+      const float c00 = A11 * A22 - A12 * A12, c01 = A02 * A12 - A01 * A22, c02 = A01 * A12 - A02 * A11;
+      const float c11 = A00 * A22 - A02 * A02, c12 = A01 * A02 - A00 * A12, c22 = A00 * A11 - A01 * A01;
+      const float det = A00 * c00 + A01 * c01 + A02 * c02;
+      if (fabsf(det) > 1e-30f) {
+        const float id = 2.f / det;
+        wv0 = id * (c00 * a0 + c01 * a1 + c02 * a2);
+        wv1 = id * (c01 * a0 + c11 * a1 + c12 * a2);
+        wv2 = id * (c02 * a0 + c12 * a1 + c22 * a2);
+      }
+    }
+    // E - I for exp([w]) to second order
+    float Em[3][3];
+    Em[0][0] = -0.5f * (wv1 * wv1 + wv2 * wv2);
+    Em[1][1] = -0.5f * (wv0 * wv0 + wv2 * wv2);
+    Em[2][2] = -0.5f * (wv0 * wv0 + wv1 * wv1);
+    Em[0][1] = -wv2 + 0.5f * wv0 * wv1;
+    Em[1][0] = wv2 + 0.5f * wv0 * wv1;
+    Em[0][2] = wv1 + 0.5f * wv0 * wv2;
+    Em[2][0] = -wv1 + 0.5f * wv0 * wv2;
+    Em[1][2] = -wv0 + 0.5f * wv1 * wv2;
+    Em[2][1] = wv0 + 0.5f * wv1 * wv2;
+    // R = (R0 + R1c)(I + Em) = R0 + C
+    df R[3][3];
+    {
+      float T1[3][3], T2[3][3];
+      matmul(R0, Em, T1);
+      matmul(R1c, Em, T2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) R[i][j] = df_two_sum(R0[i][j], R1c[i][j] + T1[i][j] + T2[i][j]);
+    }
+    df P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        P[i][j] = df_add(df_add(df_mul(R[i][0], A[0][j]), df_mul(R[i][1], A[1][j])),
+                         df_mul(R[i][2], A[2][j]));
+    const double wt = w[t];
+    df Dd[3][3];
+    df ssum = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Dd[i][j] = df_sub(F[i][j], P[i][j]);
+        ssum = df_add(ssum, df_mul(Dd[i][j], Dd[i][j]));
+      }
+    e = 0.5 * wt * df_to_double(ssum);
+    // f_a = w D gradN_a, gradN_a = row a-1 of Dm^-1 (a = 1..3), f_0 = -sum
+    double f0[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const df q = df_add(df_add(df_mul(Dd[d][0], Di[a - 1][0]), df_mul(Dd[d][1], Di[a - 1][1])),
+                            df_mul(Dd[d][2], Di[a - 1][2]));
+        const double fa = wt * df_to_double(q);
+        tetf[(size_t)(a * 3 + d) * T + t] = fa;
+        f0[d] -= fa;
+      }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) tetf[(size_t)d * T + t] = f0[d];
+    if (proj != nullptr) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) proj[(size_t)9 * t + k] = df_to_double(P[k / 3][k % 3]);
+    }
+  }
+  const double bs = block_sum(e);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
 __global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
                                 const int* __restrict__ vslot, const double* __restrict__ tetf,
                                 const uint8_t* __restrict__ pinned, double* __restrict__ g) {
@@ -289,8 +478,9 @@ __global__ void k_check_finite(int n, const double* __restrict__ v, int* __restr
 }
 
 // ---------------------------------------------------------------------------
-void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act) {
-  k_actuation<<<(T + 255) / 256, 256, 0, s>>>(T, fiber, stretch, act);
+void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act,
+                      float2* act_df) {
+  k_actuation<<<(T + 255) / 256, 256, 0, s>>>(T, fiber, stretch, act, act_df);
   count_launch();
 }
 
@@ -302,6 +492,9 @@ void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* t
   ProfScope ps(PROF_ELASTIC, s);
   if (precision == 0)
     k_elastic<0><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
+  else if (m.dminv_df && m.act_df)
+    k_elastic_df<<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv_df, m.w, m.act_df, x, tetf, proj,
+                                               partials);
   else
     k_elastic<1><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
   count_launch();

@@ -21,6 +21,8 @@ struct DevMesh {
   double* dminv = nullptr;    // 9T SoA: Dm^-1 (row-major entry k at k*T + t)
   double* w = nullptr;        // T
   double* act = nullptr;      // 6T SoA: A00 A01 A02 A11 A12 A22
+  float2* act_df = nullptr;   // 6T SoA: the same as float pairs (hi, lo)
+  float2* dminv_df = nullptr; // 9T SoA: Dm^-1 as float pairs
   double* tetf = nullptr;     // 12T SoA per-tet vertex forces ((a*3+d)*T + t)
   double* tetf_t = nullptr;   // same at the trial point
   int* vinc_ptr = nullptr;    // vertex -> incident (t*4 + a) slots
@@ -127,8 +129,11 @@ struct DevMesh {
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------
-void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act);
-// precision 0: float64 SVD; 1: float32 SVD + float64 polar refinement.
+// act_df (optional): the same 6 entries as float pairs for the mixed local step
+void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act,
+                      float2* act_df);
+// precision 0: float64 SVD; 1: float32 SVD refined to float64 accuracy in
+// double-float arithmetic (k_elastic_df).
 void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* tetf,
                     double* proj, double* partials, int precision);
 int elastic_blocks(int T);

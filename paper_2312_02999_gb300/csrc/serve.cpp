@@ -148,7 +148,7 @@ int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J) {
   const double* x0 = ms.d.rest;
   bool x0_dev = true;
   if (J.device) {
-    launch_actuation(st, m.T, J.fiber_dev, J.stretch_dev, m.act);
+    launch_actuation(st, m.T, J.fiber_dev, J.stretch_dev, m.act, m.act_df);
     if (J.x_init_dev) x0 = J.x_init_dev;
   } else {
     std::memcpy(s.h_act, J.fiber.data(), sizeof(double) * 3 * T);
@@ -156,7 +156,7 @@ int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J) {
     if (cudaMemcpyAsync(m.tetf, s.h_act, sizeof(double) * 4 * T, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
       return FSIM_ECUDA;
-    launch_actuation(st, m.T, m.tetf, m.tetf + 3 * T, m.act);
+    launch_actuation(st, m.T, m.tetf, m.tetf + 3 * T, m.act, m.act_df);
     if (J.has_x) {
       std::memcpy(s.h_x, J.x_init.data(), sizeof(double) * 3 * n);
       x0 = s.h_x;
