@@ -134,9 +134,18 @@ int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
 // constant mesh data (factor, Sigma^-1, topology) stays shared.  Used for
 // the mesh's own workspace at prefactor and for the server's extra slots.
 int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, size_t* bytes) {
-  // a copy must never replay (or destroy) another workspace's graphs
+  // a copy must never replay (or destroy) another workspace's graphs, nor
+  // use its side stream
   for (auto& g : m.graphs) g = DevMesh::Graph{};
   m.red_gen = 0;
+  m.aux_stream = nullptr;
+  m.ev_fork = m.ev_join = nullptr;
+  if (cudaStreamCreateWithFlags(&m.aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return FSIM_ECUDA;
+  }
   const size_t n = m.n, T = m.T, Ns = m.Ns;
   const size_t np = (size_t)m.Ns + m.Nt + m.Ne;
   TRY(dalloc(al, &m.x, 3 * n, bytes));
@@ -200,6 +209,11 @@ void destroy_graphs(DevMesh& m) {
     if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
     g = DevMesh::Graph{};
   }
+  if (m.ev_fork) cudaEventDestroy(m.ev_fork);
+  if (m.ev_join) cudaEventDestroy(m.ev_join);
+  if (m.aux_stream) cudaStreamDestroy(m.aux_stream);
+  m.ev_fork = m.ev_join = nullptr;
+  m.aux_stream = nullptr;
 }
 
 // Run a fixed launch sequence through a CUDA graph captured on first use

@@ -747,7 +747,9 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
   for (int e = tid; e < prow(nc); e += kST) a.spk[e] = P[e];
 }
 
-// k_small_x (grid): y = B u_c in float64, |y2|^2, X = B (L_s (x) I_3).
+// k_small_x (grid): y = B u_c in float64, |y2|^2 (PARTS & 1: these need the
+// right-hand side), X = B (L_s (x) I_3) (PARTS & 2: needs only B and L_s).
+template <int PARTS>
 __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > a.small_lim) return;
@@ -755,6 +757,7 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
   const int n3 = 3 * nc;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
+  if (PARTS & 1)
   for (int row = gtid; row < n3; row += gsz) {
     const int i = row / 3;
     const double* brow = a.Bc + (size_t)row * n3;
@@ -768,12 +771,13 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
     }
     a.y[row] = acc;
   }
-  {
+  if (PARTS & 1) {
     double q = 0.0;
     for (int e = gtid; e < 3 * a.n2; e += gsz) q += (double)a.y2[e] * (double)a.y2[e];
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0 && q != 0.0) atomicAdd(&a.nrm[2], q);
   }
+  if (PARTS & 2)
   for (int e = gtid; e < n3 * n3; e += gsz) {
     const int row = e / n3, colx = e % n3;
     const int i = row / 3, k = colx / 3, b = colx % 3;
@@ -1285,8 +1289,8 @@ constexpr size_t kSmallSmemS = sizeof(float) * ((size_t)prow(kClusNc) + 32 * kPt
 constexpr size_t kSmallSmemV = sizeof(float) * ((size_t)prow(kSmallN3) + 32 * kPtLd + kSmallN3);
 
 template <typename FT>
-cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, const FT* y2,
-                             double* z2, int* info, int num_sms, int refine, int nc_host) {
+RedArgs<FT> make_args(const DevMesh& m, const double* u, const FT* y2, double* z2, int* info,
+                      int refine) {
   RedArgs<FT> a{};
   a.n2 = m.n2; a.refine = refine;
   a.nc_dev = m.counters + 3;
@@ -1296,7 +1300,34 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
   a.clist = m.clist; a.Sinv = m.Sinv; a.Bc = m.Bc; a.bocc = m.bocc;
   a.u = u; a.y2 = y2; a.z2 = z2;
   a.info = info;
-  a.small_lim = 0;
+  a.small_lim = std::is_same<FT, float>::value ? kClusNc : 0;
+  return a;
+}
+
+// Launch one of the cluster kernels (kCl CTAs per cluster).
+cudaError_t launch_clus_v(cudaStream_t s, const RedArgs<float>& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCl);
+  cfg.blockDim = dim3(kST);
+  cfg.dynamicSmemBytes = kClusSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kCl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_clus_v, a);
+  count_launch();
+  return e;
+}
+
+template <typename FT>
+cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, const FT* y2,
+                             double* z2, int* info, int num_sms, int refine, int nc_host,
+                             bool prepared) {
+  RedArgs<FT> a = make_args<FT>(m, u, y2, z2, info, refine);
   if constexpr (std::is_same<FT, float>::value) {
     // one-CTA path for 0 < n_c <= kSmallNc, 4-CTA cluster for n_c <= kClusNc
     // (every kernel reads n_c on the device and exits when it is not its
@@ -1304,7 +1335,6 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
     // its path are launched and the z2 update runs as a plain launch, so
     // n_c <= kClusNc needs no cooperative launch (whose grid must find all of
     // its SMs free at once when other solves share the GPU).
-    a.small_lim = kClusNc;
     ProfScope ps(PROF_CHOL, s);
     const int zgrid = std::max(1, std::min(2 * std::max(1, num_sms), (m.n2 + 7) / 8));
     if (nc_host == 0) {
@@ -1314,30 +1344,23 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
     }
     const bool known = nc_host > 0 && nc_host <= kClusNc;
     const bool want_small = !known || nc_host <= kSmallNc, want_clus = !known || nc_host > kSmallNc;
-    k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
-    k_small_x<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
-    k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
-    count_launch(3);
+    if (prepared) {       // S, L_s, lists, X and N came from reduced_prepare
+      if (cudaStreamWaitEvent(s, m.ev_join, 0) != cudaSuccess) return cudaGetLastError();
+      k_small_x<1><<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+      count_launch();
+    } else {
+      k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
+      k_small_x<3><<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+      k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+      count_launch(3);
+    }
     if (want_small) {
       k_small_v<<<1, kST, kSmallSmemV, s>>>(a);
       count_launch();
     }
     if (want_clus) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(kCl);
-      cfg.blockDim = dim3(kST);
-      cfg.dynamicSmemBytes = kClusSmem;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = kCl;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_clus_v, a);
+      const cudaError_t e = launch_clus_v(s, a);
       if (e != cudaSuccess) return e;
-      count_launch();
     }
     if (known) {
       k_z2_update<<<zgrid, 256, 0, s>>>(a);
@@ -1370,10 +1393,32 @@ int reduced_path(int nc_host, int precision) {
 }
 
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
-                          double* z2, int* info, int num_sms, int precision, int nc_host) {
+                          double* z2, int* info, int num_sms, int precision, int nc_host,
+                          bool prepared) {
   if (precision == 0)
-    return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0, nc_host);
-  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4, nc_host);
+    return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0, nc_host, false);
+  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4, nc_host, prepared);
+}
+
+bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
+                     int* info, int num_sms, int nc_host) {
+  if (nc_host <= 0 || nc_host > kClusNc || !m.aux_stream || !m.ev_fork || !m.ev_join) return false;
+  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, 4);
+  cudaStream_t s2 = m.aux_stream;
+  if (cudaEventRecord(m.ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(s2, m.ev_fork, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  {
+    ProfScope ps(PROF_CHOL, s2);
+    k_small_s<<<1, kST, kSmallSmemS, s2>>>(a);
+    k_small_x<2><<<2 * std::max(1, num_sms), 256, 0, s2>>>(a);
+    k_small_n<<<2 * std::max(1, num_sms), 256, 0, s2>>>(a);
+    count_launch(3);
+  }
+  // the join is recorded even if a launch failed, so the fork always closes
+  cudaEventRecord(m.ev_join, s2);
+  return true;
 }
 
 }  // namespace fsim

@@ -261,6 +261,11 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
   const T* Z = f64 ? (const T*)m.Z : (const T*)m.Zf;
   k_gather_rhs<T><<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, g, b);
   count_launch();
+  // the reduced system's factorisation needs only B-check and Sigma^-1: in
+  // mixed precision it starts on the side stream and overlaps the forward solve
+  const bool prepared = !f64 && !dense_schur && n2 > 0 &&
+                        reduced_prepare(s, m, m.u, b + 3 * (size_t)n1, r + 3 * (size_t)n1, info,
+                                        num_sms, nc_host);
   if (n1 > 0) trisolve_fwd<T>(s, m, Z, b, y, wide);
   if (n2 > 0) {
     T* y2 = b + 3 * (size_t)n1;
@@ -287,7 +292,8 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
       // float64 factors, or float32 factors refined with float64 residuals.
       // n_c is read on the device (z2 = u when it is 0).
       ProfScope psr(PROF_REDUCED, s);
-      const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, f64 ? 0 : 1, nc_host);
+      const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, f64 ? 0 : 1, nc_host,
+                                          prepared);
       if (e != cudaSuccess) return e;
     }
     if (!f64) {

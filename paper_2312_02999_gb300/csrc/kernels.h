@@ -125,6 +125,11 @@ struct DevMesh {
   };
   static constexpr int kGraphs = 12;
   Graph graphs[kGraphs];
+  // side stream and fork / join events of this workspace: the part of the
+  // reduced system that does not need the right-hand side runs there while
+  // the forward solve runs on the solve's own stream
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int red_gen = 0;            // bumped whenever the reduced buffers move
 };
 
@@ -189,7 +194,14 @@ int pcg_global_step(cudaStream_t s, const DevMesh& m, const double* g, double* d
 // y2 (double for precision 0, float for 1) is the Schur right-hand side with
 // u = Sigma^-1 y2; it scales the refinement's stopping test.
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
-                          double* z2, int* info, int num_sms, int precision, int nc_host = -1);
+                          double* z2, int* info, int num_sms, int precision, int nc_host = -1,
+                          bool prepared = false);
+// Mixed precision, 0 < nc_host <= 128: forks the workspace's side stream off
+// s and launches there the kernels that need only B-check and Sigma^-1 (S,
+// L_s, block lists, X, N); reduced_solve(..., prepared = true) joins it.
+// Returns false (nothing launched) when that split does not apply.
+bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
+                     int* info, int num_sms, int nc_host);
 void set_solver_smem_limits(int max_bytes);
 void set_reduced_smem_limits();
 
