@@ -139,10 +139,12 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   for (auto& g : m.graphs) g = DevMesh::Graph{};
   m.red_gen = 0;
   m.aux_stream = nullptr;
-  m.ev_fork = m.ev_join = nullptr;
+  m.ev_fork = m.ev_join = m.ev_fork2 = m.ev_join2 = nullptr;
   if (cudaStreamCreateWithFlags(&m.aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&m.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&m.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&m.ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m.ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m.ev_join2, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     return FSIM_ECUDA;
   }
@@ -172,6 +174,7 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.r, 3 * (size_t)m.nf, bytes));
   TRY(dalloc(al, &m.u, 3 * (size_t)std::max(m.n2, 1), bytes));
   TRY(dalloc(al, &m.rf, 3 * (size_t)m.nf + 8, bytes));
+  TRY(dalloc(al, &m.bx, 3 * (size_t)m.nf + 8, bytes));
   TRY(dalloc(al, &m.uf, 3 * (size_t)std::max(m.n2, 1), bytes));
   TRY(dalloc(al, &m.pairs, (size_t)m.cap_act, bytes));
   TRY(dalloc(al, &m.cand, (size_t)m.cap, bytes));
@@ -211,8 +214,10 @@ void destroy_graphs(DevMesh& m) {
   }
   if (m.ev_fork) cudaEventDestroy(m.ev_fork);
   if (m.ev_join) cudaEventDestroy(m.ev_join);
+  if (m.ev_fork2) cudaEventDestroy(m.ev_fork2);
+  if (m.ev_join2) cudaEventDestroy(m.ev_join2);
   if (m.aux_stream) cudaStreamDestroy(m.aux_stream);
-  m.ev_fork = m.ev_join = nullptr;
+  m.ev_fork = m.ev_join = m.ev_fork2 = m.ev_join2 = nullptr;
   m.aux_stream = nullptr;
 }
 
@@ -529,7 +534,12 @@ fsim_status fsim_create(fsim_ctx_t* out, int device) {
   c->device = device;
   if (cudaSetDevice(device) != cudaSuccess) { delete c; return FSIM_ECUDA; }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // solve streams get the highest priority and the workspaces' side streams
+  // the default (lowest): the side stream only fills SMs the critical path
+  // leaves free (its work is off the critical path)
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
     delete c;
     return FSIM_ECUDA;
   }
@@ -807,6 +817,10 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   TRY(dalloc(ms, &ms.dxtmp, 3 * (size_t)m.n));
   ms.ws_bytes = 0;
   TRY(alloc_workspace(ms, m, ms.allocs, &ms.ws_bytes));
+  if (m.n1 > 0 && m.n2 > 0) {   // Phi = K11^-1 K12 Sigma^-1 for the mixed global step
+    TRY(dalloc(ms, &m.Phi_t, (size_t)m.n1 * m.n2));
+    CK(compute_phi(s, m, m.Phi_t));
+  }
   CK(cudaMemcpyAsync(m.x, m.rest, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToDevice, s));
   {
     Exec ex = ctx_exec(ctx, ms);

@@ -829,42 +829,74 @@ __device__ void cta_lt_apply_f(const float* Lp, int nc, const double* p, float* 
 // Refinement products in float64, one warp per row (warp w of nw):
 // w = S v with S = Sigma^-1[c, c] (x) I_3 (gathered into S64 by k_small_s)
 __device__ void refine_sv(const RedArgs<float>& a, int nc, int w, int nw) {
-  const int lane = threadIdx.x & 31;
-  for (int e = w; e < 3 * nc; e += nw) {
-    const int i = e / 3, ax = e % 3;
-    const double* srow = a.S64 + (size_t)i * nc;
-    double acc = 0.0;
-#pragma unroll 4
-    for (int j = lane; j < nc; j += 32) acc += srow[j] * a.v[3 * j + ax];
+  // four rows per pass with independent accumulators, so the loads of all
+  // four are in flight together (the pass is bound by load latency)
+  constexpr int kR = 4;
+  const int lane = threadIdx.x & 31, n3 = 3 * nc;
+  for (int e0 = w; e0 < n3; e0 += kR * nw) {
+    double acc[kR];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.w[e] = acc;
+    for (int r = 0; r < kR; ++r) {
+      acc[r] = 0.0;
+      const int e = e0 + r * nw;
+      if (e < n3) {
+        const double* srow = a.S64 + (size_t)(e / 3) * nc;
+        const int ax = e % 3;
+#pragma unroll
+        for (int q = 0; q < kClusNc / 32; ++q) {
+          const int j = lane + 32 * q;
+          if (j < nc) acc[r] += srow[j] * a.v[3 * j + ax];
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      const int e = e0 + r * nw;
+      if (lane == 0 && e < n3) a.w[e] = acc[r];
+    }
   }
 }
 
 // rho = y - v - B w over the block-row lists of B; returns this lane's share
-// of |rho|^2 (lane 0 of each warp holds it)
+// of |rho|^2 (lane 0 of each warp holds it).  Four rows per pass, as above.
 __device__ double refine_rho(const RedArgs<float>& a, int nc, int w, int nw) {
+  constexpr int kR = 4;
   const int lane = threadIdx.x & 31, n3 = 3 * nc;
   double r2 = 0.0;
-  for (int row = w; row < n3; row += nw) {
-    const int i = row / 3;
-    const double* brow = a.Bc + (size_t)row * n3;
-    const int* li = a.list + (size_t)i * nc;
-    double acc = 0.0;
-    const int ci = a.cnt[i];
-#pragma unroll 4
-    for (int e = lane; e < ci; e += 32) {
-      const int j = li[e];
-      acc += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
-             brow[3 * j + 2] * a.w[3 * j + 2];
+  for (int e0 = w; e0 < n3; e0 += kR * nw) {
+    double acc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      acc[r] = 0.0;
+      const int row = e0 + r * nw;
+      if (row < n3) {
+        const int i = row / 3;
+        const double* brow = a.Bc + (size_t)row * n3;
+        const int* li = a.list + (size_t)i * nc;
+        const int ci = a.cnt[i];
+#pragma unroll
+        for (int q = 0; q < kClusNc / 32; ++q) {
+          const int e = lane + 32 * q;
+          if (e < ci) {
+            const int j = li[e];
+            acc[r] += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
+                      brow[3 * j + 2] * a.w[3 * j + 2];
+          }
+        }
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const double rr = a.y[row] - a.v[row] - acc;
-      a.rho[row] = rr;
-      r2 += rr * rr;
+    for (int r = 0; r < kR; ++r) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      const int row = e0 + r * nw;
+      if (lane == 0 && row < n3) {
+        const double rr = a.y[row] - a.v[row] - acc[r];
+        a.rho[row] = rr;
+        r2 += rr * rr;
+      }
     }
   }
   return r2;
@@ -1398,6 +1430,66 @@ cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, con
   if (precision == 0)
     return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0, nc_host, false);
   return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4, nc_host, prepared);
+}
+
+namespace {
+
+// x1 = bx1 + Phi[:, c] v.  A CTA covers 32 consecutive x1 solver positions
+// (coalesced reads of the rows of Phi_t) with kPhiSplit warps, each summing
+// a strided share of the n_c columns; v (as float) and the c list are staged
+// in shared memory.  The work is bound by load latency, hence the split.
+constexpr int kPhiSplit = 8;
+__global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply(RedArgs<float> a, int n1,
+                                                             const float* __restrict__ phi_t,
+                                                             const float* __restrict__ bx1,
+                                                             double* __restrict__ x1) {
+  __shared__ float vs[3 * kClusNc];
+  __shared__ int cs[kClusNc];
+  __shared__ float part[kPhiSplit][3][32];
+  const int nc = *a.nc_dev;
+  const bool have = nc > 0 && nc <= a.small_lim;
+  if (have) {
+    red_layout(a, nc);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      cs[k] = a.clist[k];
+      vs[3 * k] = (float)a.v[3 * k];
+      vs[3 * k + 1] = (float)a.v[3 * k + 1];
+      vs[3 * k + 2] = (float)a.v[3 * k + 2];
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  if (have && p < n1) {
+#pragma unroll 4
+    for (int k = wq; k < nc; k += kPhiSplit) {
+      const float f = phi_t[(size_t)cs[k] * n1 + p];
+      c0 += f * vs[3 * k];
+      c1 += f * vs[3 * k + 1];
+      c2 += f * vs[3 * k + 2];
+    }
+  }
+  part[wq][0][lane] = c0;
+  part[wq][1][lane] = c1;
+  part[wq][2][lane] = c2;
+  __syncthreads();
+  if (wq < 3 && p < n1) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < kPhiSplit; ++q) t += part[q][wq][lane];
+    x1[3 * (size_t)p + wq] = (double)bx1[3 * (size_t)p + wq] + (double)t;
+  }
+}
+
+}  // namespace
+
+cudaError_t phi_apply(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
+                      int* info, const float* bx1, double* x1) {
+  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, 4);
+  k_phi_apply<<<(m.n1 + 31) / 32, 32 * kPhiSplit, 0, s>>>(a, m.n1, m.Phi_t, bx1, x1);
+  count_launch();
+  return cudaGetLastError();
 }
 
 bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,

@@ -245,6 +245,27 @@ void trisolve_bwd(cudaStream_t s, const DevMesh& m, const T* Z, const T* y, T* b
   }
 }
 
+// Columns j0 .. j0+2 of Phi = K11^-1 K12 Sigma^-1 come from one backward
+// pass with y1 = 0 and x2 = Sigma^-1 e_j (one column per right-hand side):
+// x1 = L1^-T (0 - L21^T Sigma^-1 e_j) = -Phi e_j.
+__global__ void k_phi_rhs(int n1, int n2, int j0, const double* __restrict__ Sinv,
+                          double* __restrict__ y1, double* __restrict__ b) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 3 * n1) y1[e] = 0.0;
+  if (e < 3 * n2) {
+    const int q = e / 3, d = e % 3;
+    b[3 * (size_t)n1 + e] = (j0 + d < n2) ? Sinv[(size_t)q * n2 + j0 + d] : 0.0;
+  }
+}
+
+__global__ void k_phi_store(int n1, int n2, int j0, const double* __restrict__ b,
+                            float* __restrict__ phi_t) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 3 * n1) return;
+  const int p = e / 3, d = e % 3;
+  if (j0 + d < n2) phi_t[(size_t)(j0 + d) * n1 + p] = (float)(-b[e]);
+}
+
 // Eq. 8 with H = K (x) I_3 in solver positions [x1 ; x2], r = -g-hat:
 //   lower:    z1 = L1^-1 r1,  y2 = r2 - L21 z1        (one forward pass; the
 //             x2 rows of the supernodes hold L21 = H21 L1^-T)
@@ -271,6 +292,37 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
     T* y2 = b + 3 * (size_t)n1;
     double* u = m.u;
     double* z2 = r + 3 * (size_t)n1;                // float64 dx2
+    // With Phi available the x1 block is split: x1 = L1^-T (y1 - L21^T u)
+    // (contact-free, on the side stream while the reduced system is solved)
+    // + Phi[:, c] v after it, instead of a backward pass after z2.
+    const bool phi = prepared && m.Phi_t && m.bx && n1 > 0;
+    if (phi) {
+      {
+        ProfScope psg(PROF_GEMV, s);
+        k_gemv3<float><<<nblk(n2, 8), 256, 0, s>>>(n2, m.Sinvf, (const float*)y2, m.uf);
+        k_convert<float, double><<<nblk(3 * (int64_t)n2, 256), 256, 0, s>>>(3 * n2, m.uf, u);
+        count_launch(2);
+      }
+      cudaStream_t s2 = m.aux_stream;
+      if (cudaEventRecord(m.ev_fork2, s) != cudaSuccess || cudaStreamWaitEvent(s2, m.ev_fork2, 0) != cudaSuccess)
+        return cudaGetLastError();
+      k_convert<float, float><<<nblk(3 * (int64_t)n2, 256), 256, 0, s2>>>(3 * n2, m.uf, m.bx + 3 * (size_t)n1);
+      count_launch();
+      trisolve_bwd<float>(s2, m, m.Zf, m.y1f, m.bx, false);
+      if (cudaEventRecord(m.ev_join2, s2) != cudaSuccess) return cudaGetLastError();
+      {
+        ProfScope psr(PROF_REDUCED, s);
+        const cudaError_t e = reduced_solve(s, m, u, y2, z2, info, num_sms, 1, nc_host, true);
+        if (e != cudaSuccess) return e;
+      }
+      if (cudaStreamWaitEvent(s, m.ev_join2, 0) != cudaSuccess) return cudaGetLastError();
+      const cudaError_t e = phi_apply(s, m, u, y2, z2, info, m.bx, r);
+      if (e != cudaSuccess) return e;
+      cudaMemsetAsync(dx, 0, sizeof(double) * 3 * (size_t)m.n, s);
+      k_scatter_dx<<<nblk(nf, 256), 256, 0, s>>>(nf, m.perm, r, dx);
+      count_launch();
+      return cudaGetLastError();
+    }
     if (dense_schur) {
       // Schur-only configuration: Sigma-hat factored densely (k_schur.cu)
       const cudaError_t e = sigma_hat_solve(s, m, y2, z2, info, f64 ? 0 : 1);
@@ -324,6 +376,18 @@ void set_solver_smem_limits(int max_bytes) {
   cudaFuncSetAttribute(k_bwd_chunk<double, 1024>, a, max_bytes);
   cudaFuncSetAttribute(k_fwd_chunk<float, 1024>, a, max_bytes);
   cudaFuncSetAttribute(k_bwd_chunk<float, 1024>, a, max_bytes);
+}
+
+cudaError_t compute_phi(cudaStream_t s, const DevMesh& m, float* phi_t) {
+  const int n1 = m.n1, n2 = m.n2;
+  const int nb = nblk(3 * (int64_t)std::max(n1, n2), 256);
+  for (int j0 = 0; j0 < n2; j0 += 3) {
+    k_phi_rhs<<<nb, 256, 0, s>>>(n1, n2, j0, m.Sinv, m.y1, m.r);
+    trisolve_bwd<double>(s, m, m.Z, m.y1, m.r, false);
+    k_phi_store<<<nblk(3 * (int64_t)n1, 256), 256, 0, s>>>(n1, n2, j0, m.r, phi_t);
+    count_launch(2);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, double* dx, int precision,

@@ -130,6 +130,13 @@ struct DevMesh {
   // the forward solve runs on the solve's own stream
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  // Phi = K11^-1 K12 Sigma^-1 (n1 x n2, float, stored transposed: row j of
+  // Phi_t is column j of Phi): with it the x1 block of Eq. 8 splits into the
+  // contact-free solve (which overlaps the reduced system) plus
+  // Phi[:, c] v after it (mixed precision)
+  float* Phi_t = nullptr;
+  float* bx = nullptr;        // nf*3 float solve vector of the contact-free x1 solve
   int red_gen = 0;            // bumped whenever the reduced buffers move
 };
 
@@ -202,6 +209,13 @@ cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, con
 // Returns false (nothing launched) when that split does not apply.
 bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
                      int* info, int num_sms, int nc_host);
+// x1 = bx1 + Phi[:, c] v (float64 out, solver order, 3 per position) after a
+// prepared reduced solve (k_reduced.cu); reads n_c on the device.
+cudaError_t phi_apply(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
+                      int* info, const float* bx1, double* x1);
+// Phi_t at prefactor time (k_solve.cu), from the float64 factor and Sigma^-1,
+// using the mesh workspace's float64 solve vectors as scratch.
+cudaError_t compute_phi(cudaStream_t s, const DevMesh& m, float* phi_t);
 void set_solver_smem_limits(int max_bytes);
 void set_reduced_smem_limits();
 

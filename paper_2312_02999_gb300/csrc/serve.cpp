@@ -288,8 +288,10 @@ fsim_status fsim_server_create(fsim_ctx_t ctx, const fsim_server_config* cfg, fs
   sv->coop_ctas = std::max(1, ctx->num_sms / cfg->workers);
   sv->budget = cfg->mem_budget_bytes;
   sv->workers.resize(cfg->workers);
+  int prio_lo = 0, prio_hi = 0;     // worker streams above the side streams
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   for (auto& w : sv->workers) {
-    if (cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&w.stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaHostAlloc((void**)&w.h_counters, sizeof(int) * kCounters, cudaHostAllocDefault) !=
             cudaSuccess ||
         cudaHostAlloc((void**)&w.h_scal, sizeof(double) * kScal, cudaHostAllocDefault) != cudaSuccess) {
