@@ -319,18 +319,22 @@ int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const 
   launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, kappa, prec);
   if (m.n2 > 0) launch_mark_scan(s, m);
   else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
-  TRY(sync_read(ex, m));
-  int nc = ex.h_counters[3];
-  TRY(ensure_reduced(ex, m, std::max(nc, 1)));
-  if (nc > 0) {
-    CK(cudaMemsetAsync(m.Bc, 0, sizeof(double) * 9 * (size_t)nc * nc, s));
-    CK(cudaMemsetAsync(m.bocc, 0, sizeof(int) * (size_t)nc * nc, s));
-  }
-  launch_barrier_scatter(s, m, npairs, nc, gout);
+  // n_c stays on the device until the one read-back below: B-check is zeroed
+  // and assembled in place when it fits the current reduced buffers
+  const int cap_now = m.Bc != nullptr ? m.nc_cap : 0;
+  launch_zero_reduced(s, m, cap_now);
+  launch_barrier_scatter(s, m, npairs, cap_now, 3, gout);
   const int nb = gnorm_blocks(m.n);
   launch_gnorm2(s, m, gout, m.partials, nb);
   launch_sum_partials(s, m.partials, nb, m.scal + 3);
   TRY(sync_read(ex, m));
+  const int nc = ex.h_counters[3];
+  TRY(ensure_reduced(ex, m, std::max(nc, 1)));
+  if (nc > cap_now) {       // the buffers grew: assemble B-check again
+    CK(cudaMemsetAsync(m.Bc, 0, sizeof(double) * 9 * (size_t)nc * nc, s));
+    CK(cudaMemsetAsync(m.bocc, 0, sizeof(int) * (size_t)nc * nc, s));
+    launch_barrier_scatter(s, m, npairs, m.nc_cap, 2, gout);
+  }
   *nc_out = nc;
   *gn2_out = ex.h_scal[3];
   return FSIM_OK;

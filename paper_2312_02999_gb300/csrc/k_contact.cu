@@ -475,44 +475,67 @@ __global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ 
 }
 
 // Pass C: scatter gradients (through W) into g and blocks into B-check.
+// One thread per (pair, a, b): the pair's 12 x 12 block (a, b) mapped through
+// the W rows of its vertices a and b into B-check, and (b == 0) vertex a's
+// gradient into g.  n_c is read on the device; B-check is written only when
+// it fits the reduced buffers (n_c <= nc_cap), else the host grows them and
+// scatters the Hessian blocks again.  mode: 1 gradient, 2 B-check, 3 both.
 __global__ void k_barrier_scatter(int64_t np, const unsigned long long* __restrict__ pairs,
                                   const int* __restrict__ tris, const int* __restrict__ edges,
                                   const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
                                   const double* __restrict__ Wval, const int* __restrict__ x2of,
                                   const int* __restrict__ x2mark, const double* __restrict__ pgrad,
-                                  const double* __restrict__ phess, int nc, double* __restrict__ g,
+                                  const double* __restrict__ phess, const int* __restrict__ ncp,
+                                  int nc_cap, int mode, double* __restrict__ g,
                                   double* __restrict__ Bc, int* __restrict__ bocc) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = t >> 4;
   if (p >= np) return;
+  const int a = (int)((t >> 2) & 3), b = (int)(t & 3);
+  const int nc = *ncp;
+  const bool grad = (mode & 1) && b == 0;
+  const bool hess = (mode & 2) && nc <= nc_cap;
+  if (!grad && !hess) return;
   int type, i, j;
   unpack_key(pairs[p], type, i, j);
   int V[4];
   load_pair(type, i, j, tris, edges, V);
   const int ld = 3 * nc;
-  for (int a = 0; a < 4; ++a) {
-    for (int64_t ea = Wptr[V[a]]; ea < Wptr[V[a] + 1]; ++ea) {
-      const int va = Wcol[ea];
-      const int qa = x2of[va];
-      if (qa < 0) continue;                       // pinned: no DOF
-      const double wa = Wval[ea];
+  for (int64_t ea = Wptr[V[a]]; ea < Wptr[V[a] + 1]; ++ea) {
+    const int va = Wcol[ea];
+    const int qa = x2of[va];
+    if (qa < 0) continue;                         // pinned: no DOF
+    const double wa = Wval[ea];
+    if (grad)
       for (int d = 0; d < 3; ++d) atomicAdd(g + 3 * (size_t)va + d, wa * pgrad[p * 12 + 3 * a + d]);
-      const int ca = x2mark[qa] - 1;
-      if (ca < 0 || ca >= nc) continue;
-      for (int b = 0; b < 4; ++b)
-        for (int64_t eb = Wptr[V[b]]; eb < Wptr[V[b] + 1]; ++eb) {
-          const int qb = x2of[Wcol[eb]];
-          if (qb < 0) continue;
-          const int cb = x2mark[qb] - 1;
-          if (cb < 0 || cb >= nc) continue;
-          const double ww = wa * Wval[eb];
-          const double* h = phess + p * 144 + (a * 4 + b) * 9;
-          double* dst = Bc + (size_t)(3 * ca) * ld + 3 * cb;
-          for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) atomicAdd(dst + (size_t)r * ld + c, ww * h[3 * r + c]);
-          bocc[(size_t)ca * nc + cb] = 1;
-        }
+    if (!hess) continue;
+    const int ca = x2mark[qa] - 1;
+    if (ca < 0 || ca >= nc) continue;
+    for (int64_t eb = Wptr[V[b]]; eb < Wptr[V[b] + 1]; ++eb) {
+      const int qb = x2of[Wcol[eb]];
+      if (qb < 0) continue;
+      const int cb = x2mark[qb] - 1;
+      if (cb < 0 || cb >= nc) continue;
+      const double ww = wa * Wval[eb];
+      const double* h = phess + p * 144 + (a * 4 + b) * 9;
+      double* dst = Bc + (size_t)(3 * ca) * ld + 3 * cb;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) atomicAdd(dst + (size_t)r * ld + c, ww * h[3 * r + c]);
+      bocc[(size_t)ca * nc + cb] = 1;
     }
   }
+}
+
+// Zero the first (3 n_c)^2 entries of B-check and n_c^2 of its block
+// occupancy, n_c read on the device (nothing when n_c > nc_cap).
+__global__ void k_zero_reduced(const int* __restrict__ ncp, int nc_cap, double* __restrict__ Bc,
+                               int* __restrict__ bocc) {
+  const int nc = *ncp;
+  if (nc <= 0 || nc > nc_cap) return;
+  const int64_t nb = 9 * (int64_t)nc * nc, no = (int64_t)nc * nc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb; e += stride) Bc[e] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < no; e += stride) bocc[e] = 0;
 }
 
 // Additive CCD (Li, Kaufman & Jiang 2021) time of impact of one candidate.
@@ -866,6 +889,8 @@ __global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __res
                              const double* __restrict__ ds, double skin, double margin,
                              int* counters, double* scal) {
   if (ds == nullptr && threadIdx.x == 0) scal[4] = __longlong_as_double(0x7ff0000000000000LL);  // d_min = inf
+  // maxima of the squared lengths; one square root each at the end
+  // (sqrt is monotone and correctly rounded, so this is max |.| exactly)
   double dmax = 0.0, smax = 0.0;
   for (int v = threadIdx.x; v < Ns; v += blockDim.x) {
     double d2 = 0.0, q2 = 0.0;
@@ -875,12 +900,12 @@ __global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __res
       d2 += e * e;
       if (ds) q2 += ds[3 * v + d] * ds[3 * v + d];
     }
-    dmax = fmax(dmax, sqrt(d2));
-    smax = fmax(smax, sqrt(q2));
+    dmax = fmax(dmax, d2);
+    smax = fmax(smax, q2);
   }
-  dmax = block_max_d(dmax);
+  dmax = sqrt(block_max_d(dmax));
   __syncthreads();
-  smax = block_max_d(smax);
+  smax = sqrt(block_max_d(smax));
   __shared__ int rebuild;
   if (threadIdx.x == 0) {
     const bool valid = counters[12] == 1 && counters[14] == 0;
@@ -1052,13 +1077,20 @@ void launch_ccd_reset(cudaStream_t st, const DevMesh& m) {
   count_launch();
 }
 
-void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int nc, double* g) {
+void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int nc_cap, int mode,
+                            double* g) {
   np = np < m.cap_act ? np : m.cap_act;
   if (np <= 0) return;
-  k_barrier_scatter<<<(unsigned)((np + 63) / 64), 64, 0, st>>>(np, m.pairs, m.tris, m.edges,
-                                                              m.Wptr, m.Wcol, m.Wval, m.x2of,
-                                                              m.x2mark, m.pair_grad, m.pair_hess,
-                                                              nc, g, m.Bc, m.bocc);
+  const int64_t threads = 16 * np;
+  k_barrier_scatter<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+      np, m.pairs, m.tris, m.edges, m.Wptr, m.Wcol, m.Wval, m.x2of, m.x2mark, m.pair_grad,
+      m.pair_hess, m.counters + 3, nc_cap, mode, g, m.Bc, m.bocc);
+  count_launch();
+}
+
+void launch_zero_reduced(cudaStream_t st, const DevMesh& m, int nc_cap) {
+  if (nc_cap <= 0 || m.Bc == nullptr) return;
+  k_zero_reduced<<<2 * 152, 256, 0, st>>>(m.counters + 3, nc_cap, m.Bc, m.bocc);
   count_launch();
 }
 

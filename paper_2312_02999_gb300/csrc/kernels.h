@@ -167,7 +167,12 @@ void launch_barrier_pairs(cudaStream_t s, const DevMesh& m, int64_t npairs, cons
                           double dhat, double kappa, int precision);
 void launch_mark_scan(cudaStream_t s, const DevMesh& m);
 // Scatter pair gradients into g and Hessian blocks into the dense B-check (3nc)^2.
-void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, int nc, double* g);
+// B-check and g from the per-pair blocks; n_c is read on the device and
+// B-check is written only when n_c <= nc_cap (mode: 1 gradient, 2 B-check, 3 both)
+void launch_barrier_scatter(cudaStream_t s, const DevMesh& m, int64_t npairs, int nc_cap, int mode,
+                            double* g);
+// zero B-check and its block occupancy for the n_c on the device (when n_c <= nc_cap)
+void launch_zero_reduced(cudaStream_t s, const DevMesh& m, int nc_cap);
 // Reset the CCD outputs: counters[1] = counters[9] = 0 and scal[1] = 1.
 void launch_ccd_reset(cudaStream_t s, const DevMesh& m);
 
