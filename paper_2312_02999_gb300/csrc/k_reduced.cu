@@ -689,14 +689,20 @@ __device__ void cta_trsv_packed(const float* A, const float* DI, int n, float* t
 }
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
+  // red holds kSW + 1 doubles; warp 0 adds the warp sums (float64 adds are
+  // slow on GB300: one shuffle tree, not a loop in every thread)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kSW; ++w) t += red[w];
-  return t;
+  if (wid == 0) {
+    double t = lane < kSW ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[kSW] = t;
+  }
+  __syncthreads();
+  return red[kSW];
 }
 
 // k_small_s: S = Sigma^-1[c, c], its factor (plain, row-major into a.S for
@@ -826,74 +832,82 @@ __device__ void cta_lt_apply_f(const float* Lp, int nc, const double* p, float* 
   }
 }
 
-// Refinement products in float64, one warp per row (warp w of nw):
-// w = S v with S = Sigma^-1[c, c] (x) I_3 (gathered into S64 by k_small_s)
-__device__ void refine_sv(const RedArgs<float>& a, int nc, int w, int nw) {
-  // four rows per pass with independent accumulators, so the loads of all
-  // four are in flight together (the pass is bound by load latency)
-  constexpr int kR = 4;
-  const int lane = threadIdx.x & 31, n3 = 3 * nc;
-  for (int e0 = w; e0 < n3; e0 += kR * nw) {
-    double acc[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-      acc[r] = 0.0;
-      const int e = e0 + r * nw;
-      if (e < n3) {
-        const double* srow = a.S64 + (size_t)(e / 3) * nc;
-        const int ax = e % 3;
-#pragma unroll
-        for (int q = 0; q < kClusNc / 32; ++q) {
-          const int j = lane + 32 * q;
-          if (j < nc) acc[r] += srow[j] * a.v[3 * j + ax];
-        }
+// Float64 refinement products.  GB300 issues a warp-wide float64 FMA about
+// every 64 cycles per SM sub-partition, so these loops are laid out to keep
+// the number of float64 warp instructions small: thread (vertex i, part q)
+// of kRP parts accumulates the three rows of vertex i over every kRP-th
+// term, the kRP parts (consecutive lanes) are summed by shuffles.  t is the
+// thread's index among nt threads taking part (nt a multiple of 32, the
+// same loop trip count in every lane).
+constexpr int kRP = 4;
+
+// w = S v with S = Sigma^-1[c, c] (x) I_3 (S64 gathered by k_small_s)
+__device__ void refine_sv(const RedArgs<float>& a, int nc, int t, int nt) {
+  const int total = kRP * nc;
+  for (int base = 0; base < total; base += nt) {
+    const int item = base + t;
+    const bool ok = item < total;
+    const int i = ok ? item / kRP : 0, q = item % kRP;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (ok) {
+      const double* srow = a.S64 + (size_t)i * nc;
+      for (int j = q; j < nc; j += kRP) {
+        const double sij = srow[j];
+        s0 += sij * a.v[3 * j];
+        s1 += sij * a.v[3 * j + 1];
+        s2 += sij * a.v[3 * j + 2];
       }
     }
 #pragma unroll
-    for (int r = 0; r < kR; ++r) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-      const int e = e0 + r * nw;
-      if (lane == 0 && e < n3) a.w[e] = acc[r];
+    for (int o = kRP / 2; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (ok && q == 0) {
+      a.w[3 * i] = s0;
+      a.w[3 * i + 1] = s1;
+      a.w[3 * i + 2] = s2;
     }
   }
 }
 
-// rho = y - v - B w over the block-row lists of B; returns this lane's share
-// of |rho|^2 (lane 0 of each warp holds it).  Four rows per pass, as above.
-__device__ double refine_rho(const RedArgs<float>& a, int nc, int w, int nw) {
-  constexpr int kR = 4;
-  const int lane = threadIdx.x & 31, n3 = 3 * nc;
+// rho = y - v - B w over the block-row lists of B; returns this thread's
+// share of |rho|^2
+__device__ double refine_rho(const RedArgs<float>& a, int nc, int t, int nt) {
+  const int total = kRP * nc, n3 = 3 * nc;
   double r2 = 0.0;
-  for (int e0 = w; e0 < n3; e0 += kR * nw) {
-    double acc[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-      acc[r] = 0.0;
-      const int row = e0 + r * nw;
-      if (row < n3) {
-        const int i = row / 3;
-        const double* brow = a.Bc + (size_t)row * n3;
-        const int* li = a.list + (size_t)i * nc;
-        const int ci = a.cnt[i];
-#pragma unroll
-        for (int q = 0; q < kClusNc / 32; ++q) {
-          const int e = lane + 32 * q;
-          if (e < ci) {
-            const int j = li[e];
-            acc[r] += brow[3 * j] * a.w[3 * j] + brow[3 * j + 1] * a.w[3 * j + 1] +
-                      brow[3 * j + 2] * a.w[3 * j + 2];
-          }
-        }
+  for (int base = 0; base < total; base += nt) {
+    const int item = base + t;
+    const bool ok = item < total;
+    const int i = ok ? item / kRP : 0, q = item % kRP;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (ok) {
+      const double* b0 = a.Bc + (size_t)(3 * i) * n3;
+      const double* b1 = b0 + n3;
+      const double* b2 = b1 + n3;
+      const int* li = a.list + (size_t)i * nc;
+      const int ci = a.cnt[i];
+      for (int e = q; e < ci; e += kRP) {
+        const int j3 = 3 * li[e];
+        const double w0 = a.w[j3], w1 = a.w[j3 + 1], w2 = a.w[j3 + 2];
+        s0 += b0[j3] * w0 + b0[j3 + 1] * w1 + b0[j3 + 2] * w2;
+        s1 += b1[j3] * w0 + b1[j3 + 1] * w1 + b1[j3 + 2] * w2;
+        s2 += b2[j3] * w0 + b2[j3 + 1] * w1 + b2[j3 + 2] * w2;
       }
     }
 #pragma unroll
-    for (int r = 0; r < kR; ++r) {
+    for (int o = kRP / 2; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (ok && q == 0) {
+      const double acc[3] = {s0, s1, s2};
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-      const int row = e0 + r * nw;
-      if (lane == 0 && row < n3) {
-        const double rr = a.y[row] - a.v[row] - acc[r];
+      for (int ax = 0; ax < 3; ++ax) {
+        const int row = 3 * i + ax;
+        const double rr = a.y[row] - a.v[row] - acc[ax];
         a.rho[row] = rr;
         r2 += rr * rr;
       }
@@ -907,7 +921,7 @@ __device__ double refine_rho(const RedArgs<float>& a, int nc, int w, int nw) {
 // cooperative kernel).
 __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   extern __shared__ float smem_f[];
-  __shared__ double red[kSW];
+  __shared__ double red[kSW + 1];
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > kSmallNc) return;
   red_layout(a, nc);
@@ -940,9 +954,9 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   double prev = -1.0;
   for (int it = 0; it < a.refine; ++it) {
     // w = S v with S = Sigma^-1[c, c] (x) I_3 in float64 (S gathered by k_small_s)
-    refine_sv(a, nc, tid >> 5, kSW);
+    refine_sv(a, nc, tid, kST);
     __syncthreads();
-    double r2 = refine_rho(a, nc, tid >> 5, kSW);
+    double r2 = refine_rho(a, nc, tid, kST);
     r2 = block_sum_d(r2, red);
     const double ys = __ldcg(a.nrm + 2);
     if (!(r2 > 1e-14 * ys)) break;
@@ -998,7 +1012,7 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
   __shared__ double nrm_parts[kCl];
   __shared__ float wsum[kSW][32];
   __shared__ int loff[kClusRowsMax];
-  __shared__ double red[kSW];
+  __shared__ double red[kSW + 1];
   const int nc = *a.nc_dev;
   if (nc <= kSmallNc || nc > kClusNc) return;       // uniform over the cluster
   red_layout(a, nc);
@@ -1012,7 +1026,6 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
   float* t = Ls + prow(kClusNc) + 1024 * (kClusNc / 32);   // n3: rhs / solution (own rows valid)
   float* xg = t + kClusN3;                         // n3: gathered solution (rank 0)
   // own rows: block b is owned by b % kCl; local row lb * 32 + (r % 32)
-  auto own = [&](int r) { return ((r >> 5) % kCl) == rank; };
   auto lrow = [&](int r) { return ((r >> 5) / kCl) * 32 + (r & 31); };
   if (tid < kClusRowsMax) {
     int off = 0;
@@ -1147,13 +1160,31 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
     __syncthreads();
     // trailing update of own rows: A(i, j) -= P_i . P_j, 4 x 4 tiles
     if (m > 0) {
-      const int mb = (m + 3) >> 2, nt = mb * (mb + 1) / 2;
-      for (int tt = tid; tt < nt; tt += kST) {
-        int I = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
-        while ((I + 1) * (I + 2) / 2 <= tt) ++I;
-        while (I * (I + 1) / 2 > tt) --I;
-        if (!own(k1 + 4 * I)) continue;            // 4-row tiles never straddle a block
-        const int J = tt - I * (I + 1) / 2;
+      // only this CTA's 4-row tiles (tile I covers rows k1 + 4I ..; a 32-row
+      // block b below the panel holds tiles (32b - k1)/4 + 0..7, each with
+      // I + 1 column tiles J <= I), numbered consecutively over the threads
+      const int mb = (m + 3) >> 2;
+      int bfirst = rank;
+      while (bfirst <= k) bfirst += kCl;
+      int total = 0;
+      for (int b = bfirst; 32 * b < n3; b += kCl) {
+        const int I0 = (32 * b - k1) >> 2, ns = min(8, mb - I0);
+        total += ns * (I0 + 1) + ns * (ns - 1) / 2;
+      }
+      for (int u = tid; u < total; u += kST) {
+        int rem = u, I = 0, J = 0;
+        for (int b = bfirst; 32 * b < n3; b += kCl) {
+          const int I0 = (32 * b - k1) >> 2, ns = min(8, mb - I0);
+          const int cnt = ns * (I0 + 1) + ns * (ns - 1) / 2;
+          if (rem < cnt) {
+            int s2 = 0;
+            while (rem >= I0 + s2 + 1) { rem -= I0 + s2 + 1; ++s2; }
+            I = I0 + s2;
+            J = rem;
+            break;
+          }
+          rem -= cnt;
+        }
         float acc[4][4];
 #pragma unroll
         for (int p = 0; p < 4; ++p)
@@ -1264,11 +1295,10 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
   // (L_s (x) I)^-T on the gathered solution (rank 0), result into a.v / added to it
   auto finish = [&](bool add) {
     if (rank == 0) {
-      for (int q = 0; q < kCl; ++q) {
-        const float* rt = (q == 0) ? t : cl.map_shared_rank(t, q);
-        for (int b = q; b < nblk; b += kCl)
-          for (int e = tid; e < 32; e += kST)
-            if (32 * b + e < n3) xg[32 * b + e] = rt[32 * b + e];
+      // every row from the CTA that owns it, all remote loads in flight at once
+      for (int r = tid; r < n3; r += kST) {
+        const int q = (r >> 5) % kCl;
+        xg[r] = (q == 0) ? t[r] : cl.map_shared_rank(t, q)[r];
       }
       __syncthreads();
       cta_trsv_packed<true>(Ls, LsDI, nc, xg, 3);
@@ -1297,11 +1327,12 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
 
   // ---- float64 refinement, rows split over the cluster ----------------------
   double prev = -1.0;
-  const int gw = rank * kSW + wid;                 // one warp per row, rows split over the cluster
+  // refinement threads numbered warp-interleaved over the cluster's CTAs
+  const int gt = (wid * kCl + rank) * 32 + lane;
   for (int it = 0; it < a.refine; ++it) {
-    refine_sv(a, nc, gw, kCl * kSW);
+    refine_sv(a, nc, gt, kCl * kST);
     cl.sync();
-    double r2 = refine_rho(a, nc, gw, kCl * kSW);
+    double r2 = refine_rho(a, nc, gt, kCl * kST);
     r2 = block_sum_d(r2, red);
     if (tid < kCl) cl.map_shared_rank(&nrm_parts[0], tid)[rank] = r2;
     cl.sync();
