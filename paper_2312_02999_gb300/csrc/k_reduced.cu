@@ -1000,13 +1000,16 @@ constexpr size_t kClusSmem =
     sizeof(float) * ((size_t)kClusALoc + 32 * (size_t)kClusN3 + (size_t)prow(kClusNc) +
                      1024 * (kClusNc / 32) + 2 * (size_t)kClusN3);
 
-__global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
+// (__maxnreg__ rather than __launch_bounds__: with the latter ptxas settles
+// on 64 registers and spills; 512 threads x 128 registers fill one SM)
+__global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
   namespace cgx = cooperative_groups;
   cgx::cluster_group cl = cgx::this_cluster();
   extern __shared__ float smem_f[];
   __shared__ float Ds[32][33];
-  __shared__ float Li[32][33];
   __shared__ float dv[32];
+  __shared__ float dvown[kClusRowsMax];            // 1 / L_ii of own rows
+  __shared__ float Dinv[kClusRowsMax / 32][32][33];  // own diagonal blocks, inverted at the end
   __shared__ float xb[2][32];
   __shared__ float part[2][kCl][32];
   __shared__ double nrm_parts[kCl];
@@ -1091,36 +1094,21 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
       }
       __syncthreads();
       if (tid < kb) Ds[tid][tid] = Ds[tid][tid] * dv[tid];
+      if (tid < 32) dvown[lrow(k0) + tid] = dv[tid];   // kept for the inverse below
       __syncthreads();
-      if (wid == 0) {
-        float x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          x[i] *= dv[i];
-#pragma unroll
-          for (int l = i + 1; l < 32; ++l) x[l] -= Ds[l][i] * x[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) Li[i][lane] = (i >= lane) ? x[i] : 0.f;
-      }
     }
     cl.sync();
-    if (rank != owner) {     // the owner's diagonal factor, its inverse and 1/diag
+    if (rank != owner) {     // the owner's diagonal factor and 1/diag
       const float* rD = cl.map_shared_rank(&Ds[0][0], owner);
-      const float* rL = cl.map_shared_rank(&Li[0][0], owner);
       const float* rv = cl.map_shared_rank(&dv[0], owner);
 #pragma unroll
-      for (int e = tid; e < 32 * 33; e += kST) {
-        (&Ds[0][0])[e] = rD[e];
-        (&Li[0][0])[e] = rL[e];
-      }
+      for (int e = tid; e < 32 * 33; e += kST) (&Ds[0][0])[e] = rD[e];
       if (tid < 32) dv[tid] = rv[tid];
     }
     __syncthreads();
-    // own panel rows: x L_kk^T = a (registers), into A and the panel copy;
-    // one warp per own block below the panel
+    // own panel rows: x L_kk^T = a (registers), into A and into the panel
+    // copy of every CTA of the cluster (remote stores, made visible by the
+    // cluster barrier below); one warp per own block below the panel
     for (int idx = tid; idx < kClusRowsMax; idx += kST) {
       const int b = ((idx >> 5) * kCl) + rank;
       const int r = 32 * b + (idx & 31);
@@ -1136,28 +1124,23 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
           for (int l = q + 1; l < 32; ++l) x[l] -= x[q] * Ds[l][q];
         }
 #pragma unroll
-        for (int l = 0; l < 32; ++l) {
-          row[l] = x[l];
-          Pt[l * kClusN3 + (r - k1)] = x[l];
+        for (int l = 0; l < 32; ++l) row[l] = x[l];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) Pt[l * kClusN3 + (r - k1)] = x[l];
+        for (int q = 1; q < kCl; ++q) {
+          float* dst = cl.map_shared_rank(Pt, (rank + q) % kCl);
+#pragma unroll
+          for (int l = 0; l < 32; ++l) dst[l * kClusN3 + (r - k1)] = x[l];
         }
       }
     }
+    // the owner keeps the plain diagonal factor (inverted after the loop)
+    if (rank == owner)
+      for (int e = tid; e < kb * 32; e += kST) {
+        const int i = e >> 5, j = e & 31;
+        if (j <= i) Ael(k0 + i, k0 + j) = Ds[i][j];
+      }
     cl.sync();
-    // gather the other CTAs' panel rows
-    for (int q = 0; q < kCl; ++q) {
-      if (q == rank) continue;
-      const float* rP = cl.map_shared_rank(Pt, q);
-      for (int b = q; b < nblk; b += kCl) {
-        if (b <= k) continue;
-        const int rows = min(32, n3 - 32 * b);
-#pragma unroll 4
-        for (int e = tid; e < 32 * rows; e += kST) {
-          const int l = e / rows, rr = 32 * b + e % rows - k1;
-          Pt[l * kClusN3 + rr] = rP[l * kClusN3 + rr];
-        }
-      }
-    }
-    __syncthreads();
     // trailing update of own rows: A(i, j) -= P_i . P_j, 4 x 4 tiles
     if (m > 0) {
       // only this CTA's 4-row tiles (tile I covers rows k1 + 4I ..; a 32-row
@@ -1212,12 +1195,31 @@ __global__ void __launch_bounds__(kST) k_clus_v(RedArgs<float> a) {
         }
       }
     }
-    if (rank == owner)
-      for (int e = tid; e < kb * 32; e += kST) {
-        const int i = e >> 5, j = e & 31;
-        if (j <= i) Ael(k0 + i, k0 + j) = Li[i][j];    // inverted diagonal block
-      }
     __syncthreads();
+  }
+  // L_kk^-1 of every own diagonal block (for the solves), one warp per
+  // block, all blocks at once: column `lane` by substitution in registers
+  {
+    const int b = rank + kCl * wid;
+    if (b < nblk) {
+      const int k0 = 32 * b, kb = min(32, n3 - k0), lb = lrow(k0);
+      float (*D)[33] = Dinv[wid];
+      for (int i = 0; i < 32; ++i)
+        D[i][lane] = (i < kb && lane <= i) ? A[loff[lb + i] + k0 + lane] : 0.f;
+      __syncwarp();
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        x[i] *= dvown[lb + i];
+#pragma unroll
+        for (int l = i + 1; l < 32; ++l) x[l] -= D[l][i] * x[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < kb && i >= lane) A[loff[lb + i] + k0 + lane] = x[i];
+    }
   }
   cl.sync();
 
