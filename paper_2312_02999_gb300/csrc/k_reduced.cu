@@ -485,6 +485,27 @@ __host__ __device__ constexpr int prow(int i) {
 }
 constexpr int kPtLd = kSmallN3;            // panel scratch: 32 x kPtLd floats
 
+// Outer-product elimination of the unscaled 32 x 32 diagonal block Ds: after
+// step j, Ds[i][c] (c > j) holds the Schur complement; Ds[.][j] (j < i) stays
+// the unscaled column and Ds[j][j] the pivot.  Thread (r0, c) = (tid / 32,
+// tid % 32) owns rows r0 and r0 + 16 of column c; needs 512 threads.  The
+// pivot reciprocal is the hardware approximation (2 ulp; the pivots of these
+// SPD matrices are >= 1): the IEEE division sat on the dependent chain of
+// every step and the float32 factor only preconditions float64-refined
+// solves.  Two columns per barrier measured no faster.
+__device__ __forceinline__ void eliminate_diag(float (*Ds)[33], int kb) {
+  const int tid = threadIdx.x, r0 = tid >> 5, c = tid & 31;
+  for (int j = 0; j < kb; ++j) {
+    const float inv = __fdividef(1.f, Ds[j][j]);
+    if (c > j) {
+      const float lcj = Ds[c][j] * inv;
+      if (r0 >= c) Ds[r0][c] -= Ds[r0][j] * lcj;
+      if (r0 + 16 >= c) Ds[r0 + 16][c] -= Ds[r0 + 16][j] * lcj;
+    }
+    __syncthreads();
+  }
+}
+
 // Blocked right-looking Cholesky of the packed n x n matrix A in shared
 // memory by one CTA (kST threads); 32-wide panels.  Per panel: the diagonal
 // block is factored in shared memory by all threads (outer-product form, one
@@ -509,21 +530,8 @@ __device__ void cta_chol_packed(float* A, int n, float* Pt, int* info, bool inv_
       Ds[i][j] = (i < kb && j <= i) ? A[prow(k0 + i) + k0 + j] : 0.f;
     }
     __syncthreads();
-    // outer-product elimination on the unscaled block: after step j,
-    // Ds[i][c] (c > j) holds the Schur complement; Ds[.][j] is scaled below.
-    // Thread (r, c) with r = tid / 32 owns rows r and r + 16 of column c.
-    {
-      const int r0 = tid >> 5, c = lane;
-      for (int j = 0; j < kb; ++j) {
-        const float inv = 1.f / Ds[j][j];
-        if (c > j) {
-          const float lcj = Ds[c][j] * inv;
-          if (r0 >= c) Ds[r0][c] -= Ds[r0][j] * lcj;
-          if (r0 + 16 >= c) Ds[r0 + 16][c] -= Ds[r0 + 16][j] * lcj;
-        }
-        __syncthreads();
-      }
-    }
+    // outer-product elimination on the unscaled block; Ds[.][j] is scaled below
+    eliminate_diag(Ds, kb);
     if (tid < kb) {
       float d = Ds[tid][tid];
       if (!(d > 0.f)) {
@@ -941,8 +949,13 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
   // L_s (packed plain + inverted diagonal blocks) into the panel scratch
   float* Ls = Pt;
   const float* LsDI = Pt + prow(nc);
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.spk);
+    float4* dst = reinterpret_cast<float4*>(Ls);
+    const int n4 = (prow(nc) + 1024 * ((nc + 31) / 32)) / 4;
 #pragma unroll 4
-  for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
+    for (int e = tid; e < n4; e += kST) dst[e] = src[e];
+  }
   __syncthreads();
   cta_lt_apply_f(Ls, nc, a.y, t);
   __syncthreads();
@@ -1040,16 +1053,41 @@ __global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
   }
   __syncthreads();
   auto Ael = [&](int r, int c) -> float& { return A[loff[lrow(r)] + c]; };
-  // load own rows of the packed N and L_s
-  for (int b = rank; b < nblk; b += kCl)
-#pragma unroll 4
-    for (int e = tid; e < 32 * 32 * (b + 1); e += kST) {
-      const int rr = e / (32 * (b + 1)), c = e % (32 * (b + 1));
-      const int r = b * 32 + rr;
-      if (r < n3 && c <= r) Ael(r, c) = a.N[prow(r) + c];
+  // load own rows of the packed N and L_s.  A packed row r is a 16-byte
+  // aligned run of 4 (r / 4 + 1) floats in both layouts (padding included,
+  // never read), so rows move as float4: warp w takes own rows w, w + 16, ..
+  // two rows and all their loads in flight at once (a row has <= 96 float4)
+  static_assert(kClusN3 / 4 <= 96, "a packed row must fit three float4 per lane");
+  for (int lr0 = wid; lr0 < kClusRowsMax; lr0 += 2 * kSW) {
+    float4 v[2][3];
+    int len4[2];
+    const float4* src[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int lr = lr0 + h * kSW;
+      const int r = 32 * (((lr >> 5) * kCl) + rank) + (lr & 31);
+      len4[h] = (lr < kClusRowsMax && r < n3) ? (r >> 2) + 1 : 0;
+      src[h] = reinterpret_cast<const float4*>(a.N + prow(r < n3 ? r : 0));
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (lane + 32 * u < len4[h]) v[h][u] = src[h][lane + 32 * u];
     }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (len4[h] == 0) continue;
+      float4* dst = reinterpret_cast<float4*>(A + loff[lr0 + h * kSW]);
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (lane + 32 * u < len4[h]) dst[lane + 32 * u] = v[h][u];
+    }
+  }
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.spk);
+    float4* dst = reinterpret_cast<float4*>(Ls);
+    const int n4 = (prow(nc) + 1024 * ((nc + 31) / 32)) / 4;
 #pragma unroll 4
-  for (int e = tid; e < prow(nc) + 1024 * ((nc + 31) / 32); e += kST) Ls[e] = a.spk[e];
+    for (int e = tid; e < n4; e += kST) dst[e] = src[e];
+  }
   __syncthreads();
 
   // ---- Cholesky of N over the cluster --------------------------------------
@@ -1062,18 +1100,7 @@ __global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
         Ds[i][j] = (i < kb && j <= i) ? Ael(k0 + i, k0 + j) : 0.f;
       }
       __syncthreads();
-      {
-        const int r0 = tid >> 5, c = lane;
-        for (int j = 0; j < kb; ++j) {
-          const float inv = 1.f / Ds[j][j];
-          if (c > j) {
-            const float lcj = Ds[c][j] * inv;
-            if (r0 >= c) Ds[r0][c] -= Ds[r0][j] * lcj;
-            if (r0 + 16 >= c) Ds[r0 + 16][c] -= Ds[r0 + 16][j] * lcj;
-          }
-          __syncthreads();
-        }
-      }
+      eliminate_diag(Ds, kb);
       if (tid < kb) {
         float d = Ds[tid][tid];
         if (!(d > 0.f)) {
@@ -1229,10 +1256,17 @@ __global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
     for (int k = 0; k < nblk; ++k) {
       const int k0 = 32 * k, kb = min(32, n3 - k0), owner = k % kCl, buf = k & 1;
       if (rank == owner) {
-        if (tid < kb) {
+        {   // x_k = L_kk^-1 t_k: 16 threads per row, two terms each, shuffle sum
+          const int rw = tid >> 4, pp = tid & 15;
           float acc = 0.f;
-          for (int l = 0; l <= tid; ++l) acc += Ael(k0 + tid, k0 + l) * t[k0 + l];
-          xb[buf][tid] = acc;
+          if (rw < kb) {
+            const float* drow = &Ael(k0 + rw, k0);
+            if (pp <= rw) acc += drow[pp] * t[k0 + pp];
+            if (pp + 16 <= rw) acc += drow[pp + 16] * t[k0 + pp + 16];
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (pp == 0 && rw < kb) xb[buf][rw] = acc;
         }
         __syncthreads();
         if (tid < kb) {
@@ -1284,10 +1318,17 @@ __global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
           xb[buf][tid] = s;
         }
         __syncthreads();
-        if (tid < kb) {
+        {   // x_k = L_kk^-T s_k: 16 threads per column, two terms each
+          const int col = tid >> 4, pp = tid & 15;
           float acc = 0.f;
-          for (int l = tid; l < kb; ++l) acc += Ael(k0 + l, k0 + tid) * xb[buf][l];
-          t[k0 + tid] = acc;
+          if (col < kb) {
+            if (pp >= col && pp < kb) acc += Ael(k0 + pp, k0 + col) * xb[buf][pp];
+            if (pp + 16 >= col && pp + 16 < kb)
+              acc += Ael(k0 + pp + 16, k0 + col) * xb[buf][pp + 16];
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (pp == 0 && col < kb) t[k0 + col] = acc;
         }
         __syncthreads();
       }
