@@ -32,7 +32,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged frames/s, 30k-vert face mesh; p50/p99 frame latency, mixed vs FP64"
-FP64_TFLOPS_PEAK = 1.25      # GB300 nominal dense FP64 (profiling recipe table)
 ORACLE_ITERS_PER_FRAME = 90  # mean accepted iterations per face frame (GPU and oracle agree)
 
 
@@ -557,11 +556,14 @@ def roofline_entry(cls_name, info, prof, stats):
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"})
         return base
     if cls_name == "local_step":
-        flops = 510.0 * int(info["T"]) * n_launch
-        ach = flops / (ms * 1e-3) / 1e12
-        base.update({"bound": "alu", "achieved": ach, "peak": FP64_TFLOPS_PEAK, "unit": "TFLOP/s",
-                     "frac": ach / FP64_TFLOPS_PEAK, "kernel": "k_elastic<1>",
-                     "work": "510 float64 flop per tet x T per launch"})
+        # the mixed local step (k_elastic_df) moves, per tet, its 4 vertex ids
+        # (16 B), Dm^-1 and A as float pairs (72 + 48 B), the weight (8 B) and
+        # its 12 vertex forces out (96 B), plus 24 B per vertex of positions
+        byts = (240.0 * int(info["T"]) + 24.0 * int(info["n"])) * n_launch
+        ach = byts / (ms * 1e-3) / 1e9
+        base.update({"bound": "hbm", "achieved": ach, "peak": HBM_GBS_PEAK, "unit": "GB/s",
+                     "frac": ach / HBM_GBS_PEAK, "kernel": "k_elastic_df",
+                     "work": "240 B per tet x T + 24 B per vertex x n per launch"})
         return base
     if cls_name in ("trsv_fwd", "trsv_bwd"):
         lv = max(int(info["n_levels"]), 1)
