@@ -63,6 +63,35 @@ def dist_env():
     return rank, world, local
 
 
+# ---------------------------------------------------------------------------
+# replicas over ranks (host logic only; tests/test_replicas_gloo.py runs it
+# on two gloo ranks on the CPU)
+# ---------------------------------------------------------------------------
+def stream_seeds(rank, streams):
+    """Keyframe seed of each of this rank's request streams: every (rank,
+    stream) animates its own sequence, so ranks share no frame and need no
+    data-path collective."""
+    return [3 + rank * streams + s for s in range(streams)]
+
+
+def max_over_ranks(value, world, device=None):
+    """Largest of the ranks' values (the timed region's duration): the whole
+    job is as slow as its slowest replica.  float64 all-reduce(MAX)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_fps(world, streams, steps, max_ms):
+    """Frames of all ranks (world x streams x steps) over the slowest rank's
+    timed region."""
+    return world * streams * steps / (max_ms / 1e3)
+
+
 def workload(n_target, n_frames, seed_offset=0):
     from paper_2312_02999_gb300 import inputs as I
     mesh = I.face_shell(n_target=n_target)
@@ -320,7 +349,7 @@ def run_ours(args):
     field = I.bump_field(mesh, seed=2)
     # stream s of rank r animates its own keyframe sequence (its own "actor")
     F0 = args.first_frame
-    acts = [stream_actuations(I, field, F0, W + K, seed=3 + rank * S + s) for s in range(S)]
+    acts = [stream_actuations(I, field, F0, W + K, seed=sd) for sd in stream_seeds(rank, S)]
     ctx = fsim.Context(local)
     m = ctx.upload(mesh)
     m.prefactor(fsim.params_for(mesh))
@@ -340,12 +369,6 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if world > 1:
-            t = torch.tensor([v], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return v
 
     # ---- single-stream legs: one sequence, frames back to back ----------
     def single(prec, profile):
@@ -453,7 +476,7 @@ def run_ours(args):
         clocks = clk.stop() if clk else None
         sinfo = srv.info()
         srv.close()
-        return {"total_ms": max_over_ranks(total_ms), "lat": lat, "stats": stats,
+        return {"total_ms": max_over_ranks(total_ms, world, dev), "lat": lat, "stats": stats,
                 "launches": launches, "clocks": clocks, "server": sinfo}
 
     results = {}
@@ -477,7 +500,7 @@ def run_ours(args):
         return
 
     def fps(r):
-        return world * S * K / (r["total_ms"] / 1e3)
+        return whole_job_fps(world, S, K, r["total_ms"])
 
     sm, s64 = results["single_mixed"], results["single_fp64"]
     srv_m = results["served_mixed"]
