@@ -1,4 +1,8 @@
-// Reduced contact system of Sec. 3.2 in one cooperative launch.
+// Reduced contact system of Sec. 3.2.  The cooperative kernel k_reduced
+// (float64, or n_c above the cluster path) runs the phases below in one
+// launch; the float32 paths for small n_c (k_small_s/x/n/v, the 4-CTA
+// cluster k_clus_v) run the same phases as separate kernels, the first ones
+// on a side stream.
 //
 // Eq. 10-11: Sigma-hat^-1 y2 = u - Sigma^-1 Q^T v with u = Sigma^-1 y2 and,
 // in the push-through form (B-check is PSD and usually singular, so it is
@@ -988,12 +992,15 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
 // ---------------------------------------------------------------------------
 // k_clus_v: the same solve for kSmallNc < n_c <= kClusNc on a cluster of kCl
 // CTAs.  32-row blocks of the packed N are spread block-cyclically over the
-// CTAs' shared memory; the owner of a panel factors its diagonal block and
-// the others read it (with its inverse) through distributed shared memory;
-// each CTA solves and updates only its own rows, after gathering the whole
-// panel from the other CTAs.  The triangular solves pass 32-value blocks
-// through distributed shared memory with one cluster barrier per block, and
-// the float64 residuals of the refinement are split over the CTAs.
+// CTAs' shared memory.  Per panel the owner factors its diagonal block and the
+// others copy it through distributed shared memory; each CTA solves its own
+// rows of the panel and stores them into the panel copy of every CTA
+// (distributed shared-memory stores, visible after the cluster barrier that
+// follows), then updates only its own rows.  The diagonal blocks are
+// inverted after the factorisation, one warp per block.  The triangular
+// solves pass 32-value blocks through distributed shared memory with one
+// cluster barrier per block, and the float64 residuals of the refinement are
+// split over the CTAs.
 // ---------------------------------------------------------------------------
 constexpr int kClusRowsMax = 32 * ((kClusN3 / 32 + kCl - 1) / kCl);   // own rows per CTA
 // largest packed storage of the rows one CTA owns (padded row lengths)
