@@ -558,6 +558,7 @@ def run_ours(args):
 
 FP32_TFLOPS_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 HBM_GBS_PEAK = 6777.0                                # measured copy bandwidth
+KCLUS_DRAM_BYTES = 584e3                             # k_clus_v per launch, ncu (face frames 20..)
 
 
 def roofline_entry(cls_name, info, prof, stats):
@@ -576,7 +577,12 @@ def roofline_entry(cls_name, info, prof, stats):
                      "kernel": "reduced-system kernels (k_small_s/x/n/v, k_clus_v, k_reduced<float>)",
                      "work": "13.83 n_c^3 float32 flop per launch (two Cholesky factorisations "
                              "and the N product), summed over the timed global steps",
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"})
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
+                     # DRAM bytes (read + write) of one launch of the class's main
+                     # kernel, k_clus_v, from an ncu capture of the same code on these
+                     # face frames; L2 serves the rest (N, L_s, B rows are small)
+                     "traffic": KCLUS_DRAM_BYTES,
+                     "traffic_kernel": "k_clus_v (ncu dram__bytes_read.sum + dram__bytes_write.sum)"})
         return base
     if cls_name == "local_step":
         # the mixed local step (k_elastic_df) moves, per tet, its 4 vertex ids
