@@ -493,10 +493,13 @@ constexpr int kPtLd = kSmallN3;            // panel scratch: 32 x kPtLd floats
 // step j, Ds[i][c] (c > j) holds the Schur complement; Ds[.][j] (j < i) stays
 // the unscaled column and Ds[j][j] the pivot.  Thread (r0, c) = (tid / 32,
 // tid % 32) owns rows r0 and r0 + 16 of column c; needs 512 threads.  The
-// pivot reciprocal is the hardware approximation (2 ulp; the pivots of these
-// SPD matrices are >= 1): the IEEE division sat on the dependent chain of
-// every step and the float32 factor only preconditions float64-refined
-// solves.  Two columns per barrier measured no faster.
+// pivot reciprocal is the hardware approximation (within 2 ulp for pivots
+// in [2^-126, 2^126]; those of N = I + L^T B L are >= 1, those of
+// S = Sigma^-1[c, c] are positive and far from either end): the IEEE
+// division sat on the dependent chain of every step, and these float32
+// factors are refined in float64 (N) or feed only the float32 products and
+// solves of the reduced system (S).  Two columns per barrier measured no
+// faster.
 __device__ __forceinline__ void eliminate_diag(float (*Ds)[33], int kb) {
   const int tid = threadIdx.x, r0 = tid >> 5, c = tid & 31;
   for (int j = 0; j < kb; ++j) {
