@@ -201,7 +201,7 @@ def cpu_baseline(n_target, first):
 
 def bench_config(args, world):
     S, K = args.streams, args.steps
-    return {"workload": "face_shell_30k", "n_target": args.n_target, "form": "served",
+    return {"workload": f"face_shell_{round(args.n_target / 1000)}k", "n_target": args.n_target, "form": "served",
             "streams": S, "workers": S, "frames_per_stream": K, "precision": "mixed",
             "step": f"{S} frames, one per stream (each warm-started from its own previous frame)",
             "frames": f"sequence frames {args.first_frame}.. (first solved from rest, then "
@@ -318,7 +318,7 @@ def run_compare(args):
     w10, c10, s10 = out["woodbury_kappa_x10"], out["pcg_kappa_x10"], out["schur_kappa_x10"]
     line = {"comparison": "global step, Schur + Woodbury (Eq. 8-11) vs Schur only (dense Sigma-hat, "
                           "Sec. 3.1) vs PD-preconditioned CG",
-            "workload": "face_shell_30k", "frames": f"{F0 + 1}..{F0 + K}", "precision": "float64",
+            "workload": f"face_shell_{round(args.n_target / 1000)}k", "frames": f"{F0 + 1}..{F0 + K}", "precision": "float64",
             "results": out,
             "pcg_over_woodbury_gstep": c1["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
             "schur_over_woodbury_gstep": s1["global_step_ms_per_iter"] / w1["global_step_ms_per_iter"],
