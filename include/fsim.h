@@ -134,7 +134,20 @@ typedef struct {
   double sum_nc3;         /* sum of n_c^3 over the frame's global steps (the
                              reduced system's work scales with it)            */
   int64_t cg_iterations;  /* CG iterations of the frame (FSIM_SOLVER_PCG)       */
+  int32_t reduced_steps[4]; /* global steps of the frame by the path that solved
+                               the reduced system (index = FSIM_REDUCED_*)    */
 } fsim_frame_stats;
+
+/* Path that solves the reduced contact system of Eq. 11 in one global step
+ * (chosen from n_c and the precision): */
+enum {
+  FSIM_REDUCED_UNUSED = -1,     /* no reduced system (PCG or Schur-only solver)   */
+  FSIM_REDUCED_COOPERATIVE = 0, /* grid-wide blocked Cholesky (float64 form, and
+                                   the mixed form for n_c > 128)                   */
+  FSIM_REDUCED_NONE = 1,        /* mixed form, n_c = 0: dx2 = Sigma^-1 y2          */
+  FSIM_REDUCED_ONE_CTA = 2,     /* mixed form, 0 < n_c <= 96: one CTA              */
+  FSIM_REDUCED_CLUSTER = 3      /* mixed form, 96 < n_c <= 128: 4-CTA cluster      */
+};
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
  * tol_rel 0, max_iters 500, max_ls 40, ccd_s 0.1, accd_max_iters 2000,
@@ -256,9 +269,11 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x,
                               double* bcheck_out, int64_t bcheck_cap);
 
 /* Global step (Eq. 4 through Eq. 8-11): dx_out [3n] solves
- * (H + PositiveDefinite(B)) dx = -g-hat at x (zero on pinned vertices). */
+ * (H + PositiveDefinite(B)) dx = -g-hat at x (zero on pinned vertices).
+ * path_out (may be NULL) receives the FSIM_REDUCED_* path that solved the
+ * reduced system. */
 fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x,
-                                  int precision, double* dx_out);
+                                  int precision, double* dx_out, int32_t* path_out);
 
 /* CCD step bound (Algorithm 1): alpha_m = min(1, min TOI) over the pairs
  * whose swept boxes of s -> s + W dx, inflated by dhat, overlap. */
@@ -295,8 +310,8 @@ fsim_status fsim_profile_reset(fsim_ctx_t ctx);
  * CCD step bound that allocates no device memory.  The paper has no
  * counterpart to this entry point; it exists for callers that cannot let a
  * library allocate GPU memory on its own: engines that reserve all device
- * memory up front in their own pool, applications held to a fixed memory
- * budget, or code recorded into a caller's CUDA graph.
+ * memory up front in their own pool, or applications held to a fixed memory
+ * budget.
  *
  * Computes alpha_m = min(1, min over candidate pairs of the additive-CCD time
  * of impact) exactly as the solver's CCD stage (fsim_eval_ccd) does, for
@@ -304,8 +319,13 @@ fsim_status fsim_profile_reset(fsim_ctx_t ctx);
  * tris_dev [3 Nt] and edges edges_dev [2 Ne] (the sorted unique (lo, hi)
  * pairs of the triangles' edges), all DEVICE pointers owned by the caller;
  * the result is written to the device double *alpha_dev.  Work is queued on
- * `stream` (a cudaStream_t, NULL = default stream) and the call returns after
- * that stream has finished it.
+ * `stream` (a cudaStream_t, NULL = default stream); the call then reads its
+ * status words back and synchronises that stream, so it returns after the
+ * stream has finished the work.  The candidate search tests every
+ * point-triangle and edge-edge pair (O(Ns Nt + Ne^2) box tests: meant for the
+ * few thousand primitives of a contact region); Nt and Ne are limited to
+ * 65535 * 128.  Every entry of tris_dev and edges_dev must lie in [0, Ns):
+ * primitives that break this are skipped and the call returns FSIM_EINVAL.
  *
  * Scratch: a fixed static device array of 2^20 candidate pairs (about 8 MiB),
  * present on every GPU that loads the library until the process exits.  More
@@ -314,8 +334,9 @@ fsim_status fsim_profile_reset(fsim_ctx_t ctx);
  * call on a device looks up the array's device address; make that first call
  * before any stream capture.  All calls share the array, so calls that
  * overlap on the GPU (other streams, other host threads) race: serialise them.
- * Errors: FSIM_EINVAL for null pointers, negative sizes, dhat <= 0,
- * ccd_s outside (0, 1) or accd_max_iters <= 0; FSIM_ECUDA for a CUDA error.
+ * Errors: FSIM_EINVAL for null pointers, negative or too large sizes,
+ * dhat <= 0, ccd_s outside (0, 1), accd_max_iters <= 0 or a primitive index
+ * outside [0, Ns); FSIM_ECUDA for a CUDA error.
  */
 fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_dev, int64_t Ns,
                              const int32_t* tris_dev, int64_t Nt,
@@ -397,8 +418,9 @@ fsim_status fsim_server_poll(fsim_server_t srv, int64_t ticket, int32_t* done);
 /* Block until the request finishes; copy its positions (3n, may be NULL) and
  * statistics, its latency from submit to completion and its queueing time
  * (submit to start), in milliseconds.  Each ticket is waited for once.
- * Returns the solve's status (as fsim_solve_frame would).  Must not race
- * with fsim_server_destroy. */
+ * Returns the solve's status (as fsim_solve_frame would; FSIM_ENOMEM when
+ * its slot's reduced-system buffers had to grow, because n_c rose, beyond
+ * the memory budget).  Must not race with fsim_server_destroy. */
 fsim_status fsim_server_wait(fsim_server_t srv, int64_t ticket, double* x_out,
                              fsim_frame_stats* stats, double* latency_ms, double* queue_ms);
 fsim_status fsim_server_info_get(fsim_server_t srv, fsim_server_info* info);

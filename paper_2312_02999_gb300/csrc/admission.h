@@ -91,4 +91,12 @@ inline Admission admit(const std::vector<int>& queue_mesh, const std::vector<Slo
   return a;
 }
 
+// Growth of a running slot's reduced-system buffers (n_c rose above their
+// size): allowed when the bytes of all slots plus the growth stay within the
+// budget (budget <= 0: unlimited).  Running slots are never evicted, so a
+// growth that does not fit fails its solve with FSIM_ENOMEM.
+inline bool admit_growth(size_t used, size_t delta, int64_t budget) {
+  return budget <= 0 || used + delta <= (size_t)budget;
+}
+
 }  // namespace fsim

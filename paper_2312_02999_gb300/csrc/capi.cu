@@ -106,10 +106,21 @@ int sync_read(const Exec& ex, const DevMesh& m) {
 
 // Make the reduced-system buffers of workspace m large enough for nc
 // contact vertices (grows by 1.5x, at most to n2).
+size_t reduced_bytes(int cap) {
+  if (cap <= 0) return 0;
+  const int64_t n3 = 3 * (int64_t)cap;
+  return sizeof(double) * (size_t)(n3 * n3) + sizeof(int) * (size_t)(2 * (int64_t)cap * cap + cap + 32) +
+         (sizeof(double) + sizeof(float)) * (size_t)reduced_workspace_elems(cap);
+}
+
 int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
   if (nc <= m.nc_cap && m.Bc != nullptr) return FSIM_OK;
   int cap = std::max(nc, std::max(16, m.nc_cap * 3 / 2));
   cap = std::min(cap, std::max(m.n2, 1));
+  const size_t old_bytes = m.Bc != nullptr ? reduced_bytes(m.nc_cap) : 0;
+  const size_t new_bytes = reduced_bytes(cap);
+  if (ex.grow && new_bytes > old_bytes && ex.grow(ex.grow_user, new_bytes - old_bytes) != 0)
+    return FSIM_ENOMEM;
   CK(cudaStreamSynchronize(ex.stream));
   auto release = [&](void* p) {
     if (!p) return;
@@ -119,6 +130,7 @@ int ensure_reduced(const Exec& ex, DevMesh& m, int nc) {
   };
   release(m.Bc); release(m.bocc); release(m.red); release(m.redf);
   m.Bc = nullptr; m.bocc = nullptr; m.red = nullptr; m.redf = nullptr;
+  if (ex.bytes) *ex.bytes -= std::min(*ex.bytes, old_bytes);
   const int64_t n3 = 3 * (int64_t)cap;
   TRY(dalloc(*ex.allocs, &m.Bc, (size_t)(n3 * n3), ex.bytes));
   TRY(dalloc(*ex.allocs, &m.bocc, (size_t)(2 * (int64_t)cap * cap + cap + 32), ex.bytes));
@@ -422,6 +434,7 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
       }));
     }
     st.sum_nc3 += (double)nc * nc * nc;
+    if (p.solver == FSIM_SOLVER_WOODBURY) st.reduced_steps[reduced_path(nc, prec)]++;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
     TRY(with_graph(ex, m, graph_slot(m, 10, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
@@ -491,11 +504,8 @@ void rt_free_list(std::vector<void*>& allocs) { free_list(allocs); }
 void rt_destroy_graphs(DevMesh& m) { destroy_graphs(m); }
 size_t rt_slot_bytes(const MeshState& ms) {
   if (!ms.prefactored) return 0;
-  const int64_t cap = std::min(std::max(ms.d.n2, 1), 64);
-  const int64_t n3 = 3 * cap;
-  return ms.ws_bytes + sizeof(double) * (size_t)(n3 * n3) +
-         sizeof(int) * (size_t)(2 * cap * cap + cap + 32) +
-         (sizeof(double) + sizeof(float)) * (size_t)reduced_workspace_elems((int)cap);
+  const int cap = std::min(std::max(ms.d.n2, 1), 64);
+  return ms.ws_bytes + reduced_bytes(cap);
 }
 MeshState* rt_mesh(fsim_ctx_t ctx, int mesh_id) { return get_mesh(ctx, mesh_id); }
 }  // namespace fsim
@@ -1069,7 +1079,7 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
 }
 
 fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, int precision,
-                                  double* dx_out) {
+                                  double* dx_out, int32_t* path_out) {
   MeshState* ms = get_mesh(ctx, mesh_id);
   TRY(ready(ms));
   if (!x || !dx_out || (precision != 0 && precision != 1)) return FSIM_EINVAL;
@@ -1098,6 +1108,8 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   TRY(sync_read(ex, m));
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
   CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
+  if (path_out)
+    *path_out = ms->p.solver == FSIM_SOLVER_WOODBURY ? reduced_path(nc, precision) : FSIM_REDUCED_UNUSED;
   return FSIM_OK;
 }
 

@@ -7,6 +7,8 @@
 // overlap test keeps every pair the exact float64 test keeps.  The float64
 // test (boxes inflated by dhat, closed intervals) then decides CCD candidates
 // exactly as the oracle does, and the float64 distance decides d < dhat.
+#include <mutex>
+
 #include "contact.cuh"
 #include "kernels.h"
 #include "../../include/fsim.h"
@@ -104,7 +106,9 @@ __device__ __forceinline__ void gather_X(const double* s, const int V[4], double
 __device__ __forceinline__ void append(unsigned long long key, unsigned long long* out, int* count,
                                        int* overflow, int64_t cap) {
   const int idx = atomicAdd(count, 1);
-  if (idx < cap) out[idx] = key;
+  // unsigned compare: a count that wrapped past 2^31 appends is an overflow,
+  // never a negative index
+  if ((unsigned long long)(unsigned)idx < (unsigned long long)cap) out[idx] = key;
   else atomicOr(overflow, 1);
 }
 
@@ -120,14 +124,20 @@ k_cand_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restrict
   const int t0 = blockIdx.y * kTile;
   for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
     const int t = t0 + k;
+    tid3[k][0] = -1;
     if (t < Nt) {
       int ids[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+      // caller-owned indices: a triangle with a vertex outside [0, Ns) is
+      // skipped and reported (counters[3]) instead of being read
+      if ((unsigned)ids[0] >= (unsigned)Ns || (unsigned)ids[1] >= (unsigned)Ns ||
+          (unsigned)ids[2] >= (unsigned)Ns) {
+        atomicExch(counters + 3, 1);
+        continue;
+      }
       double lo[3], hi[3];
       prim_box<3>(s, ds, ids, lo, hi);
       tb[k] = to_box32(lo, hi, 0.0);
       tid3[k][0] = ids[0]; tid3[k][1] = ids[1]; tid3[k][2] = ids[2];
-    } else {
-      tid3[k][0] = -1;
     }
   }
   __syncthreads();
@@ -138,6 +148,7 @@ k_cand_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restrict
   const Box32 vb = to_box32(vlo, vhi, dhat);
   const int nt = min(kTile, Nt - t0);
   for (int k = 0; k < nt; ++k) {
+    if (tid3[k][0] < 0) continue;
     if (!box_overlap32(vb, tb[k])) continue;
     const int a = tid3[k][0], b = tid3[k][1], c = tid3[k][2];
     if (a == v || b == v || c == v) continue;
@@ -150,7 +161,7 @@ k_cand_pt(int Ns, int Nt, const double* __restrict__ s, const double* __restrict
 }
 
 __global__ void __launch_bounds__(kTile)
-k_cand_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
+k_cand_ee(int Ns, int Ne, const double* __restrict__ s, const double* __restrict__ ds,
           const int* __restrict__ edges, double dhat, unsigned long long* __restrict__ out,
           int* counters, int64_t cap) {
   if (blockIdx.y < blockIdx.x) return;        // tiles with j-tile >= i-tile
@@ -159,8 +170,14 @@ k_cand_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
   const int j0 = blockIdx.y * kTile;
   for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
     const int e = j0 + k;
+    eid[k][0] = -1;
     if (e < Ne) {
       int ids[2] = {edges[2 * e], edges[2 * e + 1]};
+      // an edge with an endpoint outside [0, Ns) is skipped and reported
+      if ((unsigned)ids[0] >= (unsigned)Ns || (unsigned)ids[1] >= (unsigned)Ns) {
+        atomicExch(counters + 3, 1);
+        continue;
+      }
       double lo[3], hi[3];
       prim_box<2>(s, ds, ids, lo, hi);
       eb[k] = to_box32(lo, hi, 0.0);
@@ -171,6 +188,7 @@ k_cand_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
   const int i = blockIdx.x * kTile + threadIdx.x;
   if (i >= Ne) return;
   const int ia[2] = {edges[2 * i], edges[2 * i + 1]};
+  if ((unsigned)ia[0] >= (unsigned)Ns || (unsigned)ia[1] >= (unsigned)Ns) return;  // flagged above
   double ilo[3], ihi[3];
   prim_box<2>(s, ds, ia, ilo, ihi);
   const Box32 ib = to_box32(ilo, ihi, dhat);
@@ -178,6 +196,7 @@ k_cand_ee(int Ne, const double* __restrict__ s, const double* __restrict__ ds,
   for (int k = 0; k < ne; ++k) {
     const int j = j0 + k;
     if (j <= i) continue;
+    if (eid[k][0] < 0) continue;
     if (!box_overlap32(ib, eb[k])) continue;
     const int b0 = eid[k][0], b1 = eid[k][1];
     if (b0 == ia[0] || b0 == ia[1] || b1 == ia[0] || b1 == ia[1]) continue;
@@ -1100,20 +1119,24 @@ void launch_zero_reduced(cudaStream_t st, const DevMesh& m, int nc_cap) {
 // CCD step bound without any device allocation.
 //
 // Some callers cannot let a library allocate GPU memory: an animation or game
-// engine that reserves all device memory up front in its own pool, a host
-// application that must stay inside a fixed memory budget, or code that is
-// about to be recorded into someone else's CUDA graph.  For them,
+// engine that reserves all device memory up front in its own pool, or a host
+// application that must stay inside a fixed memory budget.  For them,
 // fsim_ccd_noalloc computes the same additive-CCD step bound as the solver's
 // CCD stage, with every input and output owned by the caller and its only
-// scratch (the candidate-pair list and two counters) in the fixed array below.
+// scratch (the candidate-pair list and its counters) in the fixed array below.
+// Each call reads its status words back and synchronises the caller's stream
+// before it returns.  The candidate search is brute force over all
+// point-triangle and edge-edge pairs (O(Ns Nt + Ne^2) box tests), meant for
+// the few thousand primitives of a contact region.
 // ===========================================================================
 namespace fsim {
 namespace {
 
 // Largest candidate list the static scratch holds (8 MiB of keys).
 constexpr int64_t kNoallocCandidates = int64_t(1) << 20;
-// Words [0, 2): four int counters ([1] candidates, [2] overflow flag), as the
-// pair kernels use them; words [2, 2 + kNoallocCandidates): candidate keys.
+// Words [0, 2): four int counters ([1] candidates, [2] overflow flag, [3] an
+// index outside [0, Ns) in the caller's triangles or edges), as the pair
+// kernels use them; words [2, 2 + kNoallocCandidates): candidate keys.
 // Every GPU that loads the library keeps this array until the process exits.
 constexpr int kNoallocHeaderWords = 2;
 static __device__ __align__(256) unsigned long long
@@ -1121,6 +1144,7 @@ static __device__ __align__(256) unsigned long long
 
 constexpr int kMaxDevices = 64;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;          // guards the per-device address table
 
 // ACCD over a candidate list whose length is read on the device (so the host
 // never has to read it back); fixed grid, grid-stride loop.
@@ -1163,20 +1187,27 @@ extern "C" fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_de
     return FSIM_EINVAL;
   if (Ns > 0 && (!s_dev || !ds_dev)) return FSIM_EINVAL;
   if ((Nt > 0 && !tris_dev) || (Ne > 0 && !edges_dev)) return FSIM_EINVAL;
+  // the candidate kernels tile triangles and edges along gridDim.y
+  if ((Nt + kTile - 1) / kTile > 65535 || (Ne + kTile - 1) / kTile > 65535) return FSIM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FSIM_ECUDA;
   // one-time set-up per device: the host-side name of the array is not a
   // device address, so ask the runtime for the address on this device
-  if (g_noalloc_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return FSIM_ECUDA;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return FSIM_ECUDA;
+      }
+      g_noalloc_ptr[dev] = p;
     }
-    g_noalloc_ptr[dev] = p;
+    scratch = g_noalloc_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned long long* base = (unsigned long long*)g_noalloc_ptr[dev];
+  unsigned long long* base = (unsigned long long*)scratch;
   int* counters = reinterpret_cast<int*>(base);          // header: 4 ints
   unsigned long long* keys = base + kNoallocHeaderWords;
   // the array keeps the previous call's contents: reset the counters
@@ -1191,7 +1222,7 @@ extern "C" fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_de
   }
   if (Ne > 1) {
     const unsigned ne = (unsigned)((Ne + kTile - 1) / kTile);
-    k_cand_ee<<<dim3(ne, ne), kTile, 0, st>>>((int)Ne, s_dev, ds_dev, edges_dev, dhat, keys, counters,
+    k_cand_ee<<<dim3(ne, ne), kTile, 0, st>>>((int)Ns, (int)Ne, s_dev, ds_dev, edges_dev, dhat, keys, counters,
                                               kNoallocCandidates);
   }
   k_accd_count<<<256, 128, 0, st>>>(counters, kNoallocCandidates, keys, s_dev, ds_dev, tris_dev,
@@ -1202,5 +1233,6 @@ extern "C" fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_de
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return FSIM_ECUDA;
+  if (host_counters[3]) return FSIM_EINVAL;      // an index outside [0, Ns)
   return host_counters[2] ? FSIM_ECONTACT_OVERFLOW : FSIM_OK;
 }

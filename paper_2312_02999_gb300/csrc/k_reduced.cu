@@ -20,7 +20,11 @@
 //     v += L^-T N^-1 L^T rho.  The error of v reaches the global residual as
 //     Q^T rho itself, so the stopping test compares |rho| with |y2| (the
 //     Schur right-hand side), not with |y| = |B u_c|, which carries the
-//     barrier stiffness and can be many orders larger.
+//     barrier stiffness and can be many orders larger.  At most
+//     kMixedRefineSteps steps: where cond(N) nears 1 / u32 (a pair at
+//     ~1e-3 d0 with every vertex of the reduced set in contact) a float32
+//     factor gains only 4-10x per step, and 4 steps left |rho| near
+//     1e-3 |y2|; the stopping rule ends well-conditioned solves after 1-2.
 //   8 z2 = u - (Sigma^-1[:, c] (x) I_3) v
 // Pivots use a float32 reciprocal square root refined by two float64 Newton
 // steps (float64-accurate, a far shorter dependent chain than sqrt and a
@@ -1502,6 +1506,9 @@ int64_t reduced_workspace_elems(int nc) {
          (prow(nc) + 1024 * ((int64_t)nc + 31) / 32 + 16) + 4 * n3 + (int64_t)nc * nc + 128;
 }
 
+// Most float64 refinement steps of a float32 reduced factor (see step 7).
+constexpr int kMixedRefineSteps = 12;
+
 int reduced_path(int nc_host, int precision) {
   if (precision == 0 || nc_host < 0 || nc_host > kClusNc) return 0;   // cooperative kernel
   if (nc_host == 0) return 1;
@@ -1513,7 +1520,8 @@ cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, con
                           bool prepared) {
   if (precision == 0)
     return launch_reduced_t<double>(s, m, u, (const double*)y2, z2, info, num_sms, 0, nc_host, false);
-  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, 4, nc_host, prepared);
+  return launch_reduced_t<float>(s, m, u, (const float*)y2, z2, info, num_sms, kMixedRefineSteps,
+                                 nc_host, prepared);
 }
 
 namespace {
@@ -1570,7 +1578,7 @@ __global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply(RedArgs<float> a, 
 
 cudaError_t phi_apply(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
                       int* info, const float* bx1, double* x1) {
-  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, 4);
+  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, kMixedRefineSteps);
   k_phi_apply<<<(m.n1 + 31) / 32, 32 * kPhiSplit, 0, s>>>(a, m.n1, m.Phi_t, bx1, x1);
   count_launch();
   return cudaGetLastError();
@@ -1579,7 +1587,7 @@ cudaError_t phi_apply(cudaStream_t s, const DevMesh& m, const double* u, const v
 bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
                      int* info, int num_sms, int nc_host) {
   if (nc_host <= 0 || nc_host > kClusNc || !m.aux_stream || !m.ev_fork || !m.ev_join) return false;
-  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, 4);
+  const RedArgs<float> a = make_args<float>(m, u, (const float*)y2, z2, info, kMixedRefineSteps);
   cudaStream_t s2 = m.aux_stream;
   if (cudaEventRecord(m.ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(s2, m.ev_fork, 0) != cudaSuccess) {
     cudaGetLastError();

@@ -49,6 +49,10 @@ struct Exec {
   bool alone = true;             // no other solve shares the GPU
   std::vector<void*>* allocs = nullptr;
   size_t* bytes = nullptr;
+  // asked before the reduced-system buffers grow by `delta` bytes; nonzero
+  // refuses (the solve then returns FSIM_ENOMEM).  NULL: no budget.
+  int (*grow)(void* user, size_t delta) = nullptr;
+  void* grow_user = nullptr;
 };
 
 // Allocate the per-solve buffers of workspace m (a copy of a prefactored

@@ -130,7 +130,24 @@ int make_slot(fsim_server_s* sv, const MeshState& ms, int mesh_id, Slot& s) {
   return FSIM_OK;
 }
 
-int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J) {
+// A running slot's reduced-system buffers grow under the server's lock and
+// within the memory budget (admission.h); the growth is added to `used` at
+// once, so that other workers admit new slots against the current total.
+struct Growth {
+  fsim_server_s* sv = nullptr;
+  size_t grown = 0;
+};
+
+int grow_slot(void* user, size_t delta) {
+  auto* g = static_cast<Growth*>(user);
+  std::lock_guard<std::mutex> lk(g->sv->mu);
+  if (!admit_growth(g->sv->used, delta, g->sv->budget)) return -1;
+  g->sv->used += delta;
+  g->grown += delta;
+  return 0;
+}
+
+int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J, Growth* growth) {
   const MeshState& ms = *rt_mesh(sv->ctx, J.mesh_id);
   DevMesh& m = s.d;
   cudaStream_t st = w.stream;
@@ -143,6 +160,8 @@ int run_job(fsim_server_s* sv, Worker& w, Slot& s, Job& J) {
   ex.alone = sv->n_workers == 1;
   ex.allocs = &s.allocs;
   ex.bytes = &s.bytes;
+  ex.grow = grow_slot;
+  ex.grow_user = growth;
   // actuation A = a f f^T + a^-1/2 (I - f f^T) per tet; host arrays go
   // through the slot's pinned staging (fiber into tetf, stretch after it)
   const double* x0 = ms.d.rest;
@@ -234,10 +253,14 @@ void worker_main(fsim_server_s* sv, int wi) {
     for (auto& e : evicted) free_slot(*e);
     evicted.clear();
     int rc = FSIM_OK;
+    Growth growth;
+    growth.sv = sv;
     if (fresh) rc = make_slot(sv, *rt_mesh(sv->ctx, J->mesh_id), J->mesh_id, *s);
-    if (rc == FSIM_OK) rc = run_job(sv, w, *s, *J);
+    if (rc == FSIM_OK) rc = run_job(sv, w, *s, *J, &growth);
     lk.lock();
-    sv->used = sv->used + s->bytes - bytes0;
+    // bytes0 (and any growth) were counted while the job ran; now the
+    // slot's actual size replaces them
+    sv->used = sv->used - std::min(sv->used, bytes0 + growth.grown) + s->bytes;
     s->busy = false;
     s->last_used = ++sv->clock;
     sv->running--;

@@ -27,6 +27,11 @@ FSIM_EINTERSECTING = -9
 FSIM_ENOT_READY = -10
 FP64 = 0
 MIXED = 1
+REDUCED_UNUSED = -1
+REDUCED_COOPERATIVE = 0
+REDUCED_NONE = 1
+REDUCED_ONE_CTA = 2
+REDUCED_CLUSTER = 3
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOT_SPD",
                 -5: "ENOT_CONVERGED", -6: "ELS_FAIL", -7: "ECONTACT_OVERFLOW",
@@ -54,10 +59,14 @@ class FrameStats(C.Structure):
                 ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("kappa_doublings", C.c_int32),
                 ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
                 ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double),
-                ("cg_iterations", C.c_int64)]
+                ("cg_iterations", C.c_int64), ("reduced_steps", C.c_int32 * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if k == "reduced_steps" else v
+        return out
 
 
 class MeshInfo(C.Structure):
@@ -117,7 +126,7 @@ _SIGS = {
     "fsim_eval_proxy": [_P, C.c_int, _D, _D],
     "fsim_eval_contacts": [_P, C.c_int, _D, _I32, C.c_int64, _I64, _D],
     "fsim_eval_barrier": [_P, C.c_int, _D, _D, _I32, _I32, _D, C.c_int64],
-    "fsim_eval_global_step": [_P, C.c_int, _D, C.c_int, _D],
+    "fsim_eval_global_step": [_P, C.c_int, _D, C.c_int, _D, _I32],
     "fsim_eval_ccd": [_P, C.c_int, _D, _D, _D],
     "fsim_eval_energy": [_P, C.c_int, _D, C.c_int, _D, _D],
     "fsim_mesh_info_get": [_P, C.c_int, C.POINTER(MeshInfo)],
@@ -354,12 +363,13 @@ class Mesh:
         Bc = B[: 9 * k * k].reshape(3 * k, 3 * k) if want_bcheck else None
         return g, clist[:k].copy(), Bc
 
-    def eval_global_step(self, x, precision=FP64):
+    def eval_global_step(self, x, precision=FP64, want_path=False):
         xx = self._x(x)
         dx = np.empty((self.n, 3))
-        _chk(self.lib.fsim_eval_global_step(self.ctx.h, self.id, _d(xx), int(precision), _d(dx)),
-             "fsim_eval_global_step")
-        return dx
+        path = C.c_int32(-2)
+        _chk(self.lib.fsim_eval_global_step(self.ctx.h, self.id, _d(xx), int(precision), _d(dx),
+                                            C.byref(path)), "fsim_eval_global_step")
+        return (dx, path.value) if want_path else dx
 
     def eval_ccd(self, x, dx):
         xx, dd = self._x(x), self._x(dx)

@@ -32,6 +32,9 @@ extern "C" int admit_c(int nq, const int* qmesh, int ns, const int* smesh, const
   for (size_t i = 0; i < a.evict.size(); ++i) evict_out[i] = a.evict[i];
   return a.job;
 }
+extern "C" int growth_c(long long used, long long delta, long long budget) {
+  return fsim::admit_growth((size_t)used, (size_t)delta, budget) ? 1 : 0;
+}
 '''
 
 
@@ -63,6 +66,9 @@ def admit(tmp_path_factory):
         job = lib.admit_c(nq, q, ns, sm, sb, sy, sl, len(need), nd, L(used), L(budget), max_slots,
                           C.byref(slot), ev, C.byref(nev))
         return job, slot.value, [ev[i] for i in range(nev.value)]
+    call.growth = lambda used, delta, budget: bool(lib.growth_c(C.c_longlong(used),
+                                                                C.c_longlong(delta),
+                                                                C.c_longlong(budget)))
     return call
 
 
@@ -108,3 +114,11 @@ def test_slot_cap(admit):
     slots = [(0, True, 1, 1), (1, False, 1, 2)]
     job, slot, ev = admit([2], slots, [1, 1, 1], 2, 0, max_slots=2)
     assert (job, slot, ev) == (0, -1, [1])
+
+
+def test_running_slot_growth_respects_the_budget(admit):
+    # a running slot's reduced-system buffers may grow only while all slots
+    # together stay within the budget (the solve fails with ENOMEM otherwise)
+    assert admit.growth(90, 10, 100)
+    assert not admit.growth(90, 11, 100)
+    assert admit.growth(10 ** 12, 10 ** 12, 0)          # no budget

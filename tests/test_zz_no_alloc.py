@@ -2,11 +2,14 @@
 
 Callers that cannot let a library allocate GPU memory (an engine that owns
 all device memory through its own pool, a process held to a fixed memory
-budget, code recorded into the caller's CUDA graph) pass their own device
-buffers and get the same step bound as the solver's CCD stage; the entry
-point keeps its scratch in a fixed static device array.  This test checks it
-against the existing entry point fsim_eval_ccd on two calls in a row (the
-second call must not see the first call's candidates), through the C ABI.
+budget) pass their own device buffers and get the same step bound as the
+solver's CCD stage; the entry point keeps its scratch in a fixed static
+device array.  This test checks it against the existing entry point
+fsim_eval_ccd on two calls in a row (the second call must not see the first
+call's candidates), through the C ABI; then a call with more candidates than
+the static array holds (FSIM_ECONTACT_OVERFLOW) and a call with a triangle
+index out of range (FSIM_EINVAL), each followed by a normal call that must
+again match the existing entry point.
 This file is collected last so that a failure here leaves every other test run.
 """
 import ctypes as C
@@ -78,3 +81,35 @@ def test_noalloc_ccd_matches_existing_entry_point_twice():
         bad = ctx.lib.fsim_ccd_noalloc(None, None, 5, None, 0, None, 0, p.dhat, p.ccd_s,
                                        p.accd_max_iters, C.c_void_p(alpha_d.data_ptr()), None)
         assert bad == fsim.FSIM_EINVAL
+
+        def call(s_t, ds_t, tris_t, edges_t, dhat):
+            alpha_d.fill_(-7.0)
+            torch.cuda.synchronize()
+            return ctx.lib.fsim_ccd_noalloc(
+                C.c_void_p(s_t.data_ptr()), C.c_void_p(ds_t.data_ptr()), s_t.shape[0],
+                C.c_void_p(tris_t.data_ptr()), tris_t.shape[0],
+                C.c_void_p(edges_t.data_ptr()), edges_t.shape[0], dhat, p.ccd_s,
+                p.accd_max_iters, C.c_void_p(alpha_d.data_ptr()),
+                C.c_void_p(stream.cuda_stream))
+
+        ds_last = torch.tensor(m.eval_proxy(steps[-1]), dtype=torch.float64, device=dev)
+        ref_last = m.eval_ccd(x, steps[-1])
+        # more candidates than the static array holds: with dhat far larger than
+        # the mesh every non-adjacent pair is a candidate (16x16 faces: about
+        # 0.6M point-triangle and 1.3M edge-edge pairs > 2^20)
+        big = I.two_slabs(16, 16, 2, gap=0.004)
+        sb = big.rest[big.W_col]                      # selection proxy: s = W x
+        assert np.array_equal(np.diff(big.W_rowptr), np.ones(sb.shape[0], dtype=np.int64))
+        sb_d = torch.tensor(sb, dtype=torch.float64, device=dev).contiguous()
+        dsb_d = torch.full_like(sb_d, 1e-4)
+        trb_d = torch.tensor(big.proxy_tris.astype(np.int32), device=dev).contiguous()
+        edb_d = torch.tensor(_edges(big.proxy_tris), device=dev).contiguous()
+        assert call(sb_d, dsb_d, trb_d, edb_d, 100.0) == fsim.FSIM_ECONTACT_OVERFLOW
+        assert call(s_d, ds_last, tris_d, edges_d, p.dhat) == fsim.FSIM_OK
+        assert abs(float(alpha_d.item()) - ref_last) <= 1e-12 * ref_last
+        # a triangle naming a vertex outside [0, Ns) is reported, not read
+        tris_bad = tris_d.clone()
+        tris_bad[3, 1] = s.shape[0]
+        assert call(s_d, ds_last, tris_bad, edges_d, p.dhat) == fsim.FSIM_EINVAL
+        assert call(s_d, ds_last, tris_d, edges_d, p.dhat) == fsim.FSIM_OK
+        assert abs(float(alpha_d.item()) - ref_last) <= 1e-12 * ref_last
