@@ -168,6 +168,7 @@ int alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& al, siz
   TRY(dalloc(al, &m.g, 3 * n, bytes));
   TRY(dalloc(al, &m.act, 6 * T, bytes));
   TRY(dalloc(al, &m.act_df, 6 * T, bytes));
+  TRY(dalloc(al, &m.udf, 3 * n, bytes));
   TRY(dalloc(al, &m.tetf, 12 * T, bytes));
   TRY(dalloc(al, &m.tetf_t, 12 * T, bytes));
   TRY(dalloc(al, &m.s, 3 * Ns, bytes));
@@ -326,7 +327,7 @@ int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const 
                          const double* tetf, double* gout, int64_t npairs, int prec, int* nc_out,
                          double* gn2_out, double kappa) {
   cudaStream_t s = ex.stream;
-  launch_gather_forces(s, m, tetf, gout);
+  launch_gather_forces(s, m, tetf, gout, prec);
   CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
   launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, kappa, prec);
   if (m.n2 > 0) launch_mark_scan(s, m);
@@ -732,6 +733,14 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
     TRY(upload(ms, s, &m.dminv_df, dd.data(), dd.size()));
   }
   TRY(upload(ms, s, &m.w, w.data(), w.size()));
+  {   // w as float pairs for the mixed local step
+    std::vector<float2> wd(w.size());
+    for (size_t k = 0; k < w.size(); ++k) {
+      const float h = (float)w[k];
+      wd[k] = make_float2(h, (float)(w[k] - (double)h));
+    }
+    TRY(upload(ms, s, &m.w_df, wd.data(), wd.size()));
+  }
   TRY(upload(ms, s, &m.perm, f.perm.data(), f.perm.size()));
   TRY(upload(ms, s, &m.pos, f.pos.data(), f.pos.size()));
   std::vector<int> x2of(m.n, -1);
@@ -1008,7 +1017,7 @@ fsim_status fsim_eval_elastic(fsim_ctx_t ctx, int mesh_id, const double* x, int 
   if (proj_out && !ms->proj) TRY(dalloc(*ms, &ms->proj, 9 * (size_t)m.T));
   launch_elastic(s, m, m.xt, m.tetf_t, proj_out ? ms->proj : nullptr, m.partials, precision);
   launch_sum_partials(s, m.partials, elastic_blocks(m.T), m.scal + 2);
-  launch_gather_forces(s, m, m.tetf_t, ms->gtmp);
+  launch_gather_forces(s, m, m.tetf_t, ms->gtmp, precision);
   TRY(sync_read(ctx_exec(ctx, *ms), m));
   if (energy_out) *energy_out = ctx->h_scal[2];
   if (grad_out)

@@ -236,62 +236,84 @@ k_elastic(int T, const int4* __restrict__ tets, const double* __restrict__ dminv
   if (threadIdx.x == 0) partials[blockIdx.x] = bs;
 }
 
-// Mixed-precision local step in double-float arithmetic (df64.cuh): the
-// same quantities as k_elastic<1> (float32 rotation refined to float64
-// accuracy, then p, D, energy and forces) with the float64-accurate parts
-// carried as float pairs, which GB300 executes several times faster than
-// float64.  The refinement follows polar_refine with its small terms in
-// float32: R1 = R0 + R0 D with D = (I - R0^T R0) / 2 (about 1e-7), the
-// skew part of S = R1^T M kept in double-float, w = ((tr S) I - S)^-1 2 a
-// in float32, and R = R1 exp([w]) = R0 + C with C = R0 D + R0 (E - I) +
-// R0 D (E - I) (all about 1e-7, so float32 products suffice).  Inputs and
-// outputs stay float64; Dm^-1 and A come as float pairs.
+// Mixed-precision local step in double-float arithmetic (df64.cuh), with
+// no float64 instruction per tet: GB300 issues float64 (and float64
+// conversions) at about 1/64 of the float32 rate, so the float64 loads,
+// differences, conversions and products of a per-tet float64 interface cost
+// more than the whole float32 SVD.  The kernel reads the vertex
+// displacements u = x - X as float pairs (k_disp_df, once per vertex), Dm^-1,
+// A and w as float pairs, and works with the displacement gradient:
+//   F = Ds Dm^-1 = I + Du Dm^-1,  Du = [u1 - u0, u2 - u0, u3 - u0],
+// which keeps F - I (the strain) to double-float accuracy relative to itself.
+// Then M = F A, a float32 rotation R0 of M (Jacobi SVD) refined to float64
+// accuracy as in polar_refine but with the small terms in float32:
+// R1 = R0 + R0 D with D = (I - R0^T R0) / 2 (about 1e-7), the skew part of
+// S = R1^T M kept in double-float, w = ((tr S) I - S)^-1 2 a in float32, and
+// R = R1 exp([w]) = R0 + C with C = R0 D + R0 (E - I) + R0 D (E - I) (all
+// about 1e-7, so float32 products suffice); p = R A, D = F - p, the energy
+// 1/2 w |D|^2 and the forces w D gradN_a.  Forces are written as float
+// pairs (tetf reinterpreted, the same 8 bytes per entry as float64) and
+// summed per vertex by k_gather_forces_df; the energy is summed per block in
+// double-float and converted once per block.
+__global__ void k_disp_df(int n3, const double* __restrict__ x, const double* __restrict__ rest,
+                          float2* __restrict__ udf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const df u = df_from_double(__dsub_rn(x[i], rest[i]));
+  udf[i] = make_float2(u.hi, u.lo);
+}
+
+__device__ __forceinline__ df ld_df(const float2* __restrict__ p, size_t i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
+}
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(kElasticThreads)
 k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dminv_df,
-             const double* __restrict__ w, const float2* __restrict__ act_df,
-             const double* __restrict__ x, double* __restrict__ tetf,
+             const float2* __restrict__ w_df, const float2* __restrict__ act_df,
+             const float2* __restrict__ udf, float2* __restrict__ tetf,
              double* __restrict__ proj, double* __restrict__ partials) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
+  df e = {0.f, 0.f};
   if (t < T) {
     const int4 tv = tets[t];
-    const double* x0 = x + 3 * (size_t)tv.x;
-    const double* x1 = x + 3 * (size_t)tv.y;
-    const double* x2 = x + 3 * (size_t)tv.z;
-    const double* x3 = x + 3 * (size_t)tv.w;
-    df Ds[3][3];
+    df u0[3], Du[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u0[d] = ld_df(udf, 3 * (size_t)tv.x + d);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double o = x0[d];
-      Ds[d][0] = df_from_double(x1[d] - o);
-      Ds[d][1] = df_from_double(x2[d] - o);
-      Ds[d][2] = df_from_double(x3[d] - o);
+      Du[d][0] = df_sub(ld_df(udf, 3 * (size_t)tv.y + d), u0[d]);
+      Du[d][1] = df_sub(ld_df(udf, 3 * (size_t)tv.z + d), u0[d]);
+      Du[d][2] = df_sub(ld_df(udf, 3 * (size_t)tv.w + d), u0[d]);
     }
     df Di[3][3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const float2 v = dminv_df[(size_t)k * T + t];
-      Di[k / 3][k % 3] = {v.x, v.y};
-    }
+    for (int k = 0; k < 9; ++k) Di[k / 3][k % 3] = ld_df(dminv_df, (size_t)k * T + t);
     df A[3][3];
-    {
-      const float2 a00 = act_df[0 * (size_t)T + t], a01 = act_df[1 * (size_t)T + t],
-                   a02 = act_df[2 * (size_t)T + t], a11 = act_df[3 * (size_t)T + t],
-                   a12 = act_df[4 * (size_t)T + t], a22 = act_df[5 * (size_t)T + t];
-      A[0][0] = {a00.x, a00.y};
-      A[0][1] = A[1][0] = {a01.x, a01.y};
-      A[0][2] = A[2][0] = {a02.x, a02.y};
-      A[1][1] = {a11.x, a11.y};
-      A[1][2] = A[2][1] = {a12.x, a12.y};
-      A[2][2] = {a22.x, a22.y};
-    }
+    A[0][0] = ld_df(act_df, 0 * (size_t)T + t);
+    A[0][1] = A[1][0] = ld_df(act_df, 1 * (size_t)T + t);
+    A[0][2] = A[2][0] = ld_df(act_df, 2 * (size_t)T + t);
+    A[1][1] = ld_df(act_df, 3 * (size_t)T + t);
+    A[1][2] = A[2][1] = ld_df(act_df, 4 * (size_t)T + t);
+    A[2][2] = ld_df(act_df, 5 * (size_t)T + t);
     df F[3][3], M[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        F[i][j] = df_add(df_add(df_mul(Ds[i][0], Di[0][j]), df_mul(Ds[i][1], Di[1][j])),
-                         df_mul(Ds[i][2], Di[2][j]));
+      for (int j = 0; j < 3; ++j) {
+        F[i][j] = df_add(df_add(df_mul(Du[i][0], Di[0][j]), df_mul(Du[i][1], Di[1][j])),
+                         df_mul(Du[i][2], Di[2][j]));
+        if (i == j) F[i][j] = df_add(F[i][j], df_from_float(1.f));
+      }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -381,7 +403,7 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
       for (int j = 0; j < 3; ++j)
         P[i][j] = df_add(df_add(df_mul(R[i][0], A[0][j]), df_mul(R[i][1], A[1][j])),
                          df_mul(R[i][2], A[2][j]));
-    const double wt = w[t];
+    const df wt = ld_df(w_df, t);
     df Dd[3][3];
     df ssum = {0.f, 0.f};
 #pragma unroll
@@ -391,28 +413,61 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
         Dd[i][j] = df_sub(F[i][j], P[i][j]);
         ssum = df_add(ssum, df_mul(Dd[i][j], Dd[i][j]));
       }
-    e = 0.5 * wt * df_to_double(ssum);
+    e = df_mul(wt, ssum);
+    e.hi *= 0.5f;
+    e.lo *= 0.5f;
     // f_a = w D gradN_a, gradN_a = row a-1 of Dm^-1 (a = 1..3), f_0 = -sum
-    double f0[3] = {0.0, 0.0, 0.0};
+    df f0[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
     for (int a = 1; a < 4; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const df q = df_add(df_add(df_mul(Dd[d][0], Di[a - 1][0]), df_mul(Dd[d][1], Di[a - 1][1])),
                             df_mul(Dd[d][2], Di[a - 1][2]));
-        const double fa = wt * df_to_double(q);
-        tetf[(size_t)(a * 3 + d) * T + t] = fa;
-        f0[d] -= fa;
+        const df fa = df_mul(wt, q);
+        tetf[(size_t)(a * 3 + d) * T + t] = make_float2(fa.hi, fa.lo);
+        f0[d] = df_sub(f0[d], fa);
       }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) tetf[(size_t)d * T + t] = f0[d];
+    for (int d = 0; d < 3; ++d) tetf[(size_t)d * T + t] = make_float2(f0[d].hi, f0[d].lo);
     if (proj != nullptr) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) proj[(size_t)9 * t + k] = df_to_double(P[k / 3][k % 3]);
     }
   }
-  const double bs = block_sum(e);
-  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  // energy: double-float block sum, one float64 conversion per block
+  __shared__ df red[kElasticThreads / 32];
+  e = warp_sum_df(e);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = e;
+  __syncthreads();
+  if (wid == 0) {
+    df v = lane < kElasticThreads / 32 ? red[lane] : df{0.f, 0.f};
+    v = warp_sum_df(v);
+    if (lane == 0) partials[blockIdx.x] = df_to_double(v);
+  }
+}
+
+// Per-vertex sum of the double-float per-tet forces (fixed order), one
+// float64 conversion per coordinate.
+__global__ void k_gather_forces_df(int n, int T, const int* __restrict__ vptr,
+                                   const int* __restrict__ vslot, const float2* __restrict__ tetf,
+                                   const uint8_t* __restrict__ pinned, double* __restrict__ g) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
+  if (!pinned[v]) {
+    for (int e = vptr[v]; e < vptr[v + 1]; ++e) {
+      const int slot = vslot[e];
+      const int t = slot >> 2, a = slot & 3;
+      s0 = df_add(s0, ld_df(tetf, (size_t)(a * 3 + 0) * T + t));
+      s1 = df_add(s1, ld_df(tetf, (size_t)(a * 3 + 1) * T + t));
+      s2 = df_add(s2, ld_df(tetf, (size_t)(a * 3 + 2) * T + t));
+    }
+  }
+  g[3 * (size_t)v + 0] = df_to_double(s0);
+  g[3 * (size_t)v + 1] = df_to_double(s1);
+  g[3 * (size_t)v + 2] = df_to_double(s2);
 }
 
 __global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
@@ -486,23 +541,37 @@ void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* 
 
 int elastic_blocks(int T) { return (T + kElasticThreads - 1) / kElasticThreads; }
 
+bool elastic_uses_df(const DevMesh& m, int precision) {
+  return precision != 0 && m.dminv_df && m.act_df && m.w_df && m.udf;
+}
+
 void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* tetf,
                     double* proj, double* partials, int precision) {
   const int nb = elastic_blocks(m.T);
   ProfScope ps(PROF_ELASTIC, s);
-  if (precision == 0)
+  if (precision == 0) {
     k_elastic<0><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
-  else if (m.dminv_df && m.act_df)
-    k_elastic_df<<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv_df, m.w, m.act_df, x, tetf, proj,
-                                               partials);
-  else
+    count_launch();
+  } else if (elastic_uses_df(m, precision)) {
+    k_disp_df<<<(3 * m.n + 255) / 256, 256, 0, s>>>(3 * m.n, x, m.rest, m.udf);
+    k_elastic_df<<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv_df, m.w_df, m.act_df, m.udf,
+                                               reinterpret_cast<float2*>(tetf), proj, partials);
+    count_launch(2);
+  } else {
     k_elastic<1><<<nb, kElasticThreads, 0, s>>>(m.T, m.tets, m.dminv, m.w, m.act, x, tetf, proj, partials);
-  count_launch();
+    count_launch();
+  }
 }
 
-void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g) {
-  k_gather_forces<<<(m.n + 255) / 256, 256, 0, s>>>(m.n, m.T, m.vinc_ptr, m.vinc_slot, tetf,
-                                                    m.pinned, g);
+void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g,
+                          int precision) {
+  if (elastic_uses_df(m, precision))
+    k_gather_forces_df<<<(m.n + 255) / 256, 256, 0, s>>>(m.n, m.T, m.vinc_ptr, m.vinc_slot,
+                                                         reinterpret_cast<const float2*>(tetf),
+                                                         m.pinned, g);
+  else
+    k_gather_forces<<<(m.n + 255) / 256, 256, 0, s>>>(m.n, m.T, m.vinc_ptr, m.vinc_slot, tetf,
+                                                      m.pinned, g);
   count_launch();
 }
 

@@ -23,7 +23,10 @@ struct DevMesh {
   double* act = nullptr;      // 6T SoA: A00 A01 A02 A11 A12 A22
   float2* act_df = nullptr;   // 6T SoA: the same as float pairs (hi, lo)
   float2* dminv_df = nullptr; // 9T SoA: Dm^-1 as float pairs
-  double* tetf = nullptr;     // 12T SoA per-tet vertex forces ((a*3+d)*T + t)
+  float2* w_df = nullptr;     // T: w as float pairs
+  float2* udf = nullptr;      // 3n: displacement x - rest as float pairs (mixed local step)
+  double* tetf = nullptr;     // 12T SoA per-tet vertex forces ((a*3+d)*T + t); float64, or
+                              // float pairs in the same bytes after a mixed local step
   double* tetf_t = nullptr;   // same at the trial point
   int* vinc_ptr = nullptr;    // vertex -> incident (t*4 + a) slots
   int* vinc_slot = nullptr;
@@ -145,11 +148,13 @@ struct DevMesh {
 void launch_actuation(cudaStream_t s, int T, const double* fiber, const double* stretch, double* act,
                       float2* act_df);
 // precision 0: float64 SVD; 1: float32 SVD refined to float64 accuracy in
-// double-float arithmetic (k_elastic_df).
+// double-float arithmetic (k_elastic_df; tetf then holds float pairs).
 void launch_elastic(cudaStream_t s, const DevMesh& m, const double* x, double* tetf,
                     double* proj, double* partials, int precision);
 int elastic_blocks(int T);
-void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g);
+// g = per-vertex sums of tetf, written by launch_elastic with the same precision
+void launch_gather_forces(cudaStream_t s, const DevMesh& m, const double* tetf, double* g,
+                          int precision);
 void launch_sum_partials(cudaStream_t s, const double* partials, int n, double* out);
 
 // ---- contact (k_contact.cu) -----------------------------------------------

@@ -103,31 +103,41 @@ __device__ void polar_rotation(const T M[3][3], T R[3][3]) {
   int kmin = 0;
   if (sig[1] < sig[kmin]) kmin = 1;
   if (sig[2] < sig[kmin]) kmin = 2;
-  const int ka = kmin == 0 ? 1 : 0, kb = kmin == 2 ? 1 : 2;
-  T U[3][3];
+  // columns ka < kb are the two others; selects instead of indexing with
+  // kmin keep every array in registers
+  const T sa = kmin == 0 ? sig[1] : sig[0];
+  const T sb = kmin == 2 ? sig[1] : sig[2];
+  T a[3], b[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    U[i][ka] = sig[ka] > tiny ? B[i][ka] / sig[ka] : T(0);
-    U[i][kb] = sig[kb] > tiny ? B[i][kb] / sig[kb] : T(0);
+    const T ba = kmin == 0 ? B[i][1] : B[i][0];
+    const T bb = kmin == 2 ? B[i][1] : B[i][2];
+    a[i] = sa > tiny ? ba / sa : T(0);
+    b[i] = sb > tiny ? bb / sb : T(0);
   }
-  if (!(sig[ka] > tiny)) { U[0][ka] = 1; U[1][ka] = 0; U[2][ka] = 0; }
-  if (!(sig[kb] > tiny)) {  // any unit vector orthogonal to U[:,ka]
-    T ux = U[0][ka], uy = U[1][ka], uz = U[2][ka];
-    T px = fabs(ux) < T(0.9) ? T(1) : T(0), py = fabs(ux) < T(0.9) ? T(0) : T(1), pz = T(0);
-    T cx = uy * pz - uz * py, cy = uz * px - ux * pz, cz = ux * py - uy * px;
+  if (!(sa > tiny)) { a[0] = 1; a[1] = 0; a[2] = 0; }
+  if (!(sb > tiny)) {  // any unit vector orthogonal to a
+    T px = fabs(a[0]) < T(0.9) ? T(1) : T(0), py = fabs(a[0]) < T(0.9) ? T(0) : T(1), pz = T(0);
+    T cx = a[1] * pz - a[2] * py, cy = a[2] * px - a[0] * pz, cz = a[0] * py - a[1] * px;
     T nn = sqrt_t(cx * cx + cy * cy + cz * cz);
-    U[0][kb] = cx / nn; U[1][kb] = cy / nn; U[2][kb] = cz / nn;
+    b[0] = cx / nn; b[1] = cy / nn; b[2] = cz / nn;
   }
   // the third column completes a right-handed frame in the orientation of
   // (ka, kb, kmin) inside V's frame: u_kmin = s * (u_ka x u_kb), where s is
   // the sign that makes det U = +1 for the cyclic order of the indices
-  T cx = U[1][ka] * U[2][kb] - U[2][ka] * U[1][kb];
-  T cy = U[2][ka] * U[0][kb] - U[0][ka] * U[2][kb];
-  T cz = U[0][ka] * U[1][kb] - U[1][ka] * U[0][kb];
-  const T orient = ((ka + 1) % 3 == kb) ? T(1) : T(-1);
-  U[0][kmin] = orient * cx;
-  U[1][kmin] = orient * cy;
-  U[2][kmin] = orient * cz;
+  // (s = -1 only for (ka, kb, kmin) = (0, 2, 1))
+  const T orient = kmin == 1 ? T(-1) : T(1);
+  T c[3];
+  c[0] = orient * (a[1] * b[2] - a[2] * b[1]);
+  c[1] = orient * (a[2] * b[0] - a[0] * b[2]);
+  c[2] = orient * (a[0] * b[1] - a[1] * b[0]);
+  T U[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    U[i][0] = kmin == 0 ? c[i] : a[i];
+    U[i][1] = kmin == 1 ? c[i] : (kmin == 0 ? a[i] : b[i]);
+    U[i][2] = kmin == 2 ? c[i] : b[i];
+  }
   // R = U V^T (V is a product of plane rotations, det V = +1)
   matmul_nt(U, V, R);
 }
