@@ -434,6 +434,30 @@ fsim_status fsim_server_destroy(fsim_server_t srv);
 fsim_status fsim_solve_frames(fsim_ctx_t ctx, int32_t n_req, const fsim_request* reqs,
                               int32_t workers, double* const* x_out, fsim_frame_stats* stats);
 
+/*
+ * Lock-step batched form: solve n_req frames of ONE mesh (all requests must
+ * name the same prefactored mesh, FSIM_MIXED precision, and the mesh must use
+ * FSIM_SOLVER_WOODBURY) with up to max_frames (1..64) of them advancing
+ * together through Algorithm 1.  Every stage of an iteration is one launch
+ * for all frames in the batch: the local step, constraint set, barrier
+ * derivatives, CCD and line-search trials over a table of per-frame
+ * workspaces; the triangular solves of Eq. 8 as one pass over the factor for
+ * the right-hand sides of all frames; the reduced systems of Eq. 11 side by
+ * side.  A frame that converges leaves the batch after its iteration and the
+ * next request takes its place.  Each frame's result is that of the same
+ * request solved alone (fsim_solve_frame) up to the order of floating-point
+ * atomics.  Requests are fsim_request as for the server (host or
+ * FSIM_REQ_DEVICE inputs; x_out_dev, when set, receives the positions);
+ * x_out[i] (host, 3n, may be NULL) and stats[i] (may be NULL) receive the
+ * results.  Runs on the context's stream; returns after all requests have
+ * finished, with the first non-OK status (each stats[i].status has its own).
+ * Errors: FSIM_EINVAL (mixed meshes or precisions, another solver,
+ * max_frames outside 1..64, or a mesh whose largest supernode does not fit
+ * the batched solves), FSIM_ENOT_READY, FSIM_ENOMEM.
+ */
+fsim_status fsim_solve_batch(fsim_ctx_t ctx, int32_t n_req, const fsim_request* reqs,
+                             int32_t max_frames, double* const* x_out, fsim_frame_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -497,6 +497,7 @@ namespace fsim {
 int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allocs, size_t* bytes) {
   return alloc_workspace(ms, m, allocs, bytes);
 }
+int rt_ensure_reduced(const Exec& ex, DevMesh& m, int nc) { return ensure_reduced(ex, m, nc); }
 int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                    bool init_is_dev, int precision, fsim_frame_stats* stats) {
   return solve_frame_impl(ex, ms, m, x_init, init_is_dev, precision, stats);

@@ -7,6 +7,7 @@
 // overlap test keeps every pair the exact float64 test keeps.  The float64
 // test (boxes inflated by dhat, closed intervals) then decides CCD candidates
 // exactly as the oracle does, and the float64 distance decides d < dhat.
+#include <algorithm>
 #include <mutex>
 
 #include "contact.cuh"
@@ -26,7 +27,7 @@ __device__ __forceinline__ void unpack_key(unsigned long long k, int& type, int&
   j = (int)(k & 0x7fffffffULL);
 }
 
-__global__ void k_proxy(int Ns, const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
+__device__ __forceinline__ void k_proxy_body(int Ns, const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
                         const double* __restrict__ Wval, const double* __restrict__ x,
                         double* __restrict__ s) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,6 +39,11 @@ __global__ void k_proxy(int Ns, const int64_t* __restrict__ Wptr, const int* __r
     a += wv * xv[0]; b += wv * xv[1]; c += wv * xv[2];
   }
   s[3 * (size_t)r] = a; s[3 * (size_t)r + 1] = b; s[3 * (size_t)r + 2] = c;
+}
+__global__ void k_proxy(int Ns, const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
+                        const double* __restrict__ Wval, const double* __restrict__ x,
+                        double* __restrict__ s) {
+  k_proxy_body(Ns, Wptr, Wcol, Wval, x, s);
 }
 
 // float64 box of a primitive (1 vertex, a triangle or an edge) over s and,
@@ -220,8 +226,7 @@ k_cand_ee(int Ns, int Ne, const double* __restrict__ s, const double* __restrict
 constexpr int kPairWarps = 1;
 
 template <typename ET>
-__global__ void __launch_bounds__(32 * kPairWarps)
-k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+__device__ __forceinline__ void k_barrier_pairs_body(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
                 const double* __restrict__ s, const int* __restrict__ tris,
                 const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
                 const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
@@ -335,6 +340,15 @@ k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long 
     __syncwarp();
   }
 }
+template <typename ET>
+__global__ void __launch_bounds__(32 * kPairWarps) k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+                const double* __restrict__ s, const int* __restrict__ tris,
+                const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
+                const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
+                double kappa, double* __restrict__ pgrad, double* __restrict__ phess,
+                int* __restrict__ x2mark) {
+  k_barrier_pairs_body<ET>(count, cap, pairs, s, tris, edges, Wptr, Wcol, x2of, dhat, kappa, pgrad, phess, x2mark);
+}
 
 // Edge-edge mollifier (optional): for EE pairs with c = |e_a x e_b|^2 below
 // eps = 1e-3 |E_a|^2 |E_b|^2 the pair term is kappa m(c) b(d); this pass
@@ -344,7 +358,7 @@ k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long 
 // (H_b, G: kappa b's Hessian and gradient, lifted from the reduced basis) is
 // projected onto the PSD cone by a cyclic Jacobi eigen-solve in float64 (one
 // warp per pair, lane-parallel rotations), whatever the precision.
-__global__ void __launch_bounds__(32) k_mollify_ee(const int* __restrict__ count, int64_t cap,
+__device__ __forceinline__ void k_mollify_ee_body(const int* __restrict__ count, int64_t cap,
                                                    const unsigned long long* __restrict__ pairs,
                                                    const double* __restrict__ s,
                                                    const int* __restrict__ edges,
@@ -451,9 +465,18 @@ __global__ void __launch_bounds__(32) k_mollify_ee(const int* __restrict__ count
     __syncwarp();
   }
 }
+__global__ void __launch_bounds__(32) k_mollify_ee(const int* __restrict__ count, int64_t cap,
+                                                   const unsigned long long* __restrict__ pairs,
+                                                   const double* __restrict__ s,
+                                                   const int* __restrict__ edges,
+                                                   const double* __restrict__ elen2, double dhat,
+                                                   double kappa, double* __restrict__ pgrad,
+                                                   double* __restrict__ phess) {
+  k_mollify_ee_body(count, cap, pairs, s, edges, elen2, dhat, kappa, pgrad, phess);
+}
 
 // x2mark (0/1 flags) -> x2mark[q] = c position + 1 (0 if untouched); clist; nc.
-__global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ clist,
+__device__ __forceinline__ void k_mark_scan_body(int n2, int* __restrict__ x2mark, int* __restrict__ clist,
                             int* __restrict__ counters) {
   __shared__ int warp_tot[32];
   __shared__ int carry;
@@ -492,6 +515,10 @@ __global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ 
   }
   if (threadIdx.x == 0) counters[3] = carry;
 }
+__global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ clist,
+                            int* __restrict__ counters) {
+  k_mark_scan_body(n2, x2mark, clist, counters);
+}
 
 // Pass C: scatter gradients (through W) into g and blocks into B-check.
 // One thread per (pair, a, b): the pair's 12 x 12 block (a, b) mapped through
@@ -499,7 +526,7 @@ __global__ void k_mark_scan(int n2, int* __restrict__ x2mark, int* __restrict__ 
 // gradient into g.  n_c is read on the device; B-check is written only when
 // it fits the reduced buffers (n_c <= nc_cap), else the host grows them and
 // scatters the Hessian blocks again.  mode: 1 gradient, 2 B-check, 3 both.
-__global__ void k_barrier_scatter(int64_t np, const unsigned long long* __restrict__ pairs,
+__device__ __forceinline__ void k_barrier_scatter_body(int64_t np, const unsigned long long* __restrict__ pairs,
                                   const int* __restrict__ tris, const int* __restrict__ edges,
                                   const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
                                   const double* __restrict__ Wval, const int* __restrict__ x2of,
@@ -544,10 +571,20 @@ __global__ void k_barrier_scatter(int64_t np, const unsigned long long* __restri
     }
   }
 }
+__global__ void k_barrier_scatter(int64_t np, const unsigned long long* __restrict__ pairs,
+                                  const int* __restrict__ tris, const int* __restrict__ edges,
+                                  const int64_t* __restrict__ Wptr, const int* __restrict__ Wcol,
+                                  const double* __restrict__ Wval, const int* __restrict__ x2of,
+                                  const int* __restrict__ x2mark, const double* __restrict__ pgrad,
+                                  const double* __restrict__ phess, const int* __restrict__ ncp,
+                                  int nc_cap, int mode, double* __restrict__ g,
+                                  double* __restrict__ Bc, int* __restrict__ bocc) {
+  k_barrier_scatter_body(np, pairs, tris, edges, Wptr, Wcol, Wval, x2of, x2mark, pgrad, phess, ncp, nc_cap, mode, g, Bc, bocc);
+}
 
 // Zero the first (3 n_c)^2 entries of B-check and n_c^2 of its block
 // occupancy, n_c read on the device (nothing when n_c > nc_cap).
-__global__ void k_zero_reduced(const int* __restrict__ ncp, int nc_cap, double* __restrict__ Bc,
+__device__ __forceinline__ void k_zero_reduced_body(const int* __restrict__ ncp, int nc_cap, double* __restrict__ Bc,
                                int* __restrict__ bocc) {
   const int nc = *ncp;
   if (nc <= 0 || nc > nc_cap) return;
@@ -555,6 +592,10 @@ __global__ void k_zero_reduced(const int* __restrict__ ncp, int nc_cap, double* 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb; e += stride) Bc[e] = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < no; e += stride) bocc[e] = 0;
+}
+__global__ void k_zero_reduced(const int* __restrict__ ncp, int nc_cap, double* __restrict__ Bc,
+                               int* __restrict__ bocc) {
+  k_zero_reduced_body(ncp, nc_cap, Bc, bocc);
 }
 
 // Additive CCD (Li, Kaufman & Jiang 2021) time of impact of one candidate.
@@ -612,7 +653,7 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
 }
 
-__global__ void k_prim_prep(int Ns, int Nt, int Ne, const double* __restrict__ s,
+__device__ __forceinline__ void k_prim_prep_body(int Ns, int Nt, int Ne, const double* __restrict__ s,
                             const double* __restrict__ ds, const int* __restrict__ tris,
                             const int* __restrict__ edges, double pad, float* __restrict__ box,
                             unsigned long long* __restrict__ key, float* __restrict__ sf,
@@ -657,6 +698,13 @@ __global__ void k_prim_prep(int Ns, int Nt, int Ne, const double* __restrict__ s
     }
   }
 }
+__global__ void k_prim_prep(int Ns, int Nt, int Ne, const double* __restrict__ s,
+                            const double* __restrict__ ds, const int* __restrict__ tris,
+                            const int* __restrict__ edges, double pad, float* __restrict__ box,
+                            unsigned long long* __restrict__ key, float* __restrict__ sf,
+                            float* __restrict__ dsf) {
+  k_prim_prep_body(Ns, Nt, Ne, s, ds, tris, edges, pad, box, key, sf, dsf);
+}
 
 struct Box6 {
   float v[6];   // lo[3], hi[3]
@@ -697,7 +745,7 @@ struct SweepArgs {
 // candidates, whose swept boxes (+dhat) overlap by the exact float64 test.
 // (The skin list is built with MODE 0 and a wider `near`.)
 template <int MODE>
-__global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
+__device__ __forceinline__ void k_sweep_pt_body(SweepArgs a) {
   if (a.gate && *a.gate == 0) return;
   __shared__ float tb[kTile][6];
   __shared__ int tid3[kTile][3];
@@ -743,9 +791,13 @@ __global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
     }
   }
 }
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_pt(SweepArgs a) {
+  k_sweep_pt_body<MODE>(a);
+}
 
 template <int MODE>
-__global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
+__device__ __forceinline__ void k_sweep_ee_body(SweepArgs a) {
   if (blockIdx.y < blockIdx.x) return;        // tiles with j-tile >= i-tile
   if (a.gate && *a.gate == 0) return;
   __shared__ float eb[kTile][6];
@@ -796,10 +848,14 @@ __global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
     }
   }
 }
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_ee(SweepArgs a) {
+  k_sweep_ee_body<MODE>(a);
+}
 
 // float64 narrow phase of the near pairs (one pair per thread, fixed grid,
 // length read on the device): d < dhat joins C and adds kappa b(d).
-__global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, int64_t cap_act,
+__device__ __forceinline__ void k_near_pairs_body(const int* __restrict__ near_count, int64_t cap, int64_t cap_act,
                              const unsigned long long* __restrict__ nearl,
                              const double* __restrict__ s, const int* __restrict__ tris,
                              const int* __restrict__ edges, double dhat, double kappa,
@@ -834,11 +890,20 @@ __global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, in
   }
   if (esum != 0.0) atomicAdd(scal + 0, kappa * esum);
 }
+__global__ void k_near_pairs(const int* __restrict__ near_count, int64_t cap, int64_t cap_act,
+                             const unsigned long long* __restrict__ nearl,
+                             const double* __restrict__ s, const int* __restrict__ tris,
+                             const int* __restrict__ edges, double dhat, double kappa,
+                             const double* __restrict__ elen2,
+                             unsigned long long* __restrict__ pairs, int* counters,
+                             double* __restrict__ scal) {
+  k_near_pairs_body(near_count, cap, cap_act, nearl, s, tris, edges, dhat, kappa, elen2, pairs, counters, scal);
+}
 
 // ACCD over the candidate list (length read on the device); a float32
 // early-out first: when (1 - s) d0 exceeds l_p by a clear margin the first
 // advance passes t = 1 and the float64 march would return "no impact" too.
-__global__ void k_accd_list(const int* __restrict__ cand_count, int64_t cap,
+__device__ __forceinline__ void k_accd_list_body(const int* __restrict__ cand_count, int64_t cap,
                             const unsigned long long* __restrict__ cand,
                             const double* __restrict__ s, const double* __restrict__ ds,
                             const float* __restrict__ sf, const float* __restrict__ dsf,
@@ -877,6 +942,14 @@ __global__ void k_accd_list(const int* __restrict__ cand_count, int64_t cap,
       atomicMin(reinterpret_cast<unsigned long long*>(alpha), (unsigned long long)__double_as_longlong(toi));
   }
 }
+__global__ void k_accd_list(const int* __restrict__ cand_count, int64_t cap,
+                            const unsigned long long* __restrict__ cand,
+                            const double* __restrict__ s, const double* __restrict__ ds,
+                            const float* __restrict__ sf, const float* __restrict__ dsf,
+                            const int* __restrict__ tris, const int* __restrict__ edges,
+                            double s_ratio, int max_iters, float slack, double* __restrict__ alpha) {
+  k_accd_list_body(cand_count, cap, cand, s, ds, sf, dsf, tris, edges, s_ratio, max_iters, slack, alpha);
+}
 
 // ---------------------------------------------------------------------------
 // Skin (Verlet) list.  The all-pairs sweep runs only when proxy vertices
@@ -904,7 +977,7 @@ __device__ __forceinline__ double block_max_d(double v) {
 
 // one CTA: decide whether the skin list must be rebuilt (detection) or the
 // CCD step needs the full sweep (ds != nullptr); a rebuild records sb = s
-__global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __restrict__ sb,
+__device__ __forceinline__ void k_skin_check_body(int Ns, const double* __restrict__ s, double* __restrict__ sb,
                              const double* __restrict__ ds, double skin, double margin,
                              int* counters, double* scal) {
   if (ds == nullptr && threadIdx.x == 0) scal[4] = __longlong_as_double(0x7ff0000000000000LL);  // d_min = inf
@@ -941,9 +1014,14 @@ __global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __res
   if (rebuild)
     for (int e = threadIdx.x; e < 3 * Ns; e += blockDim.x) sb[e] = s[e];
 }
+__global__ void k_skin_check(int Ns, const double* __restrict__ s, double* __restrict__ sb,
+                             const double* __restrict__ ds, double skin, double margin,
+                             int* counters, double* scal) {
+  k_skin_check_body(Ns, s, sb, ds, skin, margin, counters, scal);
+}
 
 // near list from the skin list: float32 distance at the current positions
-__global__ void k_skin_near(const int* __restrict__ counters, int64_t cap,
+__device__ __forceinline__ void k_skin_near_body(const int* __restrict__ counters, int64_t cap,
                             const unsigned long long* __restrict__ vlist, const float* __restrict__ sf,
                             const int* __restrict__ tris, const int* __restrict__ edges, float near,
                             unsigned long long* __restrict__ nearl, int* count, int* overflow) {
@@ -961,10 +1039,16 @@ __global__ void k_skin_near(const int* __restrict__ counters, int64_t cap,
     if (pair_distance_f(type, X) <= near) append(vlist[p], nearl, count, overflow, cap);
   }
 }
+__global__ void k_skin_near(const int* __restrict__ counters, int64_t cap,
+                            const unsigned long long* __restrict__ vlist, const float* __restrict__ sf,
+                            const int* __restrict__ tris, const int* __restrict__ edges, float near,
+                            unsigned long long* __restrict__ nearl, int* count, int* overflow) {
+  k_skin_near_body(counters, cap, vlist, sf, tris, edges, near, nearl, count, overflow);
+}
 
 // CCD candidates from the skin list (when counters[13] == 0): the exact
 // float64 swept-box test of the full sweep
-__global__ void k_skin_cand(int* counters, int64_t cap, const unsigned long long* __restrict__ vlist,
+__device__ __forceinline__ void k_skin_cand_body(int* counters, int64_t cap, const unsigned long long* __restrict__ vlist,
                             const unsigned long long* __restrict__ key, int Ns, int Nt,
                             unsigned long long* __restrict__ cand) {
   if (counters[13] != 0) return;
@@ -978,6 +1062,11 @@ __global__ void k_skin_cand(int* counters, int64_t cap, const unsigned long long
     const unsigned long long* kb = key + 12 * (size_t)(type == 0 ? Ns + j : Ns + Nt + j) + 6;
     if (ov64(ka, kb)) append(vlist[p], cand, counters + 1, counters + 9, cap);
   }
+}
+__global__ void k_skin_cand(int* counters, int64_t cap, const unsigned long long* __restrict__ vlist,
+                            const unsigned long long* __restrict__ key, int Ns, int Nt,
+                            unsigned long long* __restrict__ cand) {
+  k_skin_cand_body(counters, cap, vlist, key, Ns, Nt, cand);
 }
 
 // ---------------------------------------------------------------------------
@@ -1085,10 +1174,13 @@ void launch_mark_scan(cudaStream_t st, const DevMesh& m) {
   count_launch();
 }
 
-__global__ void k_ccd_reset(int* counters, double* scal) {
+__device__ __forceinline__ void k_ccd_reset_body(int* counters, double* scal) {
   counters[1] = 0;
   counters[9] = 0;
   scal[1] = 1.0;
+}
+__global__ void k_ccd_reset(int* counters, double* scal) {
+  k_ccd_reset_body(counters, scal);
 }
 
 void launch_ccd_reset(cudaStream_t st, const DevMesh& m) {
@@ -1110,6 +1202,263 @@ void launch_barrier_scatter(cudaStream_t st, const DevMesh& m, int64_t np, int n
 void launch_zero_reduced(cudaStream_t st, const DevMesh& m, int nc_cap) {
   if (nc_cap <= 0 || m.Bc == nullptr) return;
   k_zero_reduced<<<2 * 152, 256, 0, st>>>(m.counters + 3, nc_cap, m.Bc, m.bocc);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Lock-step batches: one launch serves every frame of a batch table (one
+// DevMesh per frame, all of one mesh).  The frame is blockIdx.y (blockIdx.z
+// for the 2-D tile sweeps); a frame whose `active` flag is clear returns at
+// once, uniformly for its blocks.  AT selects the evaluation point: 0 the
+// iterate (x, s), 1 the line-search trial (xt, st).  Per-frame scalars
+// (kappa of the frame) come from the table, mesh-wide ones are arguments.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ const DevMesh* bframe_c(const DevMesh* __restrict__ tab, int f) {
+  const DevMesh* m = tab + f;
+  return m->active ? m : nullptr;
+}
+}  // namespace
+
+// counters [0] |C|, [1] candidates, [2] overflow, [5] touching, [8] near
+// list and scal[0] (barrier energy) of every active frame to zero
+__global__ void k_eval_reset_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m || threadIdx.x != 0) return;
+  m->counters[0] = 0; m->counters[1] = 0; m->counters[2] = 0;
+  m->counters[5] = 0; m->counters[8] = 0;
+  m->scal[0] = 0.0;
+}
+
+// AT 0: s = W x, 1: st = W xt, 2: ds = W dx
+template <int AT>
+__global__ void k_proxy_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  const double* x = AT == 0 ? m->x : (AT == 1 ? m->xt : m->dx);
+  double* sp = AT == 0 ? m->s : (AT == 1 ? m->st : m->ds);
+  k_proxy_body(m->Ns, m->Wptr, m->Wcol, m->Wval, x, sp);
+}
+
+// detection (CCD = 0) at s / st, or the CCD step s -> s + ds (CCD = 1)
+template <int AT, int CCD>
+__global__ void k_prim_prep_b(const DevMesh* __restrict__ tab, double pad) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_prim_prep_body(m->Ns, m->Nt, m->Ne, AT ? m->st : m->s, CCD ? m->ds : nullptr, m->tris, m->edges,
+                   pad, m->pbox, m->pkey, m->sf, CCD ? m->dsf : nullptr);
+}
+
+template <int AT, int CCD>
+__global__ void k_skin_check_b(const DevMesh* __restrict__ tab, double margin) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_skin_check_body(m->Ns, AT ? m->st : m->s, m->sb, CCD ? m->ds : nullptr, m->skin, margin,
+                    m->counters, m->scal);
+}
+
+__device__ __forceinline__ SweepArgs sweep_args_b(const DevMesh* m, int mode, float nearf) {
+  if (mode == 0)
+    return SweepArgs{m->Ns, m->Nt, m->Ne, m->pbox, m->pkey, m->sf, m->tris, m->edges, nearf,
+                     m->vlist, m->counters + 10, m->counters + 14, m->cap, m->counters + 11};
+  return SweepArgs{m->Ns, m->Nt, m->Ne, m->pbox, m->pkey, m->sf, m->tris, m->edges, nearf,
+                   m->cand, m->counters + 1, m->counters + 9, m->cap, m->counters + 13};
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_pt_b(const DevMesh* __restrict__ tab, float nearf) {
+  const DevMesh* m = bframe_c(tab, blockIdx.z);
+  if (!m) return;
+  k_sweep_pt_body<MODE>(sweep_args_b(m, MODE, nearf));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTile) k_sweep_ee_b(const DevMesh* __restrict__ tab, float nearf) {
+  const DevMesh* m = bframe_c(tab, blockIdx.z);
+  if (!m) return;
+  k_sweep_ee_body<MODE>(sweep_args_b(m, MODE, nearf));
+}
+
+__global__ void k_skin_near_b(const DevMesh* __restrict__ tab, float near2) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_skin_near_body(m->counters, m->cap, m->vlist, m->sf, m->tris, m->edges, near2, m->nearl,
+                   m->counters + 8, m->counters + 2);
+}
+
+template <int AT>
+__global__ void k_near_pairs_b(const DevMesh* __restrict__ tab, double dhat) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_near_pairs_body(m->counters + 8, m->cap, m->cap_act, m->nearl, AT ? m->st : m->s, m->tris,
+                    m->edges, dhat, m->kappa_f, m->ee_moll ? m->elen2 : nullptr, m->pairs,
+                    m->counters, m->scal);
+}
+
+__global__ void __launch_bounds__(32 * kPairWarps) k_barrier_pairs_b(const DevMesh* __restrict__ tab,
+                                                                     double dhat) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_barrier_pairs_body<float>(m->counters, m->cap_act, m->pairs, m->s, m->tris, m->edges, m->Wptr,
+                              m->Wcol, m->x2of, dhat, m->kappa_f, m->pair_grad, m->pair_hess,
+                              m->x2mark);
+}
+
+__global__ void __launch_bounds__(32) k_mollify_ee_b(const DevMesh* __restrict__ tab, double dhat) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_mollify_ee_body(m->counters, m->cap_act, m->pairs, m->s, m->edges, m->elen2, dhat, m->kappa_f,
+                    m->pair_grad, m->pair_hess);
+}
+
+__global__ void k_zero_x2mark_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m->n2; q += gridDim.x * blockDim.x)
+    m->x2mark[q] = 0;
+}
+
+__global__ void k_mark_scan_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_mark_scan_body(m->n2, m->x2mark, m->clist, m->counters);
+}
+
+// B-check and its occupancy zeroed for the frame's n_c when they fit its
+// reduced buffers
+__global__ void k_zero_reduced_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m || m->Bc == nullptr) return;
+  k_zero_reduced_body(m->counters + 3, m->nc_cap, m->Bc, m->bocc);
+}
+
+// gradient (mode 1) and B-check (mode 2) scatter; the pair count is read on
+// the device (the grid covers the largest count of the batch)
+__global__ void k_barrier_scatter_b(const DevMesh* __restrict__ tab, int mode) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  int64_t np = m->counters[0];
+  np = np < m->cap_act ? np : m->cap_act;
+  k_barrier_scatter_body(np, m->pairs, m->tris, m->edges, m->Wptr, m->Wcol, m->Wval, m->x2of,
+                         m->x2mark, m->pair_grad, m->pair_hess, m->counters + 3,
+                         m->Bc != nullptr ? m->nc_cap : 0, mode, m->g, m->Bc, m->bocc);
+}
+
+__global__ void k_ccd_reset_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m || threadIdx.x != 0) return;
+  k_ccd_reset_body(m->counters, m->scal);
+}
+
+__global__ void k_skin_cand_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_skin_cand_body(m->counters, m->cap, m->vlist, m->pkey, m->Ns, m->Nt, m->cand);
+}
+
+__global__ void k_accd_list_b(const DevMesh* __restrict__ tab, double ccd_s, int accd_max_iters,
+                              float slack) {
+  const DevMesh* m = bframe_c(tab, blockIdx.y);
+  if (!m) return;
+  k_accd_list_body(m->counters + 1, m->cap, m->cand, m->s, m->ds, m->sf, m->dsf, m->tris, m->edges,
+                   ccd_s, accd_max_iters, slack, m->scal + 1);
+}
+
+namespace {
+void launch_sweeps_b(cudaStream_t st, const DevMesh* tab, int nb, const DevMesh& m0, int mode,
+                     float nearf) {
+  if (m0.Ns > 0 && m0.Nt > 0) {
+    dim3 gpt((m0.Ns + kTile - 1) / kTile, (m0.Nt + kTile - 1) / kTile, nb);
+    if (mode == 0) k_sweep_pt_b<0><<<gpt, kTile, 0, st>>>(tab, nearf);
+    else k_sweep_pt_b<1><<<gpt, kTile, 0, st>>>(tab, nearf);
+    count_launch();
+  }
+  if (m0.Ne > 1) {
+    const int ne = (m0.Ne + kTile - 1) / kTile;
+    if (mode == 0) k_sweep_ee_b<0><<<dim3(ne, ne, nb), kTile, 0, st>>>(tab, nearf);
+    else k_sweep_ee_b<1><<<dim3(ne, ne, nb), kTile, 0, st>>>(tab, nearf);
+    count_launch();
+  }
+}
+}  // namespace
+
+void launch_eval_reset_b(cudaStream_t st, const DevMesh* tab, int nb) {
+  k_eval_reset_b<<<dim3(1, nb), 32, 0, st>>>(tab);
+  count_launch();
+}
+
+void launch_proxy_b(cudaStream_t st, const DevMesh* tab, int nb, const DevMesh& m0, int at) {
+  const dim3 g((m0.Ns + 255) / 256, nb);
+  if (at == 0) k_proxy_b<0><<<g, 256, 0, st>>>(tab);
+  else if (at == 1) k_proxy_b<1><<<g, 256, 0, st>>>(tab);
+  else k_proxy_b<2><<<g, 256, 0, st>>>(tab);
+  count_launch();
+}
+
+void launch_detect_b(cudaStream_t st, const DevMesh* tab, int nb, const DevMesh& m0, int at,
+                     double dhat) {
+  ProfScope ps(PROF_DETECT, st);
+  const int np = nprim(m0);
+  if (np == 0) return;
+  const double pad = dhat + m0.skin;
+  const float margin = (float)skin_margin(m0, dhat);
+  const dim3 gp((np + 255) / 256, nb);
+  if (at) {
+    k_prim_prep_b<1, 0><<<gp, 256, 0, st>>>(tab, pad);
+    k_skin_check_b<1, 0><<<dim3(1, nb), 512, 0, st>>>(tab, margin);
+  } else {
+    k_prim_prep_b<0, 0><<<gp, 256, 0, st>>>(tab, pad);
+    k_skin_check_b<0, 0><<<dim3(1, nb), 512, 0, st>>>(tab, margin);
+  }
+  count_launch(2);
+  launch_sweeps_b(st, tab, nb, m0, 0, (float)pad + margin);
+  k_skin_near_b<<<dim3(2 * 152, nb), 128, 0, st>>>(tab, 2.0f * (float)dhat);
+  if (at) k_near_pairs_b<1><<<dim3(2 * 152, nb), 128, 0, st>>>(tab, dhat);
+  else k_near_pairs_b<0><<<dim3(2 * 152, nb), 128, 0, st>>>(tab, dhat);
+  count_launch(2);
+}
+
+void launch_barrier_b(cudaStream_t st, const DevMesh* tab, int nb, const DevMesh& m0,
+                      int64_t np_max, double dhat) {
+  k_zero_x2mark_b<<<dim3((std::max(m0.n2, 1) + 255) / 256, nb), 256, 0, st>>>(tab);
+  count_launch();
+  np_max = np_max < m0.cap_act ? np_max : m0.cap_act;
+  if (np_max > 0) {
+    ProfScope ps(PROF_BARRIER, st);
+    const int64_t want = (np_max + kPairWarps - 1) / kPairWarps;
+    const unsigned grid = (unsigned)(want < 8 * 152 ? want : 8 * 152);
+    k_barrier_pairs_b<<<dim3(grid, nb), 32 * kPairWarps, 0, st>>>(tab, dhat);
+    count_launch();
+    if (m0.ee_moll) {
+      k_mollify_ee_b<<<dim3(grid, nb), 32, 0, st>>>(tab, dhat);
+      count_launch();
+    }
+  }
+  k_mark_scan_b<<<dim3(1, nb), 1024, 0, st>>>(tab);
+  k_zero_reduced_b<<<dim3(2 * 152, nb), 256, 0, st>>>(tab);
+  count_launch(2);
+  if (np_max > 0) {
+    const int64_t threads = 16 * np_max;
+    k_barrier_scatter_b<<<dim3((unsigned)((threads + 127) / 128), nb), 128, 0, st>>>(tab, 3);
+    count_launch();
+  }
+}
+
+void launch_ccd_b(cudaStream_t st, const DevMesh* tab, int nb, const DevMesh& m0, double dhat,
+                  double ccd_s, int accd_max_iters) {
+  launch_proxy_b(st, tab, nb, m0, 2);
+  k_ccd_reset_b<<<dim3(1, nb), 32, 0, st>>>(tab);
+  count_launch();
+  ProfScope ps(PROF_CCD, st);
+  const int np = nprim(m0);
+  if (np == 0) return;
+  k_prim_prep_b<0, 1><<<dim3((np + 255) / 256, nb), 256, 0, st>>>(tab, dhat);
+  k_skin_check_b<0, 1><<<dim3(1, nb), 512, 0, st>>>(tab, 0.0);
+  k_skin_cand_b<<<dim3(2 * 152, nb), 128, 0, st>>>(tab);
+  count_launch(3);
+  launch_sweeps_b(st, tab, nb, m0, 1, 0.0f);
+  const double slack = fmax(0.01 * dhat, 1e-5 * m0.coord_scale);
+  k_accd_list_b<<<dim3(4 * 152, nb), 128, 0, st>>>(tab, ccd_s, accd_max_iters, (float)slack);
   count_launch();
 }
 

@@ -254,13 +254,20 @@ k_elastic(int T, const int4* __restrict__ tets, const double* __restrict__ dminv
 // 1/2 w |D|^2 and the forces w D gradN_a.  Forces are written as float
 // pairs (tetf reinterpreted, the same 8 bytes per entry as float64) and
 // summed per vertex by k_gather_forces_df; the energy is summed per block in
-// double-float and converted once per block.
-__global__ void k_disp_df(int n3, const double* __restrict__ x, const double* __restrict__ rest,
-                          float2* __restrict__ udf) {
+// double-float and converted once per block.  Sums of products use Dekker's
+// addition (df_add_fast); the strain D = F - p, where F and p agree to a few
+// digits, uses the full df_add.
+__device__ __forceinline__ void disp_df_body(int n3, const double* __restrict__ x,
+                                             const double* __restrict__ rest,
+                                             float2* __restrict__ udf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
   const df u = df_from_double(__dsub_rn(x[i], rest[i]));
   udf[i] = make_float2(u.hi, u.lo);
+}
+__global__ void k_disp_df(int n3, const double* __restrict__ x, const double* __restrict__ rest,
+                          float2* __restrict__ udf) {
+  disp_df_body(n3, x, rest, udf);
 }
 
 __device__ __forceinline__ df ld_df(const float2* __restrict__ p, size_t i) {
@@ -277,11 +284,14 @@ __device__ __forceinline__ df warp_sum_df(df v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kElasticThreads)
-k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dminv_df,
-             const float2* __restrict__ w_df, const float2* __restrict__ act_df,
-             const float2* __restrict__ udf, float2* __restrict__ tetf,
-             double* __restrict__ proj, double* __restrict__ partials) {
+__device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ tets,
+                                                const float2* __restrict__ dminv_df,
+                                                const float2* __restrict__ w_df,
+                                                const float2* __restrict__ act_df,
+                                                const float2* __restrict__ udf,
+                                                float2* __restrict__ tetf,
+                                                double* __restrict__ proj,
+                                                double* __restrict__ partials) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   df e = {0.f, 0.f};
   if (t < T) {
@@ -310,15 +320,15 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        F[i][j] = df_add(df_add(df_mul(Du[i][0], Di[0][j]), df_mul(Du[i][1], Di[1][j])),
+        F[i][j] = df_add_fast(df_add_fast(df_mul(Du[i][0], Di[0][j]), df_mul(Du[i][1], Di[1][j])),
                          df_mul(Du[i][2], Di[2][j]));
-        if (i == j) F[i][j] = df_add(F[i][j], df_from_float(1.f));
+        if (i == j) F[i][j] = df_add_fast(F[i][j], df_from_float(1.f));
       }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        M[i][j] = df_add(df_add(df_mul(F[i][0], A[0][j]), df_mul(F[i][1], A[1][j])),
+        M[i][j] = df_add_fast(df_add_fast(df_mul(F[i][0], A[0][j]), df_mul(F[i][1], A[1][j])),
                          df_mul(F[i][2], A[2][j]));
     float R0[3][3];
     {
@@ -335,7 +345,7 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j) {
-        df g = df_add(df_add(df_two_prod(R0[0][i], R0[0][j]), df_two_prod(R0[1][i], R0[1][j])),
+        df g = df_add_fast(df_add_fast(df_two_prod(R0[0][i], R0[0][j]), df_two_prod(R0[1][i], R0[1][j])),
                       df_two_prod(R0[2][i], R0[2][j]));
         const df r = df_sub(df_from_float(i == j ? 1.f : 0.f), g);
         Dm[i][j] = Dm[j][i] = 0.5f * (r.hi + r.lo);
@@ -348,10 +358,10 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        df acc = df_add(df_add(df_mul_f(M[0][j], R0[0][i]), df_mul_f(M[1][j], R0[1][i])),
+        df acc = df_add_fast(df_add_fast(df_mul_f(M[0][j], R0[0][i]), df_mul_f(M[1][j], R0[1][i])),
                         df_mul_f(M[2][j], R0[2][i]));
         const float c = R1c[0][i] * M[0][j].hi + R1c[1][i] * M[1][j].hi + R1c[2][i] * M[2][j].hi;
-        S[i][j] = df_add(acc, df_from_float(c));
+        S[i][j] = df_add_fast(acc, df_from_float(c));
       }
     float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
     {
@@ -401,7 +411,7 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        P[i][j] = df_add(df_add(df_mul(R[i][0], A[0][j]), df_mul(R[i][1], A[1][j])),
+        P[i][j] = df_add_fast(df_add_fast(df_mul(R[i][0], A[0][j]), df_mul(R[i][1], A[1][j])),
                          df_mul(R[i][2], A[2][j]));
     const df wt = ld_df(w_df, t);
     df Dd[3][3];
@@ -411,7 +421,7 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         Dd[i][j] = df_sub(F[i][j], P[i][j]);
-        ssum = df_add(ssum, df_mul(Dd[i][j], Dd[i][j]));
+        ssum = df_add_fast(ssum, df_mul(Dd[i][j], Dd[i][j]));
       }
     e = df_mul(wt, ssum);
     e.hi *= 0.5f;
@@ -422,7 +432,7 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
     for (int a = 1; a < 4; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const df q = df_add(df_add(df_mul(Dd[d][0], Di[a - 1][0]), df_mul(Dd[d][1], Di[a - 1][1])),
+        const df q = df_add_fast(df_add_fast(df_mul(Dd[d][0], Di[a - 1][0]), df_mul(Dd[d][1], Di[a - 1][1])),
                             df_mul(Dd[d][2], Di[a - 1][2]));
         const df fa = df_mul(wt, q);
         tetf[(size_t)(a * 3 + d) * T + t] = make_float2(fa.hi, fa.lo);
@@ -448,11 +458,21 @@ k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dm
   }
 }
 
+__global__ void __launch_bounds__(kElasticThreads)
+k_elastic_df(int T, const int4* __restrict__ tets, const float2* __restrict__ dminv_df,
+             const float2* __restrict__ w_df, const float2* __restrict__ act_df,
+             const float2* __restrict__ udf, float2* __restrict__ tetf,
+             double* __restrict__ proj, double* __restrict__ partials) {
+  elastic_df_body(T, tets, dminv_df, w_df, act_df, udf, tetf, proj, partials);
+}
+
 // Per-vertex sum of the double-float per-tet forces (fixed order), one
 // float64 conversion per coordinate.
-__global__ void k_gather_forces_df(int n, int T, const int* __restrict__ vptr,
-                                   const int* __restrict__ vslot, const float2* __restrict__ tetf,
-                                   const uint8_t* __restrict__ pinned, double* __restrict__ g) {
+__device__ __forceinline__ void gather_forces_df_body(int n, int T, const int* __restrict__ vptr,
+                                                      const int* __restrict__ vslot,
+                                                      const float2* __restrict__ tetf,
+                                                      const uint8_t* __restrict__ pinned,
+                                                      double* __restrict__ g) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
@@ -468,6 +488,11 @@ __global__ void k_gather_forces_df(int n, int T, const int* __restrict__ vptr,
   g[3 * (size_t)v + 0] = df_to_double(s0);
   g[3 * (size_t)v + 1] = df_to_double(s1);
   g[3 * (size_t)v + 2] = df_to_double(s2);
+}
+__global__ void k_gather_forces_df(int n, int T, const int* __restrict__ vptr,
+                                   const int* __restrict__ vslot, const float2* __restrict__ tetf,
+                                   const uint8_t* __restrict__ pinned, double* __restrict__ g) {
+  gather_forces_df_body(n, T, vptr, vslot, tetf, pinned, g);
 }
 
 __global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
@@ -491,11 +516,15 @@ __global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
 }
 
 // Fixed-order sum of n partials by one block (deterministic).
-__global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+__device__ __forceinline__ void sum_partials_body(const double* __restrict__ p, int n,
+                                                  double* __restrict__ out) {
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
   s = block_sum(s);
   if (threadIdx.x == 0) *out = s;
+}
+__global__ void k_sum_partials(const double* __restrict__ p, int n, double* __restrict__ out) {
+  sum_partials_body(p, n, out);
 }
 
 __global__ void k_axpy(int n3, const double* __restrict__ x, const double* __restrict__ dx,
@@ -506,8 +535,9 @@ __global__ void k_axpy(int n3, const double* __restrict__ x, const double* __res
   out[i] = x[i] + a * dx[i];
 }
 
-__global__ void k_gnorm2(int n, const double* __restrict__ g, const uint8_t* __restrict__ pinned,
-                         double* __restrict__ partials) {
+__device__ __forceinline__ void gnorm2_body(int n, const double* __restrict__ g,
+                                            const uint8_t* __restrict__ pinned,
+                                            double* __restrict__ partials) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
   if (v < n && !pinned[v]) {
@@ -516,6 +546,64 @@ __global__ void k_gnorm2(int n, const double* __restrict__ g, const uint8_t* __r
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+__global__ void k_gnorm2(int n, const double* __restrict__ g, const uint8_t* __restrict__ pinned,
+                         double* __restrict__ partials) {
+  gnorm2_body(n, g, pinned, partials);
+}
+
+// ---- lock-step batches: one launch for the frames of a batch table ----------
+// blockIdx.y selects the frame; a frame whose `active` flag is clear returns
+// at once (uniformly for its blocks).  AT selects the evaluation point: 0 =
+// the iterate (x, tetf), 1 = the line-search trial (xt, tetf_t).
+__device__ __forceinline__ const DevMesh* bframe(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = tab + blockIdx.y;
+  return m->active ? m : nullptr;
+}
+
+template <int AT>
+__global__ void k_disp_df_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  disp_df_body(3 * m->n, AT ? m->xt : m->x, m->rest, m->udf);
+}
+
+template <int AT>
+__global__ void __launch_bounds__(kElasticThreads) k_elastic_df_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  elastic_df_body(m->T, m->tets, m->dminv_df, m->w_df, m->act_df, m->udf,
+                  reinterpret_cast<float2*>(AT ? m->tetf_t : m->tetf), nullptr, m->partials);
+}
+
+// out = scal[which] of each frame: the fixed-order sum of its nparts partials
+__global__ void k_sum_partials_b(const DevMesh* __restrict__ tab, int nparts, int which) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  sum_partials_body(m->partials, nparts, m->scal + which);
+}
+
+__global__ void k_gather_forces_df_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  gather_forces_df_body(m->n, m->T, m->vinc_ptr, m->vinc_slot,
+                        reinterpret_cast<const float2*>(m->tetf), m->pinned, m->g);
+}
+
+// xt = x + (alpha_m * ls_scale) dx per frame
+__global__ void k_axpy_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * m->n) return;
+  const double a = m->scal[1] * m->ls_scale;
+  m->xt[i] = m->x[i] + a * m->dx[i];
+}
+
+__global__ void k_gnorm2_b(const DevMesh* __restrict__ tab) {
+  const DevMesh* m = bframe(tab);
+  if (!m) return;
+  gnorm2_body(m->n, m->g, m->pinned, m->partials);
 }
 
 __global__ void k_reset_pinned(int n, const uint8_t* __restrict__ pinned,
@@ -587,6 +675,36 @@ void launch_axpy_positions(cudaStream_t s, int n3, const double* x, const double
 }
 
 int gnorm_blocks(int n) { return (n + 255) / 256; }
+
+void launch_local_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, int at) {
+  ProfScope ps(PROF_ELASTIC, s);
+  const dim3 gv((3 * m0.n + 255) / 256, nb), gt(elastic_blocks(m0.T), nb);
+  if (at) {
+    k_disp_df_b<1><<<gv, 256, 0, s>>>(tab);
+    k_elastic_df_b<1><<<gt, kElasticThreads, 0, s>>>(tab);
+  } else {
+    k_disp_df_b<0><<<gv, 256, 0, s>>>(tab);
+    k_elastic_df_b<0><<<gt, kElasticThreads, 0, s>>>(tab);
+  }
+  k_sum_partials_b<<<dim3(1, nb), 1024, 0, s>>>(tab, elastic_blocks(m0.T), 2);
+  count_launch(3);
+}
+
+void launch_gather_forces_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0) {
+  k_gather_forces_df_b<<<dim3((m0.n + 255) / 256, nb), 256, 0, s>>>(tab);
+  count_launch();
+}
+
+void launch_gnorm2_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0) {
+  k_gnorm2_b<<<dim3(gnorm_blocks(m0.n), nb), 256, 0, s>>>(tab);
+  k_sum_partials_b<<<dim3(1, nb), 1024, 0, s>>>(tab, gnorm_blocks(m0.n), 3);
+  count_launch(2);
+}
+
+void launch_axpy_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0) {
+  k_axpy_b<<<dim3((3 * m0.n + 255) / 256, nb), 256, 0, s>>>(tab);
+  count_launch();
+}
 
 void launch_gnorm2(cudaStream_t s, const DevMesh& m, const double* g, double* partials, int nblk) {
   k_gnorm2<<<nblk, 256, 0, s>>>(m.n, g, m.pinned, partials);

@@ -32,6 +32,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "kernels.h"
@@ -74,6 +75,7 @@ struct RedArgs {
   double* S64;          // one-CTA path: Sigma^-1[c, c] in float64 (n_c x n_c)
   int* info;
   int small_lim;        // n_c handled by the one-CTA path (0: none)
+  int active;           // lock-step batches: the frame takes part in the launch
   FT* spk;              // one-CTA path: L_s packed, diagonal blocks inverted
 };
 
@@ -306,7 +308,7 @@ __device__ void z2_update(const RedArgs<FT>& a, int nc, int w, int nw) {
 
 // The z2 update alone (plain launch) after the one-CTA or cluster path; with
 // n_c = 0 it copies z2 = u.
-__global__ void __launch_bounds__(256) k_z2_update(RedArgs<float> a) {
+__device__ __forceinline__ void k_z2_update_body(RedArgs<float> a) {
   const int nc = *a.nc_dev;
   if (nc == 0) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * a.n2; e += gridDim.x * blockDim.x)
@@ -316,6 +318,9 @@ __global__ void __launch_bounds__(256) k_z2_update(RedArgs<float> a) {
   if (nc > a.small_lim) return;         // the cooperative kernel owns larger n_c
   red_layout(a, nc);
   z2_update(a, nc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+__global__ void __launch_bounds__(256) k_z2_update(RedArgs<float> a) {
+  k_z2_update_body(a);
 }
 
 template <typename FT>
@@ -727,7 +732,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 // k_small_s: S = Sigma^-1[c, c], its factor (plain, row-major into a.S for
 // the products; packed with inverted diagonal blocks into a.spk for the
 // solves) and the block-row lists of B.
-__global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
+__device__ __forceinline__ void k_small_s_body(RedArgs<float> a) {
   extern __shared__ float smem_f[];
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > a.small_lim) return;
@@ -771,11 +776,14 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
   }
   for (int e = tid; e < prow(nc); e += kST) a.spk[e] = P[e];
 }
+__global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
+  k_small_s_body(a);
+}
 
 // k_small_x (grid): y = B u_c in float64, |y2|^2 (PARTS & 1: these need the
 // right-hand side), X = B (L_s (x) I_3) (PARTS & 2: needs only B and L_s).
 template <int PARTS>
-__global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
+__device__ __forceinline__ void k_small_x_body(RedArgs<float> a) {
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > a.small_lim) return;
   red_layout(a, nc);
@@ -817,9 +825,13 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
     a.X[e] = acc;
   }
 }
+template <int PARTS>
+__global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
+  k_small_x_body<PARTS>(a);
+}
 
 // k_small_n (grid): N = I + (L_s (x) I_3)^T X, lower part, packed.
-__global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
+__device__ __forceinline__ void k_small_n_body(RedArgs<float> a) {
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > a.small_lim) return;
   red_layout(a, nc);
@@ -834,6 +846,9 @@ __global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
     for (int j = i; j < nc; ++j) acc += a.S[(size_t)j * nc + i] * a.X[(size_t)(3 * j + ax) * n3 + col];
     a.N[prow(row) + col] = acc;        // packed lower, the layout k_small_v factors in
   }
+}
+__global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
+  k_small_n_body(a);
 }
 
 // q = (L_s (x) I_3)^T p (float; L_s packed plain, in shared memory)
@@ -938,7 +953,7 @@ __device__ double refine_rho(const RedArgs<float>& a, int nc, int t, int nt) {
 // k_small_v (1 CTA): L_N in shared memory, v = (L_s (x) I)^-T N^-1 (L_s (x) I)^T y
 // and the float64-residual refinement of v (same stopping rule as the
 // cooperative kernel).
-__global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
+__device__ __forceinline__ void k_small_v_body(RedArgs<float> a) {
   extern __shared__ float smem_f[];
   __shared__ double red[kSW + 1];
   const int nc = *a.nc_dev;
@@ -995,6 +1010,9 @@ __global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
     __syncthreads();
   }
 }
+__global__ void __launch_bounds__(kST) k_small_v(RedArgs<float> a) {
+  k_small_v_body(a);
+}
 
 // ---------------------------------------------------------------------------
 // k_clus_v: the same solve for kSmallNc < n_c <= kClusNc on a cluster of kCl
@@ -1029,7 +1047,7 @@ constexpr size_t kClusSmem =
 
 // (__maxnreg__ rather than __launch_bounds__: with the latter ptxas settles
 // on 64 registers and spills; 512 threads x 128 registers fill one SM)
-__global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
+__device__ __forceinline__ void k_clus_v_body(RedArgs<float> a) {
   namespace cgx = cooperative_groups;
   cgx::cluster_group cl = cgx::this_cluster();
   extern __shared__ float smem_f[];
@@ -1404,6 +1422,9 @@ __global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
     finish(true);
   }
 }
+__global__ void __maxnreg__(128) k_clus_v(RedArgs<float> a) {
+  k_clus_v_body(a);
+}
 
 constexpr size_t kSmallSmemS = sizeof(float) * ((size_t)prow(kClusNc) + 32 * kPtLd);
 constexpr size_t kSmallSmemV = sizeof(float) * ((size_t)prow(kSmallN3) + 32 * kPtLd + kSmallN3);
@@ -1574,7 +1595,167 @@ __global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply(RedArgs<float> a, 
   }
 }
 
+// ---- lock-step batches: blockIdx.y = frame, RedArgs per frame on the device
+template <int PARTS>
+__global__ void __launch_bounds__(256) k_small_x_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_small_x_body<PARTS>(a);
+}
+__global__ void __launch_bounds__(kST) k_small_s_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_small_s_body(a);
+}
+__global__ void __launch_bounds__(256) k_small_n_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_small_n_body(a);
+}
+__global__ void __launch_bounds__(kST) k_small_v_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_small_v_body(a);
+}
+// one 4-CTA cluster per frame: the cluster spans blockIdx.x, the frame is
+// blockIdx.y, so the inactive test is uniform over a cluster
+__global__ void __maxnreg__(128) k_clus_v_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_clus_v_body(a);
+}
+__global__ void __launch_bounds__(256) k_z2_update_b(const RedArgs<float>* __restrict__ A) {
+  const RedArgs<float> a = A[blockIdx.y];
+  if (a.active) k_z2_update_body(a);
+}
+
+// x1 = bx1 + Phi[:, c] v for every frame and any n_c (v from whichever path
+// solved the reduced system), with bx1 read from a multi-right-hand-side
+// buffer: frame f's three columns start at column col_f of rows of nr floats.
+__global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply_b(const RedArgs<float>* __restrict__ A,
+                                                               const int* __restrict__ cols, int n1,
+                                                               const float* __restrict__ phi_t,
+                                                               const float* __restrict__ bxm, int nr,
+                                                               double* const* __restrict__ x1s) {
+  RedArgs<float> a = A[blockIdx.y];
+  if (!a.active) return;
+  __shared__ float vs[3 * kClusNc];
+  __shared__ int cs[kClusNc];
+  __shared__ float part[kPhiSplit][3][32];
+  const int nc = *a.nc_dev;
+  const int col = cols[blockIdx.y];
+  double* x1 = x1s[blockIdx.y];
+  if (nc > 0) red_layout(a, nc);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  for (int k0 = 0; k0 < nc; k0 += kClusNc) {       // n_c in chunks of the staging size
+    const int kn = min(kClusNc, nc - k0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kn; k += blockDim.x) {
+      cs[k] = a.clist[k0 + k];
+      vs[3 * k] = (float)a.v[3 * (k0 + k)];
+      vs[3 * k + 1] = (float)a.v[3 * (k0 + k) + 1];
+      vs[3 * k + 2] = (float)a.v[3 * (k0 + k) + 2];
+    }
+    __syncthreads();
+    if (p < n1) {
+#pragma unroll 4
+      for (int k = wq; k < kn; k += kPhiSplit) {
+        const float f = phi_t[(size_t)cs[k] * n1 + p];
+        c0 += f * vs[3 * k];
+        c1 += f * vs[3 * k + 1];
+        c2 += f * vs[3 * k + 2];
+      }
+    }
+  }
+  part[wq][0][lane] = c0;
+  part[wq][1][lane] = c1;
+  part[wq][2][lane] = c2;
+  __syncthreads();
+  if (wq < 3 && p < n1)  {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < kPhiSplit; ++q) t += part[q][wq][lane];
+    x1[3 * (size_t)p + wq] = (double)bxm[(size_t)p * nr + col + wq] + (double)t;
+  }
+}
+
 }  // namespace
+
+size_t reduced_args_bytes() { return sizeof(RedArgs<float>); }
+
+void reduced_args_fill(void* dst, const DevMesh& m, int active) {
+  RedArgs<float> a = make_args<float>(m, m.u, (const float*)(m.rf + 3 * (size_t)m.n1),
+                                      m.r + 3 * (size_t)m.n1, m.counters + 6, kMixedRefineSteps);
+  a.active = active;
+  std::memcpy(dst, &a, sizeof(a));
+}
+
+cudaError_t reduced_prepare_b(cudaStream_t s2, const void* args_dev, int nb, int num_sms) {
+  const auto* A = static_cast<const RedArgs<float>*>(args_dev);
+  ProfScope ps(PROF_CHOL, s2);
+  k_small_s_b<<<dim3(1, nb), kST, kSmallSmemS, s2>>>(A);
+  k_small_x_b<2><<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s2>>>(A);
+  k_small_n_b<<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s2>>>(A);
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+cudaError_t reduced_solve_b(cudaStream_t s, const void* args_dev, const void* args_host, int nb,
+                            const int* nc_host, int num_sms) {
+  const auto* A = static_cast<const RedArgs<float>*>(args_dev);
+  const auto* H = static_cast<const RedArgs<float>*>(args_host);
+  bool any_small = false, any_clus = false;
+  for (int f = 0; f < nb; ++f) {
+    if (!H[f].active) continue;
+    any_small |= nc_host[f] > 0 && nc_host[f] <= kSmallNc;
+    any_clus |= nc_host[f] > kSmallNc && nc_host[f] <= kClusNc;
+  }
+  ProfScope ps(PROF_CHOL, s);
+  k_small_x_b<1><<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s>>>(A);
+  count_launch();
+  if (any_small) {
+    k_small_v_b<<<dim3(1, nb), kST, kSmallSmemV, s>>>(A);
+    count_launch();
+  }
+  if (any_clus) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCl, nb);
+    cfg.blockDim = dim3(kST);
+    cfg.dynamicSmemBytes = kClusSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kCl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_clus_v_b, A);
+    count_launch();
+    if (e != cudaSuccess) return e;
+  }
+  // n_c beyond the cluster path: the cooperative kernel, one frame at a time
+  for (int f = 0; f < nb; ++f) {
+    if (!H[f].active || nc_host[f] <= kClusNc) continue;
+    RedArgs<float> a = H[f];
+    void* args[] = {&a};
+    const cudaError_t e = cudaLaunchCooperativeKernel((void*)k_reduced<float>,
+                                                      dim3(std::max(1, num_sms)), dim3(kRT), args,
+                                                      0, s);
+    count_launch();
+    if (e != cudaSuccess) return e;
+  }
+  const int zgrid = std::max(1, std::min(2 * std::max(1, num_sms) / nb, 64));
+  k_z2_update_b<<<dim3(zgrid, nb), 256, 0, s>>>(A);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t phi_apply_b(cudaStream_t s, const void* args_dev, const int* cols_dev, int nb, int n1,
+                        const float* phi_t, const float* bxm, int nr, double* const* x1s_dev) {
+  const auto* A = static_cast<const RedArgs<float>*>(args_dev);
+  k_phi_apply_b<<<dim3((n1 + 31) / 32, nb), 32 * kPhiSplit, 0, s>>>(A, cols_dev, n1, phi_t, bxm, nr,
+                                                                    x1s_dev);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t phi_apply(cudaStream_t s, const DevMesh& m, const double* u, const void* y2, double* z2,
                       int* info, const float* bx1, double* x1) {
@@ -1612,5 +1793,8 @@ void set_reduced_smem_limits() {
   cudaFuncSetAttribute(k_small_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemS);
   cudaFuncSetAttribute(k_small_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemV);
   cudaFuncSetAttribute(k_clus_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusSmem);
+  cudaFuncSetAttribute(k_small_s_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemS);
+  cudaFuncSetAttribute(k_small_v_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemV);
+  cudaFuncSetAttribute(k_clus_v_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusSmem);
 }
 }  // namespace fsim

@@ -201,6 +201,171 @@ __global__ void k_gemv3(int n2, const T* __restrict__ A, const T* __restrict__ y
 }
 
 // ---------------------------------------------------------------------------
+// Lock-step batches: the triangular solves and the Sigma^-1 product for the
+// right-hand sides of all frames at once.  A multi-right-hand-side buffer
+// holds, per solver position p, a row of nr floats; frame f's three columns
+// start at column 3 col_f.  The factor is read once per pass for all frames.
+// A CTA takes one work item (as in the single-frame solves) and 32 columns
+// (blockIdx.y); lane = column, each warp 4 rows (forward, GEMM) or one factor
+// column (backward); the factor tile is staged in shared memory so that every
+// factor entry is one broadcast shared-memory load for 32 columns.
+// ---------------------------------------------------------------------------
+constexpr int kMrCols = 32;
+constexpr int kMrK = 64;           // factor rows / columns staged per step
+
+__global__ void __launch_bounds__(256)
+k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
+         const int* __restrict__ nra, const int64_t* __restrict__ roff,
+         const int64_t* __restrict__ zoff, const int* __restrict__ rows,
+         const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr) {
+  extern __shared__ float bj[];                    // ns x 32
+  __shared__ __align__(16) float Zs[kMrK][32];
+  const int4 it = items[blockIdx.x];
+  const int J = it.x, r0 = it.y, rn = it.z;
+  const int cc = blockIdx.y * kMrCols;
+  const int c0 = c0a[J], ns = nsa[J], ld = ns + nra[J];
+  const float* Zj = Z + zoff[J];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < ns * kMrCols; e += blockDim.x)
+    bj[e] = b[(size_t)(c0 + e / kMrCols) * nr + cc + (e % kMrCols)];
+  // rows of the diagonal block only need k <= row (L_JJ^-1 is lower triangular)
+  const int kend = r0 < ns ? min(ns, r0 + rn) : ns;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < kend; k0 += kMrK) {
+    __syncthreads();
+    for (int e = tid; e < kMrK * 32; e += blockDim.x) {
+      const int kk = e >> 5, rr = e & 31, k = k0 + kk, r = r0 + rr;
+      Zs[kk][rr] = (k < kend && rr < rn && (r >= ns || k <= r)) ? Zj[(size_t)k * ld + r] : 0.f;
+    }
+    __syncthreads();
+    const int kn = min(kMrK, kend - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      const float bk = bj[(k0 + kk) * kMrCols + lane];
+      const float4 z = *reinterpret_cast<const float4*>(&Zs[kk][4 * wid]);
+      acc[0] += z.x * bk; acc[1] += z.y * bk; acc[2] += z.z * bk; acc[3] += z.w * bk;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = 4 * wid + q;
+    if (rr >= rn) continue;
+    const int r = r0 + rr;
+    if (r < ns) y[(size_t)(c0 + r) * nr + cc + lane] = acc[q];
+    else atomicAdd(b + (size_t)rows[roff[J] + r - ns] * nr + cc + lane, -acc[q]);
+  }
+}
+
+// x_J[k] = sum_{r >= k} Z_J[r][k] w[r], w = [y_J ; -x_R], columns k0 .. k0 + kn
+// (kn <= 8): warp c takes column k0 + c
+__global__ void __launch_bounds__(256)
+k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
+         const int* __restrict__ nra, const int64_t* __restrict__ roff,
+         const int64_t* __restrict__ zoff, const int* __restrict__ rows,
+         const float* __restrict__ Z, const float* __restrict__ y, float* __restrict__ x, int nr) {
+  constexpr int kRows = 256;
+  __shared__ float ws[kRows][32];
+  __shared__ float Zs[kBwdCols][kRows];
+  const int4 it = items[blockIdx.x];
+  const int J = it.x, k0 = it.y, kn = it.z;
+  const int cc = blockIdx.y * kMrCols;
+  const int c0 = c0a[J], ns = nsa[J], ld = ns + nra[J];
+  const float* Zj = Z + zoff[J];
+  const int* Rj = rows + roff[J];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float acc = 0.f;
+  for (int rb = k0; rb < ld; rb += kRows) {
+    const int rn = min(kRows, ld - rb);
+    __syncthreads();
+    for (int e = tid; e < rn * 32; e += blockDim.x) {
+      const int rr = e >> 5, j = e & 31, r = rb + rr;
+      ws[rr][j] = r < ns ? y[(size_t)(c0 + r) * nr + cc + j] : -x[(size_t)Rj[r - ns] * nr + cc + j];
+    }
+    for (int e = tid; e < kBwdCols * kRows; e += blockDim.x) {
+      const int c = e / kRows, rr = e % kRows, r = rb + rr, k = k0 + c;
+      Zs[c][rr] = (c < kn && rr < rn && r >= k) ? Zj[(size_t)k * ld + r] : 0.f;
+    }
+    __syncthreads();
+    if (wid < kn)
+      for (int rr = 0; rr < rn; ++rr) acc += Zs[wid][rr] * ws[rr][lane];
+  }
+  if (wid < kn) x[(size_t)(c0 + k0 + wid) * nr + cc + lane] = acc;
+}
+
+// u = Sigma^-1 y2 for all columns: rows [32 blockIdx.x, +32), columns chunk blockIdx.y
+__global__ void __launch_bounds__(256)
+k_gemm_mr(int n2, const float* __restrict__ A, const float* __restrict__ yv, float* __restrict__ u,
+          int nr) {
+  __shared__ __align__(16) float As[kMrK][32];
+  __shared__ float Ys[kMrK][32];
+  const int i0 = blockIdx.x * 32, cc = blockIdx.y * kMrCols;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < n2; k0 += kMrK) {
+    __syncthreads();
+    for (int e = tid; e < kMrK * 32; e += blockDim.x) {
+      const int rr = e / kMrK, kk = e % kMrK, i = i0 + rr, k = k0 + kk;   // coalesced along k
+      As[kk][rr] = (i < n2 && k < n2) ? A[(size_t)i * n2 + k] : 0.f;
+      const int kk2 = e >> 5, j = e & 31, k2 = k0 + kk2;
+      Ys[kk2][j] = k2 < n2 ? yv[(size_t)k2 * nr + cc + j] : 0.f;
+    }
+    __syncthreads();
+    const int kn = min(kMrK, n2 - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      const float yk = Ys[kk][lane];
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * wid]);
+      acc[0] += a.x * yk; acc[1] += a.y * yk; acc[2] += a.z * yk; acc[3] += a.w * yk;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + 4 * wid + q;
+    if (i < n2) u[(size_t)i * nr + cc + lane] = acc[q];
+  }
+}
+
+// right-hand sides r = -g of every frame into the multi-RHS buffer (zero
+// columns for inactive frames, so that stale columns never grow)
+__global__ void k_gather_rhs_mr(const DevMesh* __restrict__ tab, float* __restrict__ rb, int nr) {
+  const DevMesh& m = tab[blockIdx.y];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m.nf) return;
+  float* dst = rb + (size_t)p * nr + 3 * m.col;
+  if (!m.active) { dst[0] = 0.f; dst[1] = 0.f; dst[2] = 0.f; return; }
+  const int v = m.perm[p];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dst[d] = (float)(-m.g[3 * (size_t)v + d]);
+}
+
+// per frame: u (float64) and y2 (float) in the frame's own buffers for the
+// reduced system; x2 rows of the contact-free backward solve = u (all columns)
+__global__ void k_unpack_mr(const DevMesh* __restrict__ tab, const float* __restrict__ ub,
+                            const float* __restrict__ rb, float* __restrict__ bx, int nr) {
+  const DevMesh& m = tab[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n2) return;
+  if (blockIdx.y == 0)
+    for (int j = 0; j < nr; ++j) bx[(size_t)(m.n1 + i) * nr + j] = ub[(size_t)i * nr + j];
+  if (!m.active) return;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    m.u[3 * (size_t)i + d] = (double)ub[(size_t)i * nr + 3 * m.col + d];
+    m.rf[3 * (size_t)(m.n1 + i) + d] = rb[(size_t)(m.n1 + i) * nr + 3 * m.col + d];
+  }
+}
+
+// dx of every active frame from its float64 solution r (solver order); zero
+// on pinned vertices
+__global__ void k_scatter_dx_b(const DevMesh* __restrict__ tab) {
+  const DevMesh& m = tab[blockIdx.y];
+  if (!m.active) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m.n) return;
+  const int p = m.pos[v];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) m.dx[3 * (size_t)v + d] = p >= 0 ? m.r[3 * (size_t)p + d] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 namespace {
@@ -366,7 +531,74 @@ cudaError_t global_step_t(cudaStream_t s, const DevMesh& m, const double* g, dou
 
 }  // namespace
 
+cudaError_t global_step_b(const BatchStep& bs) {
+  const DevMesh& m = *bs.m0;
+  cudaStream_t s = bs.s, s2 = bs.s2;
+  const int nb = bs.nb, nr = bs.nr, n1 = m.n1, n2 = m.n2, nf = m.nf;
+  const int chunks = nr / kMrCols;
+  k_gather_rhs_mr<<<dim3((nf + 255) / 256, nb), 256, 0, s>>>(bs.tab, bs.rb, nr);
+  count_launch();
+  // S, L_s, block lists, X, N of every frame need only B-check and Sigma^-1:
+  // on the side stream, overlapping the forward solve
+  if (cudaEventRecord(bs.ev[0], s) != cudaSuccess || cudaStreamWaitEvent(s2, bs.ev[0], 0) != cudaSuccess)
+    return cudaGetLastError();
+  cudaError_t e = reduced_prepare_b(s2, bs.args_dev, nb, bs.num_sms);
+  if (e != cudaSuccess) return e;
+  if (cudaEventRecord(bs.ev[1], s2) != cudaSuccess) return cudaGetLastError();
+  for (int l = 0; l < m.n_levels && n1 > 0; ++l) {
+    const int a = m.h_fwd_ptr[l], z = m.h_fwd_ptr[l + 1];
+    if (z <= a) continue;
+    ProfScope ps(PROF_TRSV_FWD, s);
+    const size_t sm = sizeof(float) * kMrCols * (size_t)m.h_level_maxns[l];
+    k_fwd_mr<<<dim3(z - a, chunks), 256, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                   m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.rb,
+                                                   bs.yb, nr);
+    count_launch();
+  }
+  {
+    ProfScope ps(PROF_GEMV, s);
+    k_gemm_mr<<<dim3((n2 + 31) / 32, chunks), 256, 0, s>>>(n2, m.Sinvf, bs.rb + (size_t)n1 * nr,
+                                                           bs.ub, nr);
+    k_unpack_mr<<<dim3((n2 + 255) / 256, nb), 256, 0, s>>>(bs.tab, bs.ub, bs.rb, bs.bx, nr);
+    count_launch(2);
+  }
+  // the contact-free backward solve x1 = L1^-T (y1 - L21^T u) on the side
+  // stream while the reduced systems are solved
+  if (cudaEventRecord(bs.ev[2], s) != cudaSuccess || cudaStreamWaitEvent(s2, bs.ev[2], 0) != cudaSuccess)
+    return cudaGetLastError();
+  for (int l = m.n_levels - 1; l >= 0 && n1 > 0; --l) {
+    const int a = m.h_bwd_ptr[l], z = m.h_bwd_ptr[l + 1];
+    if (z <= a) continue;
+    ProfScope ps(PROF_TRSV_BWD, s2);
+    k_bwd_mr<<<dim3(z - a, chunks), 256, 0, s2>>>(m.bwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+                                                  m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.yb,
+                                                  bs.bx, nr);
+    count_launch();
+  }
+  if (cudaEventRecord(bs.ev[3], s2) != cudaSuccess) return cudaGetLastError();
+  if (cudaStreamWaitEvent(s, bs.ev[1], 0) != cudaSuccess) return cudaGetLastError();
+  {
+    ProfScope ps(PROF_REDUCED, s);
+    e = reduced_solve_b(s, bs.args_dev, bs.args_host, nb, bs.nc_host, bs.num_sms);
+    if (e != cudaSuccess) return e;
+  }
+  if (cudaStreamWaitEvent(s, bs.ev[3], 0) != cudaSuccess) return cudaGetLastError();
+  e = phi_apply_b(s, bs.args_dev, bs.cols_dev, nb, n1, m.Phi_t, bs.bx, nr, bs.x1s_dev);
+  if (e != cudaSuccess) return e;
+  k_scatter_dx_b<<<dim3((m.n + 255) / 256, nb), 256, 0, s>>>(bs.tab);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool batch_supported(const DevMesh& m, int nr) {
+  if (!m.Zf || !m.Phi_t || !m.Sinvf || m.n1 <= 0 || m.n2 <= 0 || nr % kMrCols != 0) return false;
+  int maxns = 0;
+  for (int l = 0; l < m.n_levels; ++l) maxns = std::max(maxns, m.h_level_maxns[l]);
+  return sizeof(float) * kMrCols * (size_t)maxns <= 160 * 1024;
+}
+
 void set_solver_smem_limits(int max_bytes) {
+  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
   cudaFuncSetAttribute(k_bwd_chunk<double, 256>, a, max_bytes);

@@ -141,6 +141,12 @@ struct DevMesh {
   float* Phi_t = nullptr;
   float* bx = nullptr;        // nf*3 float solve vector of the contact-free x1 solve
   int red_gen = 0;            // bumped whenever the reduced buffers move
+  // lock-step batches (batch.cu): read by the batched kernels from the
+  // device copy of a batch table
+  int active = 0;             // the frame takes part in the launch
+  double kappa_f = 0.0;       // barrier stiffness of the frame
+  double ls_scale = 1.0;      // line-search factor of the trial step
+  int col = 0;                // frame's column block (3 columns) in multi-RHS buffers
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------
@@ -236,6 +242,59 @@ void launch_gnorm2(cudaStream_t s, const DevMesh& m, const double* g, double* pa
 int gnorm_blocks(int n);
 void launch_reset_pinned(cudaStream_t s, const DevMesh& m, double* x);
 void launch_check_finite(cudaStream_t s, int n, const double* v, int* flag);
+
+// ---- lock-step batches -------------------------------------------------------
+// `tab` is a device array of nb DevMesh copies (frames of one mesh); m0 is a
+// host copy of any of them (mesh-wide sizes and constants).  Every launch
+// serves the frames whose `active` flag is set; `at` 0 evaluates at x, 1 at xt.
+void launch_eval_reset_b(cudaStream_t s, const DevMesh* tab, int nb);
+void launch_local_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, int at);
+void launch_proxy_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, int at);
+void launch_detect_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, int at, double dhat);
+void launch_gather_forces_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0);
+// x2 marks, per-pair derivatives (largest pair count np_max), n_c list,
+// B-check (zeroed and assembled when n_c fits nc_cap) and the gradient
+void launch_barrier_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, int64_t np_max,
+                      double dhat);
+void launch_gnorm2_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0);
+// ds = W dx, candidates and the additive-CCD bound alpha_m into scal[1]
+void launch_ccd_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0, double dhat,
+                  double ccd_s, int accd_max_iters);
+// xt = x + alpha_m ls_scale dx
+void launch_axpy_b(cudaStream_t s, const DevMesh* tab, int nb, const DevMesh& m0);
+
+// Global step (Eq. 8-11, mixed precision) of every active frame of a batch:
+// one multi-right-hand-side forward pass, one Sigma^-1 product and one
+// contact-free backward pass for all frames (k_solve.cu), the reduced
+// systems of all frames in batched launches (k_reduced.cu), then
+// x1 = bx1 + Phi[:, c] v and dx per frame.
+struct BatchStep {
+  cudaStream_t s = nullptr, s2 = nullptr;   // main and side stream
+  cudaEvent_t ev[4] = {};                   // fork / join events
+  const DevMesh* tab = nullptr;             // device table (nb frames)
+  const DevMesh* m0 = nullptr;              // host copy of one frame (mesh constants)
+  int nb = 0, nr = 0;                       // frames; columns of the multi-RHS buffers
+  float* rb = nullptr;                      // nf x nr right-hand sides (solver order)
+  float* yb = nullptr;                      // n1 x nr forward result
+  float* ub = nullptr;                      // n2 x nr Sigma^-1 y2
+  float* bx = nullptr;                      // nf x nr contact-free backward solution
+  const void* args_dev = nullptr;           // nb reduced-system argument blocks (device)
+  const void* args_host = nullptr;          // the same on the host
+  const int* nc_host = nullptr;             // n_c per frame
+  const int* cols_dev = nullptr;            // 3 col per frame (device)
+  double* const* x1s_dev = nullptr;         // r of each frame (device array of pointers)
+  int num_sms = 1;
+};
+cudaError_t global_step_b(const BatchStep& bs);
+// whether the batched solves can serve this mesh with nr columns
+bool batch_supported(const DevMesh& m, int nr);
+size_t reduced_args_bytes();
+void reduced_args_fill(void* dst, const DevMesh& m, int active);
+cudaError_t reduced_prepare_b(cudaStream_t s2, const void* args_dev, int nb, int num_sms);
+cudaError_t reduced_solve_b(cudaStream_t s, const void* args_dev, const void* args_host, int nb,
+                            const int* nc_host, int num_sms);
+cudaError_t phi_apply_b(cudaStream_t s, const void* args_dev, const int* cols_dev, int nb, int n1,
+                        const float* phi_t, const float* bxm, int nr, double* const* x1s_dev);
 
 // number of kernel launches issued through these launchers (per process)
 int64_t launch_counter();

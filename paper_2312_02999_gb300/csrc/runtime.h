@@ -58,6 +58,8 @@ struct Exec {
 // Allocate the per-solve buffers of workspace m (a copy of a prefactored
 // mesh's DevMesh whose constant pointers stay shared).
 int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allocs, size_t* bytes);
+// Grow the reduced-system buffers of workspace m to hold nc (synchronises ex.stream).
+int rt_ensure_reduced(const Exec& ex, DevMesh& m, int nc);
 // Algorithm 1 for one frame on workspace m; actuation must already be in m.act.
 int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                    bool init_is_dev, int precision, fsim_frame_stats* stats);

@@ -145,6 +145,8 @@ _SIGS = {
     "fsim_server_destroy": [_P],
     "fsim_solve_frames": [_P, C.c_int32, C.POINTER(Request), C.c_int32, C.POINTER(_D),
                           C.POINTER(FrameStats)],
+    "fsim_solve_batch": [_P, C.c_int32, C.POINTER(Request), C.c_int32, C.POINTER(_D),
+                         C.POINTER(FrameStats)],
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
@@ -492,3 +494,40 @@ def solve_frames(ctx: "Context", requests, workers: int = 4):
     stats = (FrameStats * max(n, 1))()
     rc = ctx.lib.fsim_solve_frames(ctx.h, n, reqs, int(workers), ptrs, stats)
     return int(rc), outs, [stats[i].as_dict() for i in range(n)]
+
+
+def solve_batch(ctx: "Context", requests, max_frames: int = 16, want_positions: bool = True):
+    """Lock-step batched form (fsim_solve_batch): requests are (mesh, fiber,
+    stretch, x_init or None) host tuples of ONE mesh, mixed precision;
+    returns (status, [positions or None], [stats])."""
+    n = len(requests)
+    keep, reqs = [], (Request * max(n, 1))()
+    outs = []
+    for i, (mesh, fiber, stretch, x_init) in enumerate(requests):
+        f = np.ascontiguousarray(fiber, dtype=np.float64)
+        a = np.ascontiguousarray(stretch, dtype=np.float64)
+        xi = None if x_init is None else np.ascontiguousarray(x_init, dtype=np.float64)
+        keep += [f, a, xi]
+        reqs[i] = Request(mesh.id, MIXED, _d(f), _d(a), _d(xi), 0, 0, None)
+        outs.append(np.empty((mesh.n, 3), dtype=np.float64) if want_positions else None)
+    ptrs = (_D * max(n, 1))(*[_d(o) for o in outs])
+    stats = (FrameStats * max(n, 1))()
+    rc = ctx.lib.fsim_solve_batch(ctx.h, n, reqs, int(max_frames), ptrs, stats)
+    return int(rc), outs, [stats[i].as_dict() for i in range(n)]
+
+
+def solve_batch_dev(ctx: "Context", mesh: "Mesh", fiber_ptrs, stretch_ptrs, x_init_ptrs,
+                    x_out_ptrs, max_frames: int = 16):
+    """Lock-step batched form with device inputs and outputs (FSIM_REQ_DEVICE):
+    per request the device pointers of its fiber (3T), stretch (T), start
+    positions (3n, or 0 for the rest pose) and output positions (3n, or 0).
+    Returns (status, [stats])."""
+    n = len(fiber_ptrs)
+    dp = lambda p: C.cast(C.c_void_p(p), _D) if p else None
+    reqs = (Request * max(n, 1))()
+    for i in range(n):
+        reqs[i] = Request(mesh.id, MIXED, dp(fiber_ptrs[i]), dp(stretch_ptrs[i]),
+                          dp(x_init_ptrs[i]), FSIM_REQ_DEVICE, 0, dp(x_out_ptrs[i]))
+    stats = (FrameStats * max(n, 1))()
+    rc = ctx.lib.fsim_solve_batch(ctx.h, n, reqs, int(max_frames), None, stats)
+    return int(rc), [stats[i].as_dict() for i in range(n)]

@@ -1,0 +1,121 @@
+"""Lock-step batched frame solves (fsim_solve_batch) against solo solves and the oracle.
+
+A batch advances up to max_frames frames of one mesh together through
+Algorithm 1 (batched launches, one multi-right-hand-side pass over the
+factor, reduced systems side by side); more requests than slots exercise the
+continuous admission of pending requests into the slots of finished frames.
+Every frame must equal the same request solved alone (mixed precision) within
+the mixed-precision bar, 1e-6 of the bounding-box diagonal, with iteration
+counts within 2; the face frames are also compared with the stored oracle
+frames (tests/golden).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2312_02999_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                    "face_seq3_f20_f21.npz")
+
+
+@pytest.fixture(scope="module")
+def fsim():
+    from paper_2312_02999_gb300 import build
+    build.build()
+    from paper_2312_02999_gb300 import fsim as f
+    return f
+
+
+@pytest.fixture(scope="module")
+def ctx(fsim):
+    c = fsim.Context(0)
+    yield c
+    c.close()
+
+
+def _diag(mesh):
+    return float(np.linalg.norm(mesh.rest.max(0) - mesh.rest.min(0)))
+
+
+def _pressed(mesh, seed, scale=1e-4, shift=0.0033):
+    rng = np.random.default_rng(seed)
+    x = mesh.rest.copy()
+    free = mesh.pinned == 0
+    x[free] += scale * rng.standard_normal((int(free.sum()), 3))
+    top = mesh.rest[:, 2] > mesh.rest[:, 2].mean()
+    x[top & free, 2] -= shift
+    return x
+
+
+@pytest.mark.parametrize("nx,max_frames", [(4, 3), (6, 4), (8, 2)])
+def test_batch_equals_solo_solves(fsim, ctx, nx, max_frames):
+    # two slabs pressed together: n_c ~ 50 (one-CTA reduced path), ~98
+    # (4-CTA cluster) and ~162 (cooperative kernel); five requests with their
+    # own actuation and start state, more than the batch's slots
+    mesh = I.two_slabs(nx, nx, 2, gap=0.004)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    reqs, solo = [], []
+    for k in range(5):
+        act = I.slab_actuation(mesh, seed=20 + k)
+        x0 = _pressed(mesh, seed=40 + k)
+        reqs.append((m, act.fiber, act.stretch, x0))
+        m.set_actuation(act.fiber, act.stretch)
+        rc, st = m.solve_frame(x_init=x0, precision=fsim.MIXED)
+        assert rc == 0
+        solo.append((m.positions(), st))
+    rc, xs, sts = fsim.solve_batch(ctx, reqs, max_frames=max_frames)
+    assert rc == 0
+    diag = _diag(mesh)
+    paths = np.zeros(4, dtype=int)
+    for (xo, so), x, st in zip(solo, xs, sts):
+        assert st["status"] == 0
+        assert abs(st["iterations"] - so["iterations"]) <= 2, (st["iterations"], so["iterations"])
+        assert np.abs(x - xo).max() <= 1e-6 * diag
+        assert st["contacts"] > 0
+        paths += np.array(st["reduced_steps"])
+    # the batch really took the reduced-system path of this contact size
+    want = {4: fsim.REDUCED_ONE_CTA, 6: fsim.REDUCED_CLUSTER, 8: fsim.REDUCED_COOPERATIVE}[nx]
+    assert paths[want] > 0, paths
+
+
+@pytest.mark.slow
+def test_batch_face_frames_match_the_oracle(fsim, ctx):
+    gold = dict(np.load(GOLD))
+    mesh = I.face_shell()
+    field = I.bump_field(mesh, seed=int(gold["field_seed"]))
+    coeffs = I.keyframe_coeffs(seed=int(gold["seq_seed"]))
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    f20, f21 = gold["frames"].tolist()
+    a20 = I.bump_actuation(field, coeffs[f20])
+    a21 = I.bump_actuation(field, coeffs[f21])
+    # frame 20 from rest and frame 21 from the oracle's frame-20 result, in one batch
+    rc, xs, sts = fsim.solve_batch(ctx, [(m, a20.fiber, a20.stretch, None),
+                                         (m, a21.fiber, a21.stretch, gold["x0"])], max_frames=2)
+    assert rc == 0
+    diag = _diag(mesh)
+    for k, (x, st) in enumerate(zip(xs, sts)):
+        assert st["status"] == 0 and st["n_c_max"] > 0
+        err = np.abs(x - gold[f"x{k}"]).max() / diag
+        assert err <= 1e-6, (k, err)
+        assert abs(st["iterations"] - int(gold[f"iterations{k}"])) <= 2
+
+
+def test_batch_argument_errors(fsim, ctx):
+    mesh = I.two_slabs(3, 3, 2)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    act = I.slab_actuation(mesh, seed=1)
+    rc, _, _ = fsim.solve_batch(ctx, [(m, act.fiber, act.stretch, None)], max_frames=0)
+    assert rc == fsim.FSIM_EINVAL
+    bad = act.stretch.copy()
+    bad[0] = -1.0
+    rc, _, sts = fsim.solve_batch(ctx, [(m, act.fiber, bad, None),
+                                        (m, act.fiber, act.stretch, None)], max_frames=2)
+    assert rc == fsim.FSIM_ENONFINITE
+    assert sts[0]["status"] == fsim.FSIM_ENONFINITE and sts[1]["status"] == 0
