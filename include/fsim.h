@@ -113,6 +113,11 @@ typedef struct {
                                e_b|^2, m(c) = (2 - c/eps) c/eps below
                                eps = 1e-3 |E_a|^2 |E_b|^2 (rest proxy edges),
                                1 above; 0 (default): plain b(d)              */
+  int32_t reduced_one_cta_max; /* mixed precision: the largest n_c whose reduced
+                               system one CTA solves; larger n_c up to 128 go
+                               to a 4-CTA cluster, beyond that to the
+                               cooperative kernel.  <= 0 selects 96 (the most
+                               one CTA's shared memory holds); a tuning knob */
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1
@@ -145,8 +150,9 @@ enum {
   FSIM_REDUCED_COOPERATIVE = 0, /* grid-wide blocked Cholesky (float64 form, and
                                    the mixed form for n_c > 128)                   */
   FSIM_REDUCED_NONE = 1,        /* mixed form, n_c = 0: dx2 = Sigma^-1 y2          */
-  FSIM_REDUCED_ONE_CTA = 2,     /* mixed form, 0 < n_c <= 96: one CTA              */
-  FSIM_REDUCED_CLUSTER = 3      /* mixed form, 96 < n_c <= 128: 4-CTA cluster      */
+  FSIM_REDUCED_ONE_CTA = 2,     /* mixed form, 0 < n_c <= reduced_one_cta_max
+                                   (96 by default): one CTA                       */
+  FSIM_REDUCED_CLUSTER = 3      /* mixed form, above that up to 128: 4-CTA cluster */
 };
 
 /* Fill *p with the defaults: weight_scale 1e3, kappa auto, tol_abs 1e-8,
@@ -392,10 +398,19 @@ typedef struct {
 #define FSIM_REQ_DEVICE 1
 
 typedef struct {
-  int32_t workers;          /* concurrent solves, 1..16                         */
-  int32_t reserved0;
-  int64_t mem_budget_bytes; /* cap on the bytes of all workspace slots; <= 0
-                               means no cap                                     */
+  int32_t workers;          /* concurrent solves (batch_frames < 2) or
+                               concurrent batches (batch_frames >= 2), 1..16   */
+  int32_t batch_frames;     /* 0 or 1: every request is its own solve on its own
+                               worker.  2..64: each worker runs a lock-step
+                               batch of up to this many frames of one mesh (as
+                               fsim_solve_batch), and at every iteration
+                               boundary takes the oldest queued requests of its
+                               mesh into the slots of finished frames; such a
+                               server accepts FSIM_MIXED requests of meshes
+                               using FSIM_SOLVER_WOODBURY (FSIM_EINVAL at
+                               submit otherwise)                              */
+  int64_t mem_budget_bytes; /* cap on the bytes of all workspace slots (and
+                               batches); <= 0 means no cap                     */
 } fsim_server_config;
 
 typedef struct {

@@ -24,11 +24,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <deque>
+#include <new>
 #include <vector>
 
 #include "kernels.h"
 #include "runtime.h"
+#include "batch.h"
 
 using namespace fsim;
 
@@ -56,7 +57,7 @@ constexpr double kKappaMaxRatio = 100.0;
 enum Phase { FREE = 0, INIT = 1, ITER = 2 };
 
 struct Frame {
-  int req = -1;
+  BatchReq br;
   Phase phase = FREE;
   fsim_frame_stats st{};
   double E = 0.0, gn = 0.0, tol = 0.0, kappa = 0.0, d_prev = INFINITY, scale = 1.0;
@@ -77,16 +78,20 @@ int dalloc_b(std::vector<void*>& allocs, T** p, size_t count) {
   return FSIM_OK;
 }
 
+}  // namespace
+
+namespace fsim {
+
 class Batch {
  public:
-  Batch(fsim_ctx_t ctx, MeshState& ms, int cap) : ctx_(ctx), ms_(ms), cap_(cap) {}
+  Batch(fsim_ctx_t ctx, MeshState& ms, int cap, cudaStream_t stream)
+      : ctx_(ctx), ms_(ms), cap_(cap), s_(stream) {}
   ~Batch() { release(); }
 
   int init() {
     const DevMesh& m0 = ms_.d;
     nr_ = ((3 * cap_ + 31) / 32) * 32;
     if (!batch_supported(m0, nr_)) return FSIM_EINVAL;
-    s_ = ctx_->stream;
     BCK(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
     for (auto& e : ev_) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     frames_.assign(cap_, Frame{});
@@ -101,6 +106,7 @@ class Batch {
       m = m0;
       size_t bytes = 0;
       BTRY(rt_alloc_workspace(ms_, m, allocs_, &bytes));
+      bytes_ += bytes + rt_reduced_bytes(std::min(std::max(m.n2, 1), 64));
       m.counters = counters_ + (size_t)kCounters * f;
       m.scal = scal_ + (size_t)kScal * f;
       m.col = f;
@@ -113,6 +119,7 @@ class Batch {
     BTRY(dalloc_b(allocs_, &yb_, (size_t)std::max(m0.n1, 1) * nr_));
     BTRY(dalloc_b(allocs_, &ub_, (size_t)std::max(m0.n2, 1) * nr_));
     BTRY(dalloc_b(allocs_, &bx_, nf * nr_));
+    bytes_ += sizeof(float) * (2 * nf + std::max(m0.n1, 1) + std::max(m0.n2, 1)) * nr_;
     BCK(cudaMemset(rb_, 0, sizeof(float) * nf * nr_));
     BCK(cudaMemset(bx_, 0, sizeof(float) * nf * nr_));
     BTRY(dalloc_b(allocs_, &tab_dev_, (size_t)cap_));
@@ -139,36 +146,41 @@ class Batch {
     return FSIM_OK;
   }
 
-  // Solve every request (all of this batch's mesh, mixed precision).
-  int run(int n_req, const fsim_request* reqs, double* const* x_out, fsim_frame_stats* stats) {
-    std::deque<int> pending;
-    for (int i = 0; i < n_req; ++i) pending.push_back(i);
-    reqs_ = reqs;
-    x_out_ = x_out;
-    stats_ = stats;
-    first_err_ = FSIM_OK;
+  size_t bytes() const { return bytes_; }
+
+  // Solve requests until `pull` has none left and every slot is free.  At
+  // every iteration boundary `pull` is asked for a request for each free
+  // slot; `done` receives each finished request (after its positions have
+  // reached x_host / x_out_dev) with its status and statistics.
+  int run(const BatchPull& pull, const BatchDone& done) {
+    done_ = &done;
     for (;;) {
-      // admit pending requests into free slots
       bool any_new = false;
-      for (int f = 0; f < cap_ && !pending.empty(); ++f) {
+      for (int f = 0; f < cap_; ++f) {
         if (frames_[f].phase != FREE) continue;
-        const int r = pending.front();
-        pending.pop_front();
-        const int rc = start_frame(f, r);
+        BatchReq br;
+        if (!pull(&br)) break;
+        frames_[f].br = br;
+        const int rc = start_frame(f);
         if (rc == FSIM_ECUDA) return rc;
-        if (rc != FSIM_OK) { finish_error(f, rc); continue; }
+        if (rc != FSIM_OK) { finish(f, rc, false); continue; }
         any_new = true;
       }
       if (any_new) BTRY(initial_state());
+      BTRY(notify());
       bool any_iter = false;
       for (auto& fr : frames_) any_iter |= fr.phase == ITER;
       if (!any_iter) {
-        if (pending.empty()) break;
+        bool any_busy = false;
+        for (auto& fr : frames_) any_busy |= fr.phase != FREE;
+        if (!any_busy && !any_new) break;
         continue;
       }
       BTRY(iterate());
+      BTRY(notify());
     }
-    return first_err_;
+    BCK(cudaStreamSynchronize(s_));
+    return notify();
   }
 
  private:
@@ -187,6 +199,7 @@ class Batch {
   void release() {
     if (s_) cudaStreamSynchronize(s_);
     if (s2_) cudaStreamSynchronize(s2_);
+    if (ev_done_) cudaEventDestroy(ev_done_);
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
     for (auto& e : ev_)
@@ -231,16 +244,19 @@ class Batch {
   int* cnt(int f) { return h_counters_ + (size_t)kCounters * f; }
   double* scl(int f) { return h_scal_ + (size_t)kScal * f; }
 
-  int start_frame(int f, int r) {
-    const fsim_request& q = reqs_[r];
+  int start_frame(int f) {
     Frame& fr = frames_[f];
+    const BatchReq br = fr.br;
     fr = Frame{};
-    fr.req = r;
+    fr.br = br;
+    const fsim_request& q = br.req;
     fr.st.alpha_min = 1.0;
     fr.kappa = ms_.kappa;
     DevMesh& m = tab_[f];
     const size_t n = (size_t)m.n, T = (size_t)m.T;
     const bool dev = (q.flags & FSIM_REQ_DEVICE) != 0;
+    if (q.mesh_id < 0 || rt_mesh(ctx_, q.mesh_id) != &ms_ || q.precision != FSIM_MIXED)
+      return FSIM_EINVAL;
     if (dev) {
       launch_actuation(s_, m.T, q.fiber, q.stretch, m.act, m.act_df);
     } else {
@@ -265,29 +281,31 @@ class Batch {
     return FSIM_OK;
   }
 
-  void finish(int f, int rc) {
+  // The frame's result is queued for copy-out; the request is reported to
+  // `done` at the next synchronisation (notify), when the copies are complete.
+  void finish(int f, int rc, bool copy = true) {
     Frame& fr = frames_[f];
     fr.st.status = rc;
-    fr.st.grad_norm = fr.gn;
-    fr.st.energy = fr.E;
-    fr.st.contacts = fr.npairs;
-    const fsim_request& q = reqs_[fr.req];
-    DevMesh& m = tab_[f];
-    const size_t bytes = sizeof(double) * 3 * (size_t)m.n;
-    if (q.x_out_dev) cudaMemcpyAsync(q.x_out_dev, m.x, bytes, cudaMemcpyDeviceToDevice, s_);
-    if (x_out_ && x_out_[fr.req]) cudaMemcpyAsync(x_out_[fr.req], m.x, bytes, cudaMemcpyDeviceToHost, s_);
-    if (stats_) stats_[fr.req] = fr.st;
-    if (rc != FSIM_OK && first_err_ == FSIM_OK) first_err_ = rc;
+    if (copy) {
+      fr.st.grad_norm = fr.gn;
+      fr.st.energy = fr.E;
+      fr.st.contacts = fr.npairs;
+      DevMesh& m = tab_[f];
+      const size_t bytes = sizeof(double) * 3 * (size_t)m.n;
+      if (fr.br.req.x_out_dev)
+        cudaMemcpyAsync(fr.br.req.x_out_dev, m.x, bytes, cudaMemcpyDeviceToDevice, s_);
+      if (fr.br.x_host) cudaMemcpyAsync(fr.br.x_host, m.x, bytes, cudaMemcpyDeviceToHost, s_);
+    }
+    finished_.push_back({fr.br.user, rc, fr.st});
     fr.phase = FREE;
-    fr.req = -1;
   }
-  void finish_error(int f, int rc) {
-    Frame& fr = frames_[f];
-    fr.st.status = rc;
-    if (stats_) stats_[fr.req] = fr.st;
-    if (first_err_ == FSIM_OK) first_err_ = rc;
-    fr.phase = FREE;
-    fr.req = -1;
+
+  int notify() {
+    if (finished_.empty()) return FSIM_OK;
+    BCK(cudaStreamSynchronize(s_));
+    for (const auto& d : finished_) (*done_)(d.user, d.rc, d.st);
+    finished_.clear();
+    return FSIM_OK;
   }
 
   void adapt_kappa(Frame& fr, double d_min, double* Eb) {
@@ -404,7 +422,7 @@ class Batch {
       if (act[f]) {
         Frame& fr = frames_[f];
         fr.st.sum_nc3 += (double)fr.nc * fr.nc * fr.nc;
-        fr.st.reduced_steps[reduced_path(fr.nc, FSIM_MIXED)]++;
+        fr.st.reduced_steps[reduced_path(fr.nc, FSIM_MIXED, tab_[f].one_cta_max)]++;
       }
     }
     BCK(cudaMemcpyAsync(args_dev_, h_args_, args_bytes_ * cap_, cudaMemcpyHostToDevice, s_));
@@ -508,13 +526,33 @@ class Batch {
   const int* cols_dev_ = nullptr;
   double** x1s_dev_ = nullptr;
   double** h_x1s_ = nullptr;
-  const fsim_request* reqs_ = nullptr;
-  double* const* x_out_ = nullptr;
-  fsim_frame_stats* stats_ = nullptr;
-  int first_err_ = FSIM_OK;
+  struct Finished {
+    void* user;
+    int rc;
+    fsim_frame_stats st;
+  };
+  std::vector<Finished> finished_;
+  const BatchDone* done_ = nullptr;
+  cudaEvent_t ev_done_ = nullptr;
+  size_t bytes_ = 0;
 };
 
-}  // namespace
+Batch* batch_create(fsim_ctx_t ctx, MeshState& ms, int cap, cudaStream_t stream, int* status) {
+  auto* b = new (std::nothrow) Batch(ctx, ms, cap, stream);
+  if (!b) { *status = FSIM_ENOMEM; return nullptr; }
+  *status = b->init();
+  if (*status != FSIM_OK) { delete b; return nullptr; }
+  return b;
+}
+void batch_destroy(Batch* b) { delete b; }
+size_t batch_bytes(const Batch* b) { return b ? b->bytes() : 0; }
+int batch_run(Batch* b, const BatchPull& pull, const BatchDone& done) { return b->run(pull, done); }
+bool batch_servable(const MeshState& ms, const fsim_request& q) {
+  return ms.prefactored && q.precision == FSIM_MIXED && ms.p.solver == FSIM_SOLVER_WOODBURY &&
+         batch_supported(ms.d, 32);
+}
+
+}  // namespace fsim
 
 extern "C" fsim_status fsim_solve_batch(fsim_ctx_t ctx, int32_t n_req, const fsim_request* reqs,
                                         int32_t max_frames, double* const* x_out,
@@ -534,10 +572,25 @@ extern "C" fsim_status fsim_solve_batch(fsim_ctx_t ctx, int32_t n_req, const fsi
   }
   if (ms->p.solver != FSIM_SOLVER_WOODBURY) return FSIM_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FSIM_ECUDA;
-  Batch b(ctx, *ms, std::min<int>(max_frames, n_req));
-  int rc = b.init();
-  if (rc != FSIM_OK) return rc;
-  rc = b.run(n_req, reqs, x_out, stats);
+  int rc = FSIM_OK;
+  Batch* b = batch_create(ctx, *ms, std::min<int>(max_frames, n_req), ctx->stream, &rc);
+  if (!b) return rc;
+  int next = 0, first_err = FSIM_OK;
+  const BatchPull pull = [&](BatchReq* out) {
+    if (next >= n_req) return false;
+    out->req = reqs[next];
+    out->user = reinterpret_cast<void*>((intptr_t)next);
+    out->x_host = x_out ? x_out[next] : nullptr;
+    ++next;
+    return true;
+  };
+  const BatchDone done = [&](void* user, int st_rc, const fsim_frame_stats& st) {
+    const int i = (int)reinterpret_cast<intptr_t>(user);
+    if (stats) stats[i] = st;
+    if (st_rc != FSIM_OK && first_err == FSIM_OK) first_err = st_rc;
+  };
+  rc = batch_run(b, pull, done);
+  batch_destroy(b);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return FSIM_ECUDA;
-  return rc;
+  return rc != FSIM_OK ? rc : first_err;
 }

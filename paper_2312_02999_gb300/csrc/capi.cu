@@ -427,7 +427,7 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     } else {
       // one graph per precision and reduced-system path (n_c decides the path)
       const bool schur = p.solver == FSIM_SOLVER_SCHUR;
-      const int gkey = 8 * prec + (schur ? 4 : reduced_path(nc, prec));
+      const int gkey = 8 * prec + (schur ? 4 : reduced_path(nc, prec, m.one_cta_max));
       TRY(with_graph(ex, m, graph_slot(m, 0, 6, m.g, gkey), m.g, gkey, m.red_gen, [&]() -> int {
         CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
         CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone, schur, nc));
@@ -435,7 +435,7 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
       }));
     }
     st.sum_nc3 += (double)nc * nc * nc;
-    if (p.solver == FSIM_SOLVER_WOODBURY) st.reduced_steps[reduced_path(nc, prec)]++;
+    if (p.solver == FSIM_SOLVER_WOODBURY) st.reduced_steps[reduced_path(nc, prec, m.one_cta_max)]++;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
     TRY(with_graph(ex, m, graph_slot(m, 10, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
@@ -498,6 +498,7 @@ int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allo
   return alloc_workspace(ms, m, allocs, bytes);
 }
 int rt_ensure_reduced(const Exec& ex, DevMesh& m, int nc) { return ensure_reduced(ex, m, nc); }
+size_t rt_reduced_bytes(int nc_cap) { return reduced_bytes(nc_cap); }
 int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                    bool init_is_dev, int precision, fsim_frame_stats* stats) {
   return solve_frame_impl(ex, ms, m, x_init, init_is_dev, precision, stats);
@@ -832,6 +833,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
     CK(cudaStreamSynchronize(s));
   }
   m.skin = p->skin > 0.0 ? p->skin : std::max(10.0 * p->dhat, 0.25 * ms.mean_edge);
+  m.one_cta_max = p->reduced_one_cta_max > 0 ? std::min(p->reduced_one_cta_max, 96) : 96;
   m.ee_moll = p->ee_mollifier ? 1 : 0;
   m.cap_act = p->active_capacity > 0 ? p->active_capacity
                                      : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));
@@ -1119,7 +1121,8 @@ fsim_status fsim_eval_global_step(fsim_ctx_t ctx, int mesh_id, const double* x, 
   if (ctx->h_counters[6]) return FSIM_ENOT_SPD;
   CK(cudaMemcpy(dx_out, ms->dxtmp, sizeof(double) * 3 * (size_t)m.n, cudaMemcpyDeviceToHost));
   if (path_out)
-    *path_out = ms->p.solver == FSIM_SOLVER_WOODBURY ? reduced_path(nc, precision) : FSIM_REDUCED_UNUSED;
+    *path_out = ms->p.solver == FSIM_SOLVER_WOODBURY ? reduced_path(nc, precision, m.one_cta_max)
+                                                     : FSIM_REDUCED_UNUSED;
   return FSIM_OK;
 }
 

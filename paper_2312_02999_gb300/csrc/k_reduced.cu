@@ -76,6 +76,8 @@ struct RedArgs {
   int* info;
   int small_lim;        // n_c handled by the one-CTA path (0: none)
   int active;           // lock-step batches: the frame takes part in the launch
+  int one_cta_max;      // largest n_c of the one-CTA path (float32 factors); the
+                        // 4-CTA cluster takes n_c up to kClusNc above it
   FT* spk;              // one-CTA path: L_s packed, diagonal blocks inverted
 };
 
@@ -957,7 +959,7 @@ __device__ __forceinline__ void k_small_v_body(RedArgs<float> a) {
   extern __shared__ float smem_f[];
   __shared__ double red[kSW + 1];
   const int nc = *a.nc_dev;
-  if (nc == 0 || nc > kSmallNc) return;
+  if (nc == 0 || nc > a.one_cta_max) return;
   red_layout(a, nc);
   const int n3 = 3 * nc;
   const int tid = threadIdx.x;
@@ -1062,7 +1064,7 @@ __device__ __forceinline__ void k_clus_v_body(RedArgs<float> a) {
   __shared__ int loff[kClusRowsMax];
   __shared__ double red[kSW + 1];
   const int nc = *a.nc_dev;
-  if (nc <= kSmallNc || nc > kClusNc) return;       // uniform over the cluster
+  if (nc <= a.one_cta_max || nc > kClusNc) return;  // uniform over the cluster
   red_layout(a, nc);
   const int n3 = 3 * nc, nblk = (n3 + 31) / 32;
   const int rank = (int)cl.block_rank();
@@ -1442,6 +1444,7 @@ RedArgs<FT> make_args(const DevMesh& m, const double* u, const FT* y2, double* z
   a.u = u; a.y2 = y2; a.z2 = z2;
   a.info = info;
   a.small_lim = std::is_same<FT, float>::value ? kClusNc : 0;
+  a.one_cta_max = std::min(m.one_cta_max, kSmallNc);
   return a;
 }
 
@@ -1484,7 +1487,8 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
       return cudaGetLastError();
     }
     const bool known = nc_host > 0 && nc_host <= kClusNc;
-    const bool want_small = !known || nc_host <= kSmallNc, want_clus = !known || nc_host > kSmallNc;
+    const bool want_small = !known || nc_host <= a.one_cta_max;
+    const bool want_clus = !known || nc_host > a.one_cta_max;
     if (prepared) {       // S, L_s, lists, X and N came from reduced_prepare
       if (cudaStreamWaitEvent(s, m.ev_join, 0) != cudaSuccess) return cudaGetLastError();
       k_small_x<1><<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
@@ -1530,10 +1534,10 @@ int64_t reduced_workspace_elems(int nc) {
 // Most float64 refinement steps of a float32 reduced factor (see step 7).
 constexpr int kMixedRefineSteps = 12;
 
-int reduced_path(int nc_host, int precision) {
+int reduced_path(int nc_host, int precision, int one_cta_max) {
   if (precision == 0 || nc_host < 0 || nc_host > kClusNc) return 0;   // cooperative kernel
   if (nc_host == 0) return 1;
-  return nc_host <= kSmallNc ? 2 : 3;
+  return nc_host <= std::min(one_cta_max, kSmallNc) ? 2 : 3;
 }
 
 cudaError_t reduced_solve(cudaStream_t s, const DevMesh& m, const double* u, const void* y2,
@@ -1704,8 +1708,8 @@ cudaError_t reduced_solve_b(cudaStream_t s, const void* args_dev, const void* ar
   bool any_small = false, any_clus = false;
   for (int f = 0; f < nb; ++f) {
     if (!H[f].active) continue;
-    any_small |= nc_host[f] > 0 && nc_host[f] <= kSmallNc;
-    any_clus |= nc_host[f] > kSmallNc && nc_host[f] <= kClusNc;
+    any_small |= nc_host[f] > 0 && nc_host[f] <= H[f].one_cta_max;
+    any_clus |= nc_host[f] > H[f].one_cta_max && nc_host[f] <= kClusNc;
   }
   ProfScope ps(PROF_CHOL, s);
   k_small_x_b<1><<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s>>>(A);

@@ -220,6 +220,7 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
          const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr) {
   extern __shared__ float bj[];                    // ns x 32
   __shared__ __align__(16) float Zs[kMrK][32];
+  __shared__ float part[8][32][33];
   const int4 it = items[blockIdx.x];
   const int J = it.x, r0 = it.y, rn = it.z;
   const int cc = blockIdx.y * kMrCols;
@@ -230,7 +231,11 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
     bj[e] = b[(size_t)(c0 + e / kMrCols) * nr + cc + (e % kMrCols)];
   // rows of the diagonal block only need k <= row (L_JJ^-1 is lower triangular)
   const int kend = r0 < ns ? min(ns, r0 + rn) : ns;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  // warp w sums the terms k = w (mod 8) for all 32 rows (lane = column), so
+  // each thread keeps 32 independent accumulators
+  float acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.f;
   for (int k0 = 0; k0 < kend; k0 += kMrK) {
     __syncthreads();
     for (int e = tid; e < kMrK * 32; e += blockDim.x) {
@@ -239,32 +244,45 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
     }
     __syncthreads();
     const int kn = min(kMrK, kend - k0);
-    for (int kk = 0; kk < kn; ++kk) {
+    for (int kk = wid; kk < kn; kk += 8) {
       const float bk = bj[(k0 + kk) * kMrCols + lane];
-      const float4 z = *reinterpret_cast<const float4*>(&Zs[kk][4 * wid]);
-      acc[0] += z.x * bk; acc[1] += z.y * bk; acc[2] += z.z * bk; acc[3] += z.w * bk;
+      const float4* zr = reinterpret_cast<const float4*>(&Zs[kk][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < 8; ++q4) {
+        const float4 z = zr[q4];
+        acc[4 * q4] += z.x * bk; acc[4 * q4 + 1] += z.y * bk;
+        acc[4 * q4 + 2] += z.z * bk; acc[4 * q4 + 3] += z.w * bk;
+      }
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int rr = 4 * wid + q;
+  for (int q = 0; q < 32; ++q) part[wid][q][lane] = acc[q];
+  __syncthreads();
+  for (int e = tid; e < 32 * kMrCols; e += blockDim.x) {
+    const int rr = e >> 5, j = e & 31;
     if (rr >= rn) continue;
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += part[w][rr][j];
     const int r = r0 + rr;
-    if (r < ns) y[(size_t)(c0 + r) * nr + cc + lane] = acc[q];
-    else atomicAdd(b + (size_t)rows[roff[J] + r - ns] * nr + cc + lane, -acc[q]);
+    if (r < ns) y[(size_t)(c0 + r) * nr + cc + j] = t;
+    else atomicAdd(b + (size_t)rows[roff[J] + r - ns] * nr + cc + j, -t);
   }
 }
 
 // x_J[k] = sum_{r >= k} Z_J[r][k] w[r], w = [y_J ; -x_R], columns k0 .. k0 + kn
-// (kn <= 8): warp c takes column k0 + c
+// (kn <= 8): warp w sums the rows r = w (mod 8) for all kn columns (lane =
+// right-hand-side column), then the 8 partial sums are added
 __global__ void __launch_bounds__(256)
 k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
          const int* __restrict__ nra, const int64_t* __restrict__ roff,
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
          const float* __restrict__ Z, const float* __restrict__ y, float* __restrict__ x, int nr) {
   constexpr int kRows = 256;
-  __shared__ float ws[kRows][32];
-  __shared__ float Zs[kBwdCols][kRows];
+  __shared__ __align__(16) float ws[kRows][32];
+  __shared__ __align__(16) float Zs[kRows][kBwdCols];
+  // the warps' partial sums reuse ws once the row loop is done
+  float (*part)[kBwdCols][33] = reinterpret_cast<float (*)[kBwdCols][33]>(&ws[0][0]);
   const int4 it = items[blockIdx.x];
   const int J = it.x, k0 = it.y, kn = it.z;
   const int cc = blockIdx.y * kMrCols;
@@ -272,7 +290,9 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
   const float* Zj = Z + zoff[J];
   const int* Rj = rows + roff[J];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float acc = 0.f;
+  float acc[kBwdCols];
+#pragma unroll
+  for (int c = 0; c < kBwdCols; ++c) acc[c] = 0.f;
   for (int rb = k0; rb < ld; rb += kRows) {
     const int rn = min(kRows, ld - rb);
     __syncthreads();
@@ -282,13 +302,30 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
     }
     for (int e = tid; e < kBwdCols * kRows; e += blockDim.x) {
       const int c = e / kRows, rr = e % kRows, r = rb + rr, k = k0 + c;
-      Zs[c][rr] = (c < kn && rr < rn && r >= k) ? Zj[(size_t)k * ld + r] : 0.f;
+      Zs[rr][c] = (c < kn && rr < rn && r >= k) ? Zj[(size_t)k * ld + r] : 0.f;
     }
     __syncthreads();
-    if (wid < kn)
-      for (int rr = 0; rr < rn; ++rr) acc += Zs[wid][rr] * ws[rr][lane];
+    for (int rr = wid; rr < rn; rr += 8) {
+      const float wv = ws[rr][lane];
+      const float4 z0 = *reinterpret_cast<const float4*>(&Zs[rr][0]);
+      const float4 z1 = *reinterpret_cast<const float4*>(&Zs[rr][4]);
+      acc[0] += z0.x * wv; acc[1] += z0.y * wv; acc[2] += z0.z * wv; acc[3] += z0.w * wv;
+      acc[4] += z1.x * wv; acc[5] += z1.y * wv; acc[6] += z1.z * wv; acc[7] += z1.w * wv;
+    }
   }
-  if (wid < kn) x[(size_t)(c0 + k0 + wid) * nr + cc + lane] = acc;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kBwdCols; ++c) part[wid][c][lane] = acc[c];
+  __syncthreads();
+  if (tid < kBwdCols * 32) {
+    const int c = tid >> 5;
+    if (c < kn) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w][c][lane];
+      x[(size_t)(c0 + k0 + c) * nr + cc + lane] = t;
+    }
+  }
 }
 
 // u = Sigma^-1 y2 for all columns: rows [32 blockIdx.x, +32), columns chunk blockIdx.y
@@ -598,7 +635,9 @@ bool batch_supported(const DevMesh& m, int nr) {
 }
 
 void set_solver_smem_limits(int max_bytes) {
-  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+  // k_fwd_mr: its staged right-hand sides (ns x 32 floats) beside 42 KB of
+  // static shared memory; batch_supported keeps ns x 128 B within 160 KB
+  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, 176 * 1024);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
   cudaFuncSetAttribute(k_bwd_chunk<double, 256>, a, max_bytes);

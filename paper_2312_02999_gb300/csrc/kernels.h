@@ -147,6 +147,7 @@ struct DevMesh {
   double kappa_f = 0.0;       // barrier stiffness of the frame
   double ls_scale = 1.0;      // line-search factor of the trial step
   int col = 0;                // frame's column block (3 columns) in multi-RHS buffers
+  int one_cta_max = 96;       // mixed reduced system: largest n_c on the one-CTA path
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------
@@ -199,7 +200,7 @@ cudaError_t global_step(cudaStream_t s, const DevMesh& m, const double* g, doubl
                         int* info_dev, int num_sms, bool alone, bool dense_schur = false,
                         int nc_host = -1);
 // Reduced-system path a global step takes for this n_c and precision (graph key).
-int reduced_path(int nc_host, int precision);
+int reduced_path(int nc_host, int precision, int one_cta_max);
 // Schur-only variant of the x2 block (k_schur.cu): z2 = Sigma-hat^-1 y2 with
 // Sigma-hat = Sigma (x) I_3 + B-check assembled densely and factored by
 // Cholesky (float64, or float32 + two float64 refinement steps).

@@ -60,6 +60,8 @@ struct Exec {
 int rt_alloc_workspace(const MeshState& ms, DevMesh& m, std::vector<void*>& allocs, size_t* bytes);
 // Grow the reduced-system buffers of workspace m to hold nc (synchronises ex.stream).
 int rt_ensure_reduced(const Exec& ex, DevMesh& m, int nc);
+// Device bytes of the reduced-system buffers sized for nc_cap.
+size_t rt_reduced_bytes(int nc_cap);
 // Algorithm 1 for one frame on workspace m; actuation must already be in m.act.
 int rt_solve_frame(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                    bool init_is_dev, int precision, fsim_frame_stats* stats);

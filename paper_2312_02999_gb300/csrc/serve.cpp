@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "admission.h"
+#include "batch.h"
 #include "runtime.h"
 
 using namespace fsim;
@@ -83,6 +84,7 @@ struct Worker {
 struct fsim_server_s {
   fsim_ctx_t ctx = nullptr;
   int n_workers = 1;
+  int batch_frames = 0;          // >= 2: workers run lock-step batches (batch.cu)
   int coop_ctas = 1;
   int64_t budget = 0;
   size_t used = 0;
@@ -286,6 +288,136 @@ void worker_main(fsim_server_s* sv, int wi) {
   }
 }
 
+// Batch worker: serves the queue with lock-step batches of up to
+// batch_frames frames of one mesh (continuous batching at iteration
+// granularity: at every iteration boundary the batch takes the oldest queued
+// requests of its mesh into the slots of finished frames).  A worker keeps
+// its batch while requests for that mesh arrive and rebuilds it for another
+// mesh when its own mesh has none queued.
+void batch_worker_main(fsim_server_s* sv, int wi) {
+  cudaSetDevice(sv->ctx->device);
+  Worker& w = sv->workers[wi];
+  Batch* b = nullptr;
+  int b_mesh = -1;
+  size_t b_bytes = 0;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  for (;;) {
+    while (!sv->stop && sv->queue.empty()) sv->cv.wait(lk);
+    if (sv->stop) break;
+    // the mesh of the oldest request; keep the current batch if it has work
+    int mesh = sv->queue.front()->mesh_id;
+    for (Job* j : sv->queue)
+      if (j->mesh_id == b_mesh) { mesh = b_mesh; break; }
+    if (mesh != b_mesh || b == nullptr) {
+      if (b) {
+        lk.unlock();
+        batch_destroy(b);
+        lk.lock();
+        sv->used -= std::min(sv->used, b_bytes);
+        b = nullptr;
+        b_bytes = 0;
+        b_mesh = -1;
+      }
+      MeshState& ms = *rt_mesh(sv->ctx, mesh);
+      const size_t per = slot_need(ms);
+      int cap = sv->batch_frames;
+      if (sv->budget > 0) {
+        const size_t room = (size_t)sv->budget > sv->used ? (size_t)sv->budget - sv->used : 0;
+        cap = std::min<int>(cap, (int)(room / std::max<size_t>(per, 1)));
+      }
+      int rc = cap >= 1 ? FSIM_OK : FSIM_ENOMEM;
+      if (rc == FSIM_OK) {
+        sv->used += (size_t)cap * per;          // reserved while the batch is built
+        lk.unlock();
+        b = batch_create(sv->ctx, ms, cap, w.stream, &rc);
+        lk.lock();
+        sv->used -= std::min(sv->used, (size_t)cap * per);
+        if (b) {
+          b_bytes = batch_bytes(b);
+          sv->used += b_bytes;
+          b_mesh = mesh;
+        }
+      }
+      if (!b) {     // the oldest request of this mesh cannot be served
+        for (size_t k = 0; k < sv->queue.size(); ++k) {
+          Job* J = sv->queue[k];
+          if (J->mesh_id != mesh) continue;
+          sv->queue.erase(sv->queue.begin() + k);
+          J->started = true;
+          J->t_start = J->t_end = Clock::now();
+          J->status = J->st.status = rc;
+          J->done = true;
+          sv->completed++;
+          break;
+        }
+        sv->cv.notify_all();
+        continue;
+      }
+    }
+    sv->running++;
+    sv->peak_running = std::max(sv->peak_running, sv->running);
+    const int64_t n = rt_mesh(sv->ctx, b_mesh)->d.n;
+    const BatchPull pull = [&](BatchReq* out) {
+      std::lock_guard<std::mutex> g(sv->mu);
+      for (size_t k = 0; k < sv->queue.size(); ++k) {
+        Job* J = sv->queue[k];
+        if (J->mesh_id != b_mesh) continue;
+        sv->queue.erase(sv->queue.begin() + k);
+        J->started = true;
+        J->t_start = Clock::now();
+        fsim_request q{};
+        q.mesh_id = J->mesh_id;
+        q.precision = J->precision;
+        q.x_out_dev = J->x_out_dev;
+        if (J->device) {
+          q.fiber = J->fiber_dev;
+          q.stretch = J->stretch_dev;
+          q.x_init = J->x_init_dev;
+          q.flags = FSIM_REQ_DEVICE;
+          out->x_host = nullptr;
+        } else {
+          q.fiber = J->fiber.data();
+          q.stretch = J->stretch.data();
+          q.x_init = J->has_x ? J->x_init.data() : nullptr;
+          J->x_out.resize(3 * (size_t)n);
+          out->x_host = J->x_out.data();
+        }
+        out->req = q;
+        out->user = J;
+        return true;
+      }
+      return false;
+    };
+    const BatchDone done = [&](void* user, int rc, const fsim_frame_stats& st) {
+      std::lock_guard<std::mutex> g(sv->mu);
+      Job* J = static_cast<Job*>(user);
+      J->st = st;
+      J->status = J->st.status = rc;
+      J->t_end = Clock::now();
+      J->done = true;
+      sv->completed++;
+      sv->cv.notify_all();
+    };
+    lk.unlock();
+    const int rc = batch_run(b, pull, done);
+    lk.lock();
+    sv->running--;
+    if (rc == FSIM_ECUDA) {      // a failed batch is not reused
+      lk.unlock();
+      batch_destroy(b);
+      lk.lock();
+      sv->used -= std::min(sv->used, b_bytes);
+      b = nullptr;
+      b_mesh = -1;
+      b_bytes = 0;
+    }
+  }
+  lk.unlock();
+  if (b) batch_destroy(b);
+  lk.lock();
+  sv->used -= std::min(sv->used, b_bytes);
+}
+
 bool actuation_ok(const double* fiber, const double* stretch, int64_t T) {
   for (int64_t t = 0; t < T; ++t) {
     const double a = stretch[t];
@@ -301,13 +433,16 @@ bool actuation_ok(const double* fiber, const double* stretch, int64_t T) {
 extern "C" {
 
 fsim_status fsim_server_create(fsim_ctx_t ctx, const fsim_server_config* cfg, fsim_server_t* out) {
-  if (!ctx || !cfg || !out || cfg->workers < 1 || cfg->workers > 16) return FSIM_EINVAL;
+  if (!ctx || !cfg || !out || cfg->workers < 1 || cfg->workers > 16 || cfg->batch_frames < 0 ||
+      cfg->batch_frames > 64)
+    return FSIM_EINVAL;
   *out = nullptr;
   cudaSetDevice(ctx->device);
   auto* sv = new (std::nothrow) fsim_server_s();
   if (!sv) return FSIM_ENOMEM;
   sv->ctx = ctx;
   sv->n_workers = cfg->workers;
+  sv->batch_frames = cfg->batch_frames;
   sv->coop_ctas = std::max(1, ctx->num_sms / cfg->workers);
   sv->budget = cfg->mem_budget_bytes;
   sv->workers.resize(cfg->workers);
@@ -328,7 +463,8 @@ fsim_status fsim_server_create(fsim_ctx_t ctx, const fsim_server_config* cfg, fs
       return FSIM_ENOMEM;
     }
   }
-  for (int i = 0; i < cfg->workers; ++i) sv->workers[i].th = std::thread(worker_main, sv, i);
+  for (int i = 0; i < cfg->workers; ++i)
+    sv->workers[i].th = std::thread(sv->batch_frames >= 2 ? batch_worker_main : worker_main, sv, i);
   *out = sv;
   return FSIM_OK;
 }
@@ -342,6 +478,9 @@ fsim_status fsim_server_submit(fsim_server_t sv, const fsim_request* req, int64_
   if (!req->fiber || !req->stretch || (req->flags & ~FSIM_REQ_DEVICE)) return FSIM_EINVAL;
   // a request whose workspace alone exceeds the budget could never start
   if (sv->budget > 0 && slot_need(*ms) > (size_t)sv->budget) return FSIM_ENOMEM;
+  // a batch server serves what the lock-step batches can (mixed precision,
+  // Woodbury global step)
+  if (sv->batch_frames >= 2 && !batch_servable(*ms, *req)) return FSIM_EINVAL;
   const int64_t T = ms->d.T, n = ms->d.n;
   auto J = std::make_unique<Job>();
   J->mesh_id = req->mesh_id;

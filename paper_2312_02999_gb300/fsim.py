@@ -51,7 +51,7 @@ class Params(C.Structure):
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
                 ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
                 ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double), ("adaptive_kappa", C.c_int32),
-                ("ee_mollifier", C.c_int32)]
+                ("ee_mollifier", C.c_int32), ("reduced_one_cta_max", C.c_int32)]
 
 
 class FrameStats(C.Structure):
@@ -90,7 +90,7 @@ class Request(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("workers", C.c_int32), ("reserved0", C.c_int32), ("mem_budget_bytes", C.c_int64)]
+    _fields_ = [("workers", C.c_int32), ("batch_frames", C.c_int32), ("mem_budget_bytes", C.c_int64)]
 
 
 class ServerInfo(C.Structure):
@@ -402,10 +402,11 @@ class Server:
     """Continuous-batching request server (fsim_server_*): `workers` frame
     solves run at once, each on its own CUDA stream and workspace slot."""
 
-    def __init__(self, ctx: "Context", workers: int = 4, mem_budget_bytes: int = 0):
+    def __init__(self, ctx: "Context", workers: int = 4, mem_budget_bytes: int = 0,
+                 batch_frames: int = 0):
         self.ctx = ctx
         self.lib = ctx.lib
-        cfg = ServerConfig(int(workers), 0, int(mem_budget_bytes))
+        cfg = ServerConfig(int(workers), int(batch_frames), int(mem_budget_bytes))
         h = _P()
         _chk(self.lib.fsim_server_create(ctx.h, C.byref(cfg), C.byref(h)), "fsim_server_create")
         self.h = h

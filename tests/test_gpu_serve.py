@@ -135,3 +135,29 @@ def test_server_rejects_bad_requests(setup):
         assert e.value.status == fsim.FSIM_ENOT_READY
     finally:
         raw.close()
+
+
+def test_batch_server_results_match_solo_solves(setup):
+    # batch workers: lock-step batches of up to 3 frames per mesh; the six
+    # mixed requests of each mesh pass through three slots, so later requests
+    # are admitted into the slots of finished frames at iteration boundaries
+    fsim, ctx, meshes = setup
+    reqs = [r for r in _requests(meshes) if r[3] == 1] * 2
+    solo = [_alone(fsim, meshes, r) for r in reqs]
+    with fsim.Server(ctx, workers=2, batch_frames=3) as srv:
+        tickets = [srv.submit(meshes[mi][1], act.fiber, act.stretch, x0, prec)
+                   for (mi, act, x0, prec) in reqs]
+        outs = [srv.wait(t) for t in tickets]
+        info = srv.info()
+        # a batch server serves the mixed precision only
+        mesh, m, acts = meshes[0]
+        with pytest.raises(fsim.FsimError) as e:
+            srv.submit(m, acts[0].fiber, acts[0].stretch, None, fsim.FP64)
+        assert e.value.status == fsim.FSIM_EINVAL
+    assert info["completed"] == len(reqs) and info["queued"] == 0
+    for (mi, act, x0, prec), (rc0, x_solo, st0), (rc, x, st, lat, q) in zip(reqs, solo, outs):
+        mesh = meshes[mi][0]
+        assert rc == 0 and rc0 == 0
+        assert abs(st["iterations"] - st0["iterations"]) <= 2
+        assert np.abs(x - x_solo).max() <= _tol(mesh, prec)
+        assert lat >= q >= 0.0
