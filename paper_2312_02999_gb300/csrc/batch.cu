@@ -111,6 +111,11 @@ class Batch {
       m.scal = scal_ + (size_t)kScal * f;
       m.col = f;
       m.active = 0;
+      // the reduced systems of a batch run in one launch per kernel, so one
+      // path for every 0 < n_c <= 128 (the 4-CTA clusters) keeps the one-CTA
+      // and cluster launches from running one after the other; a mesh whose
+      // reduced_one_cta_max was set keeps that split
+      if (ms_.p.reduced_one_cta_max <= 0) m.one_cta_max = 0;
       Exec ex = exec();
       BTRY(rt_ensure_reduced(ex, m, std::min(std::max(m.n2, 1), 64)));
     }

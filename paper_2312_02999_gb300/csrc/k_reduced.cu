@@ -1444,7 +1444,7 @@ RedArgs<FT> make_args(const DevMesh& m, const double* u, const FT* y2, double* z
   a.u = u; a.y2 = y2; a.z2 = z2;
   a.info = info;
   a.small_lim = std::is_same<FT, float>::value ? kClusNc : 0;
-  a.one_cta_max = std::min(m.one_cta_max, kSmallNc);
+  a.one_cta_max = std::max(0, std::min(m.one_cta_max, kSmallNc));
   return a;
 }
 
@@ -1746,7 +1746,8 @@ cudaError_t reduced_solve_b(cudaStream_t s, const void* args_dev, const void* ar
     count_launch();
     if (e != cudaSuccess) return e;
   }
-  const int zgrid = std::max(1, std::min(2 * std::max(1, num_sms) / nb, 64));
+  // float64 row products: enough warps per frame to keep the float64 pipes busy
+  const int zgrid = std::max(2, std::min(8 * std::max(1, num_sms) / nb, 64));
   k_z2_update_b<<<dim3(zgrid, nb), 256, 0, s>>>(A);
   count_launch();
   return cudaGetLastError();

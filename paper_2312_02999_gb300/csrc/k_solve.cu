@@ -213,47 +213,86 @@ __global__ void k_gemv3(int n2, const T* __restrict__ A, const T* __restrict__ y
 constexpr int kMrCols = 32;
 constexpr int kMrK = 64;           // factor rows / columns staged per step
 
+// The staged tiles are loaded with every load of a thread in flight at once
+// (register staging, fixed trip counts) and the next tile is fetched while
+// the current one is used: a staging loop that waited for one load per
+// iteration cost a memory latency per element row, which set the time of the
+// levels with the largest supernodes.
 __global__ void __launch_bounds__(256)
 k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
          const int* __restrict__ nra, const int64_t* __restrict__ roff,
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
          const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr) {
   extern __shared__ float bj[];                    // ns x 32
-  __shared__ __align__(16) float Zs[kMrK][32];
-  __shared__ float part[8][32][33];
+  __shared__ __align__(16) float Zs[2][kMrK][32];
+  __shared__ float part[8][32][32];                // warp partial sums (no padding needed:
+                                                   // lanes always index the last dimension)
   const int4 it = items[blockIdx.x];
   const int J = it.x, r0 = it.y, rn = it.z;
   const int cc = blockIdx.y * kMrCols;
   const int c0 = c0a[J], ns = nsa[J], ld = ns + nra[J];
   const float* Zj = Z + zoff[J];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int e = tid; e < ns * kMrCols; e += blockDim.x)
-    bj[e] = b[(size_t)(c0 + e / kMrCols) * nr + cc + (e % kMrCols)];
   // rows of the diagonal block only need k <= row (L_JJ^-1 is lower triangular)
   const int kend = r0 < ns ? min(ns, r0 + rn) : ns;
+  constexpr int kPer = kMrK * 32 / 256;            // Z elements per thread per tile
+  float zr[kPer];
+  auto load_z = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + 256 * i, kk = e >> 5, rr = e & 31, k = k0 + kk, r = r0 + rr;
+      zr[i] = (k < kend && rr < rn && (r >= ns || k <= r)) ? __ldg(Zj + (size_t)k * ld + r) : 0.f;
+    }
+  };
+  auto store_z = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + 256 * i;
+      Zs[buf][e >> 5][e & 31] = zr[i];
+    }
+  };
+  load_z(0);
+  {   // right-hand sides of the supernode's columns, 8 loads in flight per thread
+    const int tot = ns * kMrCols;
+    for (int e0 = 0; e0 < tot; e0 += 8 * 256) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = e0 + tid + 256 * i;
+        v[i] = e < tot ? b[(size_t)(c0 + e / kMrCols) * nr + cc + (e % kMrCols)] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = e0 + tid + 256 * i;
+        if (e < tot) bj[e] = v[i];
+      }
+    }
+  }
+  store_z(0);
+  __syncthreads();
   // warp w sums the terms k = w (mod 8) for all 32 rows (lane = column), so
   // each thread keeps 32 independent accumulators
   float acc[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+  int buf = 0;
   for (int k0 = 0; k0 < kend; k0 += kMrK) {
-    __syncthreads();
-    for (int e = tid; e < kMrK * 32; e += blockDim.x) {
-      const int kk = e >> 5, rr = e & 31, k = k0 + kk, r = r0 + rr;
-      Zs[kk][rr] = (k < kend && rr < rn && (r >= ns || k <= r)) ? Zj[(size_t)k * ld + r] : 0.f;
-    }
-    __syncthreads();
+    const bool more = k0 + kMrK < kend;
+    if (more) load_z(k0 + kMrK);                   // next tile in flight
     const int kn = min(kMrK, kend - k0);
     for (int kk = wid; kk < kn; kk += 8) {
       const float bk = bj[(k0 + kk) * kMrCols + lane];
-      const float4* zr = reinterpret_cast<const float4*>(&Zs[kk][0]);
+      const float4* zp = reinterpret_cast<const float4*>(&Zs[buf][kk][0]);
 #pragma unroll
       for (int q4 = 0; q4 < 8; ++q4) {
-        const float4 z = zr[q4];
+        const float4 z = zp[q4];
         acc[4 * q4] += z.x * bk; acc[4 * q4 + 1] += z.y * bk;
         acc[4 * q4 + 2] += z.z * bk; acc[4 * q4 + 3] += z.w * bk;
       }
     }
+    if (more) store_z(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int q = 0; q < 32; ++q) part[wid][q][lane] = acc[q];
@@ -270,88 +309,145 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
   }
 }
 
-// x_J[k] = sum_{r >= k} Z_J[r][k] w[r], w = [y_J ; -x_R], columns k0 .. k0 + kn
-// (kn <= 8): warp w sums the rows r = w (mod 8) for all kn columns (lane =
-// right-hand-side column), then the 8 partial sums are added
+// x_J[k] += sum_r Z_J[r][k] w[r] over the item's rows r in [max(k0, rb0),
+// rb0 + kBwdRowSplit) (r >= k), w = [y_J ; -x_R], for up to 32 columns
+// k0 .. k0 + kn of Z_J and 32 right-hand-side columns; x_J is zeroed before
+// the pass and the row ranges of a column group add their partial sums
+// atomically.  w and the Z tile are staged in 64-row tiles (w once for all
+// kn columns, the next tile in flight while the current one is used); warp w
+// sums the rows r = w (mod 8) with 32 independent accumulators (one per
+// factor column, lane = right-hand-side column), then the 8 partial sums are
+// added
 __global__ void __launch_bounds__(256)
 k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
          const int* __restrict__ nra, const int64_t* __restrict__ roff,
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
          const float* __restrict__ Z, const float* __restrict__ y, float* __restrict__ x, int nr) {
-  constexpr int kRows = 256;
-  __shared__ __align__(16) float ws[kRows][32];
-  __shared__ __align__(16) float Zs[kRows][kBwdCols];
-  // the warps' partial sums reuse ws once the row loop is done
-  float (*part)[kBwdCols][33] = reinterpret_cast<float (*)[kBwdCols][33]>(&ws[0][0]);
+  constexpr int kRows = 64;
+  constexpr int kPer = kRows * 32 / 256;           // elements per thread per tile
+  __shared__ __align__(16) float buf[2 * 2 * kRows * 32 + 64];   // [2][ws | Zs]
   const int4 it = items[blockIdx.x];
   const int J = it.x, k0 = it.y, kn = it.z;
   const int cc = blockIdx.y * kMrCols;
-  const int c0 = c0a[J], ns = nsa[J], ld = ns + nra[J];
+  const int c0 = c0a[J], ns = nsa[J];
+  const int ld = min(ns + nra[J], it.w + kBwdRowSplit);   // end of this item's rows
+  const int ldz = ns + nra[J];                             // column stride of Z_J
   const float* Zj = Z + zoff[J];
   const int* Rj = rows + roff[J];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float acc[kBwdCols];
+  float wr[kPer], zr[kPer];
+  auto load = [&](int rb) {
 #pragma unroll
-  for (int c = 0; c < kBwdCols; ++c) acc[c] = 0.f;
-  for (int rb = k0; rb < ld; rb += kRows) {
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + 256 * i, rr = e >> 5, j = e & 31, r = rb + rr;
+      wr[i] = r < ld ? (r < ns ? y[(size_t)(c0 + r) * nr + cc + j]
+                               : -x[(size_t)__ldg(Rj + r - ns) * nr + cc + j])
+                     : 0.f;
+      // Z_J[r][k0 + j] (lower triangle of the diagonal block)
+      zr[i] = (r < ld && j < kn && r >= k0 + j) ? __ldg(Zj + (size_t)(k0 + j) * ldz + r) : 0.f;
+    }
+  };
+  auto store = [&](int bsel) {
+    float* ws = buf + bsel * 2 * kRows * 32;
+    float* zs = ws + kRows * 32;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + 256 * i;
+      ws[e] = wr[i];
+      zs[e] = zr[i];
+    }
+  };
+  float acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+  const int r_first = max(k0, it.w);
+  load(r_first);
+  store(0);
+  __syncthreads();
+  int bsel = 0;
+  for (int rb = r_first; rb < ld; rb += kRows) {
+    const bool more = rb + kRows < ld;
+    if (more) load(rb + kRows);
     const int rn = min(kRows, ld - rb);
-    __syncthreads();
-    for (int e = tid; e < rn * 32; e += blockDim.x) {
-      const int rr = e >> 5, j = e & 31, r = rb + rr;
-      ws[rr][j] = r < ns ? y[(size_t)(c0 + r) * nr + cc + j] : -x[(size_t)Rj[r - ns] * nr + cc + j];
-    }
-    for (int e = tid; e < kBwdCols * kRows; e += blockDim.x) {
-      const int c = e / kRows, rr = e % kRows, r = rb + rr, k = k0 + c;
-      Zs[rr][c] = (c < kn && rr < rn && r >= k) ? Zj[(size_t)k * ld + r] : 0.f;
-    }
-    __syncthreads();
+    const float* ws = buf + bsel * 2 * kRows * 32;
+    const float* zs = ws + kRows * 32;
     for (int rr = wid; rr < rn; rr += 8) {
-      const float wv = ws[rr][lane];
-      const float4 z0 = *reinterpret_cast<const float4*>(&Zs[rr][0]);
-      const float4 z1 = *reinterpret_cast<const float4*>(&Zs[rr][4]);
-      acc[0] += z0.x * wv; acc[1] += z0.y * wv; acc[2] += z0.z * wv; acc[3] += z0.w * wv;
-      acc[4] += z1.x * wv; acc[5] += z1.y * wv; acc[6] += z1.z * wv; acc[7] += z1.w * wv;
+      const float wv = ws[rr * 32 + lane];
+      const float4* zp = reinterpret_cast<const float4*>(zs + rr * 32);
+#pragma unroll
+      for (int q4 = 0; q4 < 8; ++q4) {
+        const float4 z = zp[q4];
+        acc[4 * q4] += z.x * wv; acc[4 * q4 + 1] += z.y * wv;
+        acc[4 * q4 + 2] += z.z * wv; acc[4 * q4 + 3] += z.w * wv;
+      }
     }
+    if (more) store(bsel ^ 1);
+    __syncthreads();
+    bsel ^= 1;
   }
-  __syncthreads();
+  // the warps' partial sums reuse the tiles: 8 x 32 x 32 floats fit the
+  // 2 x 2 x 64 x 32 of buf (lanes index the last dimension, no padding needed)
+  static_assert(8 * 32 * 32 <= 2 * 2 * kRows * 32, "partial sums must fit the tile buffer");
+  float (*part)[32][32] = reinterpret_cast<float (*)[32][32]>(buf);
 #pragma unroll
-  for (int c = 0; c < kBwdCols; ++c) part[wid][c][lane] = acc[c];
+  for (int c = 0; c < 32; ++c) part[wid][c][lane] = acc[c];
   __syncthreads();
-  if (tid < kBwdCols * 32) {
-    const int c = tid >> 5;
-    if (c < kn) {
-      float t = 0.f;
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    const int c = e >> 5, j = e & 31;
+    if (c >= kn) continue;
+    float t = 0.f;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) t += part[w][c][lane];
-      x[(size_t)(c0 + k0 + c) * nr + cc + lane] = t;
-    }
+    for (int w = 0; w < 8; ++w) t += part[w][c][j];
+    atomicAdd(x + (size_t)(c0 + k0 + c) * nr + cc + j, t);
   }
 }
 
-// u = Sigma^-1 y2 for all columns: rows [32 blockIdx.x, +32), columns chunk blockIdx.y
+// u = Sigma^-1 y2 for all columns: rows [32 blockIdx.x, +32), columns chunk
+// blockIdx.y; A and y2 tiles register-staged, the next tile in flight
 __global__ void __launch_bounds__(256)
 k_gemm_mr(int n2, const float* __restrict__ A, const float* __restrict__ yv, float* __restrict__ u,
           int nr) {
-  __shared__ __align__(16) float As[kMrK][32];
-  __shared__ float Ys[kMrK][32];
+  __shared__ __align__(16) float As[2][kMrK][32];
+  __shared__ float Ys[2][kMrK][32];
+  constexpr int kPer = kMrK * 32 / 256;
   const int i0 = blockIdx.x * 32, cc = blockIdx.y * kMrCols;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < n2; k0 += kMrK) {
-    __syncthreads();
-    for (int e = tid; e < kMrK * 32; e += blockDim.x) {
+  float ar[kPer], yr[kPer];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = tid + 256 * q;
       const int rr = e / kMrK, kk = e % kMrK, i = i0 + rr, k = k0 + kk;   // coalesced along k
-      As[kk][rr] = (i < n2 && k < n2) ? A[(size_t)i * n2 + k] : 0.f;
+      ar[q] = (i < n2 && k < n2) ? __ldg(A + (size_t)i * n2 + k) : 0.f;
       const int kk2 = e >> 5, j = e & 31, k2 = k0 + kk2;
-      Ys[kk2][j] = k2 < n2 ? yv[(size_t)k2 * nr + cc + j] : 0.f;
+      yr[q] = k2 < n2 ? yv[(size_t)k2 * nr + cc + j] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int bsel) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = tid + 256 * q;
+      As[bsel][e % kMrK][e / kMrK] = ar[q];
+      Ys[bsel][e >> 5][e & 31] = yr[q];
+    }
+  };
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  load(0);
+  store(0);
+  __syncthreads();
+  int bsel = 0;
+  for (int k0 = 0; k0 < n2; k0 += kMrK) {
+    const bool more = k0 + kMrK < n2;
+    if (more) load(k0 + kMrK);
     const int kn = min(kMrK, n2 - k0);
     for (int kk = 0; kk < kn; ++kk) {
-      const float yk = Ys[kk][lane];
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * wid]);
+      const float yk = Ys[bsel][kk][lane];
+      const float4 a = *reinterpret_cast<const float4*>(&As[bsel][kk][4 * wid]);
       acc[0] += a.x * yk; acc[1] += a.y * yk; acc[2] += a.z * yk; acc[3] += a.w * yk;
     }
+    if (more) store(bsel ^ 1);
+    __syncthreads();
+    bsel ^= 1;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -601,13 +697,16 @@ cudaError_t global_step_b(const BatchStep& bs) {
   }
   // the contact-free backward solve x1 = L1^-T (y1 - L21^T u) on the side
   // stream while the reduced systems are solved
+  // x1 rows of the backward solution accumulate atomically: zeroed first
+  if (n1 > 0 && cudaMemsetAsync(bs.bx, 0, sizeof(float) * (size_t)n1 * nr, s2) != cudaSuccess)
+    return cudaGetLastError();
   if (cudaEventRecord(bs.ev[2], s) != cudaSuccess || cudaStreamWaitEvent(s2, bs.ev[2], 0) != cudaSuccess)
     return cudaGetLastError();
   for (int l = m.n_levels - 1; l >= 0 && n1 > 0; --l) {
-    const int a = m.h_bwd_ptr[l], z = m.h_bwd_ptr[l + 1];
+    const int a = m.h_bwd32_ptr[l], z = m.h_bwd32_ptr[l + 1];
     if (z <= a) continue;
     ProfScope ps(PROF_TRSV_BWD, s2);
-    k_bwd_mr<<<dim3(z - a, chunks), 256, 0, s2>>>(m.bwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+    k_bwd_mr<<<dim3(z - a, chunks), 256, 0, s2>>>(m.bwd_items32 + a, m.sn_c0, m.sn_ns, m.sn_nr1,
                                                   m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.yb,
                                                   bs.bx, nr);
     count_launch();
@@ -635,9 +734,9 @@ bool batch_supported(const DevMesh& m, int nr) {
 }
 
 void set_solver_smem_limits(int max_bytes) {
-  // k_fwd_mr: its staged right-hand sides (ns x 32 floats) beside 42 KB of
+  // k_fwd_mr: its staged right-hand sides (ns x 32 floats) beside 48 KB of
   // static shared memory; batch_supported keeps ns x 128 B within 160 KB
-  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, 176 * 1024);
+  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, 170 * 1024);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
   cudaFuncSetAttribute(k_bwd_chunk<double, 256>, a, max_bytes);

@@ -75,6 +75,9 @@ struct DevMesh {
   int4* bwd_items = nullptr;  // (J, first column, columns, 0)
   int* h_fwd_ptr = nullptr;   // HOST (n_levels + 1)
   int* h_bwd_ptr = nullptr;   // HOST (n_levels + 1)
+  int4* bwd_items32 = nullptr;  // (J, first column, columns <= 32, first row) for the batched
+                                // solve: rows [first row, + kBwdRowSplit) of Z_J
+  int* h_bwd32_ptr = nullptr; // HOST (n_levels + 1)
   double* y1 = nullptr;       // n1*3 forward-solve scratch
   float* y1f = nullptr;
   double* Sinv = nullptr;     // n2 x n2 Schur-complement inverse (Sec. 3.2)
@@ -243,6 +246,9 @@ void launch_gnorm2(cudaStream_t s, const DevMesh& m, const double* g, double* pa
 int gnorm_blocks(int n);
 void launch_reset_pinned(cudaStream_t s, const DevMesh& m, double* x);
 void launch_check_finite(cudaStream_t s, int n, const double* v, int* flag);
+
+// rows of Z_J one batched backward work item covers
+constexpr int kBwdRowSplit = 256;
 
 // ---- lock-step batches -------------------------------------------------------
 // `tab` is a device array of nb DevMesh copies (frames of one mesh); m0 is a

@@ -51,14 +51,17 @@ def _pressed(mesh, seed, scale=1e-4, shift=0.0033):
     return x
 
 
-@pytest.mark.parametrize("nx,max_frames", [(4, 3), (6, 4), (8, 2)])
-def test_batch_equals_solo_solves(fsim, ctx, nx, max_frames):
-    # two slabs pressed together: n_c ~ 50 (one-CTA reduced path), ~98
-    # (4-CTA cluster) and ~162 (cooperative kernel); five requests with their
-    # own actuation and start state, more than the batch's slots
+@pytest.mark.parametrize("nx,max_frames,one_cta_max,path", [
+    (4, 3, 0, "CLUSTER"), (4, 3, 96, "ONE_CTA"), (6, 4, 0, "CLUSTER"), (8, 2, 0, "COOPERATIVE")])
+def test_batch_equals_solo_solves(fsim, ctx, nx, max_frames, one_cta_max, path):
+    # two slabs pressed together: n_c ~ 50, ~98 and ~162; five requests with
+    # their own actuation and start state, more than the batch's slots.  A
+    # batch solves every 0 < n_c <= 128 on the 4-CTA cluster path unless the
+    # mesh sets reduced_one_cta_max (then n_c up to it takes the one-CTA
+    # path); larger n_c take the cooperative kernel
     mesh = I.two_slabs(nx, nx, 2, gap=0.004)
     m = ctx.upload(mesh)
-    m.prefactor(fsim.params_for(mesh))
+    m.prefactor(fsim.params_for(mesh, reduced_one_cta_max=one_cta_max))
     reqs, solo = [], []
     for k in range(5):
         act = I.slab_actuation(mesh, seed=20 + k)
@@ -79,8 +82,7 @@ def test_batch_equals_solo_solves(fsim, ctx, nx, max_frames):
         assert st["contacts"] > 0
         paths += np.array(st["reduced_steps"])
     # the batch really took the reduced-system path of this contact size
-    want = {4: fsim.REDUCED_ONE_CTA, 6: fsim.REDUCED_CLUSTER, 8: fsim.REDUCED_COOPERATIVE}[nx]
-    assert paths[want] > 0, paths
+    assert paths[getattr(fsim, "REDUCED_" + path)] > 0, paths
 
 
 @pytest.mark.slow

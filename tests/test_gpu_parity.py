@@ -228,8 +228,8 @@ def test_global_step_matches_direct_solve(fsim, slab_small, prec, state, res_tol
 
 @pytest.mark.parametrize("state", ["mild", "stiff"])
 @pytest.mark.parametrize("nx,n_c,path,one_cta_max", [
-    (4, 50, "ONE_CTA", 0), (4, 50, "CLUSTER", 32), (6, 98, "CLUSTER", 0), (7, 128, "CLUSTER", 0),
-    (8, 162, "COOPERATIVE", 0)])
+    (4, 50, "ONE_CTA", 0), (4, 50, "CLUSTER", 32), (3, 32, "CLUSTER", 1), (6, 98, "CLUSTER", 0),
+    (7, 128, "CLUSTER", 0), (8, 162, "COOPERATIVE", 0)])
 def test_mixed_global_step_on_each_reduced_path(fsim, ctx, nx, n_c, path, one_cta_max, state):
     # Eq. 11 in the push-through form: the mixed form solves the reduced
     # system on one CTA (n_c <= 96), a 4-CTA cluster (96 < n_c <= 128) or
@@ -238,7 +238,8 @@ def test_mixed_global_step_on_each_reduced_path(fsim, ctx, nx, n_c, path, one_ct
     # (162 at nx = 8 in the stiff state; one vertex fewer in the mild one).
     # Each case asserts the path taken and compares dx element by element
     # with the oracle's direct solve of (H + B) dx = -g.  With
-    # reduced_one_cta_max = 32 the cluster path also serves n_c = 50.
+    # reduced_one_cta_max = 32 the cluster path also serves n_c = 50, and
+    # with 1 it serves n_c = 32 (3 row blocks for 4 CTAs: one owns none).
     mesh = I.two_slabs(nx, nx, 2, gap=0.004)
     act = I.slab_actuation(mesh, seed=11)
     m, pr = _pair(fsim, ctx, mesh, act, reduced_one_cta_max=one_cta_max)
