@@ -350,6 +350,31 @@ fsim_status fsim_ccd_noalloc(const double* s_dev, const double* ds_dev, int64_t 
                              double ccd_s, int32_t accd_max_iters, double* alpha_dev,
                              void* stream);
 
+/*
+ * Automatic collision region.  The paper takes the collision-aware region x2
+ * and its proxy surface from the user (Sec. 3.1, Fig. 2a) and names their
+ * automatic selection as future work (Sec. 5); this selects them from the
+ * rest geometry: a boundary vertex can take part in contact when another
+ * boundary vertex lies closer than `radius` at rest (float64 squared
+ * distance, strict) but more than `rings` surface edges away (two sides of
+ * a slit, two bodies across a gap).  The proxy is every boundary triangle
+ * (a tet face met once) whose three vertices can take part in contact and
+ * are not all pinned (pinned may be NULL); W is the selection of its
+ * vertices, so the result feeds fsim_mesh_upload as proxy_tris (local
+ * numbering) with W_rowptr = 0..Nv, W_col = proxy_verts, W_val = 1.
+ *   rest_xyz [3n], tets [4T] (ids in [0, n)), pinned [n] or NULL
+ *   proxy_tris [3 tris_cap] <- sorted triangles in proxy-vertex numbering
+ *   proxy_verts [verts_cap] <- proxy vertex ids (mesh numbering, increasing)
+ * *n_tris and *n_verts receive the counts; with both caps 0 only the counts
+ * are returned (call again with buffers that large).  Host only (no GPU).
+ * Errors: FSIM_EINVAL for bad sizes or ids, radius <= 0, rings < 0, or caps
+ * smaller than the counts.
+ */
+fsim_status fsim_select_region(const double* rest_xyz, int64_t n, const int32_t* tets, int64_t T,
+                               const uint8_t* pinned, double radius, int32_t rings,
+                               int32_t* proxy_tris, int64_t tris_cap, int64_t* n_tris,
+                               int32_t* proxy_verts, int64_t verts_cap, int64_t* n_verts);
+
 /* Sizes of a mesh (n, T, Ns, Nt, Ne, free / x1 / x2 vertex counts), the
  * scalar factor's stored entries and supernode / level counts, the bytes of
  * one per-solve workspace (what each request-server slot of this mesh

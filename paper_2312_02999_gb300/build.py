@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_local.cu", "k_contact.cu", "k_solve.cu", "k_reduced.cu", "k_pcg.cu",
-           "k_schur.cu", "batch.cu", "prefactor.cpp", "serve.cpp"]
-NO_FMA = {"k_contact.cu"}
+           "k_schur.cu", "batch.cu", "prefactor.cpp", "serve.cpp", "region.cpp"]
+NO_FMA = {"k_contact.cu", "region.cpp"}
 
 
 def _nvcc() -> str:
@@ -39,6 +39,8 @@ def _compile(src: str) -> str:
             flags += ["--fmad=false"]
     else:
         flags += ["-x", "c++"]
+        if src in NO_FMA:
+            flags += ["-Xcompiler", "-ffp-contract=off"]
     cmd = [_nvcc(), "-c", path, "-o", obj] + flags
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -147,6 +147,8 @@ _SIGS = {
                           C.POINTER(FrameStats)],
     "fsim_solve_batch": [_P, C.c_int32, C.POINTER(Request), C.c_int32, C.POINTER(_D),
                          C.POINTER(FrameStats)],
+    "fsim_select_region": [_D, C.c_int64, _I32, C.c_int64, _U8, C.c_double, C.c_int32, _I32,
+                           C.c_int64, _I64, _I32, C.c_int64, _I64],
 }
 
 PROF_CLASSES = ["local_step", "detect", "trsv_fwd", "trsv_bwd", "chol", "barrier", "ccd",
@@ -184,6 +186,10 @@ def _d(a):
 
 def _i32(a):
     return a.ctypes.data_as(_I32) if a is not None else None
+
+
+def _u8(a):
+    return a.ctypes.data_as(_U8) if a is not None else None
 
 
 def _chk(st, what):
@@ -532,3 +538,23 @@ def solve_batch_dev(ctx: "Context", mesh: "Mesh", fiber_ptrs, stretch_ptrs, x_in
     stats = (FrameStats * max(n, 1))()
     rc = ctx.lib.fsim_solve_batch(ctx.h, n, reqs, int(max_frames), None, stats)
     return int(rc), [stats[i].as_dict() for i in range(n)]
+
+
+def select_region(rest, tets, pinned, radius: float, rings: int):
+    """fsim_select_region: (proxy triangles in proxy-vertex numbering, proxy
+    vertex ids) of the automatically selected collision region (host only)."""
+    lib = load()
+    X = np.ascontiguousarray(rest, dtype=np.float64).reshape(-1)
+    tt = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1)
+    pn = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
+    nt, nv = C.c_int64(), C.c_int64()
+    n, T = X.size // 3, tt.size // 4
+    _chk(lib.fsim_select_region(_d(X), n, _i32(tt), T, _u8(pn) if pn is not None else None,
+                                float(radius), int(rings), None, 0, C.byref(nt), None, 0,
+                                C.byref(nv)), "fsim_select_region")
+    tris = np.empty((max(nt.value, 1), 3), dtype=np.int32)
+    verts = np.empty(max(nv.value, 1), dtype=np.int32)
+    _chk(lib.fsim_select_region(_d(X), n, _i32(tt), T, _u8(pn) if pn is not None else None,
+                                float(radius), int(rings), _i32(tris), nt.value, C.byref(nt),
+                                _i32(verts), nv.value, C.byref(nv)), "fsim_select_region")
+    return tris[: nt.value].copy(), verts[: nv.value].copy()
