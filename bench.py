@@ -61,9 +61,10 @@ def parse():
                     help="timed frames per stream of the float64 served leg")
     ap.add_argument("--quick", action="store_true",
                     help="skip the float64 served leg, the host-buffer leg and the low-latency leg")
-    ap.add_argument("--legs", choices=["all", "single", "compare", "cpu-frame", "configs"],
+    ap.add_argument("--legs", choices=["all", "single", "served", "compare", "cpu-frame", "configs"],
                     default="all",
-                    help="single: only the single-sequence legs (profiling runs); compare: "
+                    help="single: only the single-sequence legs (profiling runs); served: only "
+                         "the headline served leg (profiling runs); compare: "
                          "global step by Schur + Woodbury vs PD-preconditioned CG, at kappa and "
                          "10 kappa (the paper's solver comparison), float64; cpu-frame: one whole "
                          "oracle face frame on the host; configs: the batched (4 meshes) and "
@@ -569,6 +570,16 @@ def run_ours(args):
                 "streams": nstreams, "frames": frames_timed}
 
     results = {}
+    if args.legs == "served":
+        r = served(fsim.MIXED, True, S, args.batch_workers, args.batch_frames, K)
+        if rank == 0:
+            print(json.dumps({"partial": "headline served leg only",
+                              "value": whole_job_fps(world, S, K, r["total_ms"]),
+                              "latency_ms": {"p50": percentile(r["lat"], 50),
+                                             "p99": percentile(r["lat"], 99)},
+                              "gpu_launches": int(r["launches"])}), flush=True)
+        ctx.close()
+        return
     results["single_mixed"] = single(fsim.MIXED, profile=True)
     results["single_fp64"] = single(fsim.FP64, profile=False)
     if args.legs == "single":
