@@ -848,7 +848,10 @@ def run_configs(args):
                          "workers": workers, "batch_frames": bframes,
                          "frames_per_s": N / span, "latency_ms": {"p50": percentile(lats, 50),
                                                                   "p99": percentile(lats, 99)},
-                         "failed": len(bad)})
+                         "failed": len(bad),
+                         "status": {fsim.STATUS_NAMES.get(c, str(c)): int(n) for c, n in
+                                    zip(*np.unique([r[0] for r in res], return_counts=True))},
+                         "fp64_global_steps": int(sum(r[2]["fp64_steps"] for r in res))})
     out["served_8_meshes"] = {"meshes": [{"mesh": f"face_shell_{round(nt / 1000)}k", "n": me[0].n,
                                           "n2": int(me[2].info()["n2"]),
                                           "prefactor_s": round(me[3], 2)}

@@ -141,6 +141,11 @@ typedef struct {
   int64_t cg_iterations;  /* CG iterations of the frame (FSIM_SOLVER_PCG)       */
   int32_t reduced_steps[4]; /* global steps of the frame by the path that solved
                                the reduced system (index = FSIM_REDUCED_*)    */
+  int32_t fp64_steps;       /* FSIM_MIXED: global steps taken with the float64
+                               factors because a float32 factor of the reduced
+                               (or Schur) system lost positive definiteness:
+                               the failed step is redone in float64 and every
+                               later global step of the frame stays there   */
 } fsim_frame_stats;
 
 /* Path that solves the reduced contact system of Eq. 11 in one global step

@@ -63,7 +63,9 @@ struct Frame {
   double E = 0.0, gn = 0.0, tol = 0.0, kappa = 0.0, d_prev = INFINITY, scale = 1.0;
   int nc = 0;
   int64_t npairs = 0;
-  bool searching = false, accepted = false;
+  int trial = 0;            // line-search trials since the frame's last global step
+  bool redone = false;      // this iteration's step was redone in float64
+  bool fp64 = false;        // the frame's global steps use the float64 factors
 };
 
 template <typename T>
@@ -142,7 +144,8 @@ class Batch {
     std::vector<int> hc(cap_);
     for (int f = 0; f < cap_; ++f) hc[f] = 3 * f;
     BCK(cudaMemcpy(cols, hc.data(), sizeof(int) * cap_, cudaMemcpyHostToDevice));
-    BCK(cudaHostAlloc((void**)&h_tab_, sizeof(DevMesh) * cap_, cudaHostAllocDefault));
+    BCK(cudaHostAlloc((void**)&h_tab_, sizeof(DevMesh) * cap_ * kTabRing, cudaHostAllocDefault));
+    for (auto& e : ev_tab_) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     BCK(cudaHostAlloc((void**)&h_counters_, sizeof(int) * kCounters * cap_, cudaHostAllocDefault));
     BCK(cudaHostAlloc((void**)&h_scal_, sizeof(double) * kScal * cap_, cudaHostAllocDefault));
     BCK(cudaHostAlloc((void**)&h_x1s_, sizeof(double*) * cap_, cudaHostAllocDefault));
@@ -205,6 +208,8 @@ class Batch {
     if (s_) cudaStreamSynchronize(s_);
     if (s2_) cudaStreamSynchronize(s2_);
     if (ev_done_) cudaEventDestroy(ev_done_);
+    for (auto& e : ev_tab_)
+      if (e) cudaEventDestroy(e);
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
     for (auto& e : ev_)
@@ -228,14 +233,22 @@ class Batch {
   }
 
   // table upload with the active flags of `want` (per frame)
+  // (the host copy comes from a ring of pinned tables: an asynchronous copy
+  // reads its source when it runs, so a table is not rewritten before the
+  // copy that reads it has completed)
   int upload_table(const std::vector<char>& want) {
+    const int slot = tab_slot_;
+    tab_slot_ = (tab_slot_ + 1) % kTabRing;
+    BCK(cudaEventSynchronize(ev_tab_[slot]));
+    DevMesh* h = h_tab_ + (size_t)cap_ * slot;
     for (int f = 0; f < cap_; ++f) {
       tab_[f].active = want[f] ? 1 : 0;
       tab_[f].kappa_f = frames_[f].kappa;
       tab_[f].ls_scale = frames_[f].scale;
-      h_tab_[f] = tab_[f];
+      h[f] = tab_[f];
     }
-    BCK(cudaMemcpyAsync(tab_dev_, h_tab_, sizeof(DevMesh) * cap_, cudaMemcpyHostToDevice, s_));
+    BCK(cudaMemcpyAsync(tab_dev_, h, sizeof(DevMesh) * cap_, cudaMemcpyHostToDevice, s_));
+    BCK(cudaEventRecord(ev_tab_[slot], s_));
     return FSIM_OK;
   }
 
@@ -256,6 +269,7 @@ class Batch {
     fr.br = br;
     const fsim_request& q = br.req;
     fr.st.alpha_min = 1.0;
+    tab_[f].bar64 = 0;
     fr.kappa = ms_.kappa;
     DevMesh& m = tab_[f];
     const size_t n = (size_t)m.n, T = (size_t)m.T;
@@ -402,6 +416,32 @@ class Batch {
     return FSIM_OK;
   }
 
+  // The single-frame float64 global step (Eq. 8-11) and CCD bound of frame f
+  // on its own workspace, on the batch's stream.  With `hessian` (the frame's
+  // first float64 step) the frame's contact Hessian is first assembled again
+  // at x with float64 pair eigen-solves, as it is for the rest of the frame;
+  // x is evaluated again because the trial evaluation replaced its pair list.
+  int redo_fp64(int f, bool hessian) {
+    DevMesh& m = tab_[f];
+    const fsim_params& p = ms_.p;
+    if (hessian) {
+      m.bar64 = 1;
+      std::vector<char> one(cap_, 0);
+      one[f] = 1;
+      BTRY(evaluate(one, 0));
+      BTRY(read_back());
+      BTRY(gradient(one));
+    }
+    BCK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s_));
+    BCK(global_step(s_, m, m.g, m.dx, FSIM_FP64, m.counters + 6, ctx_->num_sms, false, false,
+                    frames_[f].nc));
+    launch_proxy(s_, m, m.dx, m.ds);
+    launch_ccd_reset(s_, m);
+    launch_ccd(s_, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
+    BCK(cudaGetLastError());
+    return FSIM_OK;
+  }
+
   int iterate() {
     const fsim_params& p = ms_.p;
     std::vector<char> act(cap_, 0);
@@ -417,17 +457,25 @@ class Batch {
     bool any = false;
     for (char a : act) any |= a != 0;
     if (!any) return FSIM_OK;
-    // global step of every active frame
-    BTRY(upload_table(act));
+    // global step of every active frame: the batched mixed-precision step for
+    // most, the single-frame float64 step for frames switched to float64
+    std::vector<char> gact(cap_, 0);
+    bool any_b = false;
+    for (int f = 0; f < cap_; ++f) {
+      gact[f] = act[f] && !frames_[f].fp64;
+      any_b |= gact[f] != 0;
+    }
+    BTRY(upload_table(gact));
     std::vector<int> nc_host(cap_, 0);
     for (int f = 0; f < cap_; ++f) {
-      reduced_args_fill(h_args_ + args_bytes_ * f, tab_[f], act[f]);
+      reduced_args_fill(h_args_ + args_bytes_ * f, tab_[f], gact[f]);
       h_x1s_[f] = tab_[f].r;
-      nc_host[f] = frames_[f].nc;
+      nc_host[f] = gact[f] ? frames_[f].nc : 0;
       if (act[f]) {
         Frame& fr = frames_[f];
         fr.st.sum_nc3 += (double)fr.nc * fr.nc * fr.nc;
-        fr.st.reduced_steps[reduced_path(fr.nc, FSIM_MIXED, tab_[f].one_cta_max)]++;
+        fr.st.reduced_steps[reduced_path(fr.nc, fr.fp64 ? FSIM_FP64 : FSIM_MIXED,
+                                         tab_[f].one_cta_max)]++;
       }
     }
     BCK(cudaMemcpyAsync(args_dev_, h_args_, args_bytes_ * cap_, cudaMemcpyHostToDevice, s_));
@@ -449,17 +497,28 @@ class Batch {
     bs.cols_dev = cols_dev_;
     bs.x1s_dev = x1s_dev_;
     bs.num_sms = ctx_->num_sms;
-    BCK(global_step_b(bs));
-    // CCD step bound of every active frame
-    launch_ccd_b(s_, tab_dev_, cap_, tab_[0], p.dhat, p.ccd_s, p.accd_max_iters);
-    BCK(cudaGetLastError());
+    if (any_b) {
+      BCK(global_step_b(bs));
+      // CCD step bound of every frame of the batched step
+      launch_ccd_b(s_, tab_dev_, cap_, tab_[0], p.dhat, p.ccd_s, p.accd_max_iters);
+      BCK(cudaGetLastError());
+    }
+    for (int f = 0; f < cap_; ++f)
+      if (act[f] && frames_[f].fp64) {
+        frames_[f].st.fp64_steps++;
+        BTRY(redo_fp64(f, false));
+      }
     // backtracking line searches, all frames' trials in one evaluation
     std::vector<char> srch = act;
     std::vector<double> Et(cap_, 0.0);
     std::vector<int64_t> npt(cap_, 0);
     std::vector<char> ok(cap_, 0);
-    for (int f = 0; f < cap_; ++f) frames_[f].scale = 1.0;
-    for (int k = 0; k <= p.max_ls; ++k) {
+    for (int f = 0; f < cap_; ++f) {
+      frames_[f].scale = 1.0;
+      frames_[f].trial = 0;
+      frames_[f].redone = frames_[f].fp64;
+    }
+    for (int k = 0; k <= p.max_ls + 1; ++k) {
       bool any_s = false;
       for (char c : srch) any_s |= c != 0;
       if (!any_s) break;
@@ -468,8 +527,24 @@ class Batch {
       for (int f = 0; f < cap_; ++f) {
         if (!srch[f]) continue;
         Frame& fr = frames_[f];
-        if (k == 0 && cnt(f)[6]) { srch[f] = 0; act[f] = 0; finish(f, FSIM_ENOT_SPD); continue; }
-        if (k == 0 && cnt(f)[9]) { srch[f] = 0; act[f] = 0; finish(f, FSIM_ECONTACT_OVERFLOW); continue; }
+        if (fr.trial == 0 && cnt(f)[6] && !fr.redone) {
+          // the float32 factor of the frame's reduced system lost positive
+          // definiteness: its step again in float64 (the single-frame global
+          // step on its own workspace), then its CCD bound; its line search
+          // starts over at the next trial
+          fr.redone = true;
+          fr.fp64 = true;
+          fr.st.fp64_steps++;
+          fr.st.reduced_steps[reduced_path(fr.nc, FSIM_MIXED, tab_[f].one_cta_max)]--;
+          fr.st.reduced_steps[reduced_path(fr.nc, FSIM_FP64, tab_[f].one_cta_max)]++;
+          BTRY(redo_fp64(f, true));
+          fr.scale = 1.0;
+          continue;
+        }
+        if (fr.trial > p.max_ls) { srch[f] = 0; continue; }
+        if (fr.trial == 0 && cnt(f)[6]) { srch[f] = 0; act[f] = 0; finish(f, FSIM_ENOT_SPD); continue; }
+        if (fr.trial == 0 && cnt(f)[9]) { srch[f] = 0; act[f] = 0; finish(f, FSIM_ECONTACT_OVERFLOW); continue; }
+        fr.trial++;
         fr.st.ls_trials++;
         const double e = scl(f)[2] + scl(f)[0];
         if (cnt(f)[2]) { srch[f] = 0; act[f] = 0; finish(f, FSIM_ECONTACT_OVERFLOW); continue; }
@@ -485,6 +560,7 @@ class Batch {
           continue;
         }
         fr.scale *= 0.5;
+        if (fr.trial > p.max_ls) srch[f] = 0;     // out of halvings: ELS_FAIL below
       }
     }
     std::vector<char> grad(cap_, 0);
@@ -521,7 +597,10 @@ class Batch {
   double* scal_ = nullptr;
   float *rb_ = nullptr, *yb_ = nullptr, *ub_ = nullptr, *bx_ = nullptr;
   DevMesh* tab_dev_ = nullptr;
-  DevMesh* h_tab_ = nullptr;
+  static constexpr int kTabRing = 4;
+  DevMesh* h_tab_ = nullptr;       // kTabRing pinned tables of cap_ frames
+  cudaEvent_t ev_tab_[kTabRing] = {nullptr, nullptr, nullptr, nullptr};
+  int tab_slot_ = 0;
   int* h_counters_ = nullptr;
   double* h_scal_ = nullptr;
   size_t args_bytes_ = 0;

@@ -325,13 +325,15 @@ int evaluate(const Exec& ex, const MeshState& ms, const DevMesh& m, const double
 // Gradient g-hat (elastic from tetf + barrier over the pairs in m.pairs at
 // sb) into gout, the contact-affected set, B-check and ||g||^2.
 // Requires counters[0] (|C|) already on the host in npairs.
+// bprec is the precision of the pairs' PSD eigen-solves (prec unless the
+// frame switched its contact Hessian to float64).
 int gradient_and_hessian(const Exec& ex, const MeshState& ms, DevMesh& m, const double* sb,
                          const double* tetf, double* gout, int64_t npairs, int prec, int* nc_out,
-                         double* gn2_out, double kappa) {
+                         double* gn2_out, double kappa, int bprec = -1) {
   cudaStream_t s = ex.stream;
   launch_gather_forces(s, m, tetf, gout, prec);
   CK(cudaMemsetAsync(m.x2mark, 0, sizeof(int) * std::max(m.n2, 1), s));
-  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, kappa, prec);
+  launch_barrier_pairs(s, m, npairs, sb, ms.p.dhat, kappa, bprec < 0 ? prec : bprec);
   if (m.n2 > 0) launch_mark_scan(s, m);
   else CK(cudaMemsetAsync(m.counters + 3, 0, sizeof(int), s));
   // n_c stays on the device until the one read-back below: B-check is zeroed
@@ -413,6 +415,13 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     tol = std::max(p.tol_abs, p.tol_rel * gn);
     if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
   }
+  // precision of the contact Hessian and the global step: the frame's own,
+  // until a float32 factor of the reduced (or Schur) system loses positive
+  // definiteness; from then on the frame's pair eigen-solves and global steps
+  // run in float64 (a frame that got that stiff stays stiff while its pairs
+  // stay close, and the float32 eigen-solve's relative floor drops the soft
+  // directions of such pairs)
+  int gprec = prec;
   while (rc == FSIM_OK) {
     st.n_c = nc;
     st.n_c_max = std::max(st.n_c_max, nc);
@@ -429,15 +438,16 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     } else {
       // one graph per precision and reduced-system path (n_c decides the path)
       const bool schur = p.solver == FSIM_SOLVER_SCHUR;
-      const int gkey = 8 * prec + (schur ? 4 : reduced_path(nc, prec, m.one_cta_max));
+      const int gkey = 8 * gprec + (schur ? 4 : reduced_path(nc, gprec, m.one_cta_max));
       TRY(with_graph(ex, m, graph_slot(m, 0, 6, m.g, gkey), m.g, gkey, m.red_gen, [&]() -> int {
         CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
-        CK(global_step(s, m, m.g, m.dx, prec, m.counters + 6, ex.coop_ctas, ex.alone, schur, nc));
+        CK(global_step(s, m, m.g, m.dx, gprec, m.counters + 6, ex.coop_ctas, ex.alone, schur, nc));
         return FSIM_OK;
       }));
+      if (gprec != prec) st.fp64_steps++;
     }
     st.sum_nc3 += (double)nc * nc * nc;
-    if (p.solver == FSIM_SOLVER_WOODBURY) st.reduced_steps[reduced_path(nc, prec, m.one_cta_max)]++;
+    if (p.solver == FSIM_SOLVER_WOODBURY) st.reduced_steps[reduced_path(nc, gprec, m.one_cta_max)]++;
     // CCD step bound; the ACCD kernel reads the candidate count on the device,
     // and the overflow / factorisation flags are checked at the next read-back
     TRY(with_graph(ex, m, graph_slot(m, 10, 2, m.s, 0), m.s, 0, 0, [&]() -> int {
@@ -448,13 +458,45 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
       return FSIM_OK;
     }));
     // backtracking line search from alpha_m on E-hat = E + B
-    bool accepted = false;
+    bool accepted = false, redone = false;
     double scale = 1.0, Et = 0.0;
     int64_t np_t = 0;
     for (int k = 0; k <= p.max_ls; ++k) {
       launch_axpy_positions(s, 3 * m.n, m.x, m.dx, m.scal + 1, scale, m.xt);
       TRY(eval_at(m.xt, m.st, m.tetf_t));
       TRY(sync_read(ex, m));
+      if (k == 0 && ex.h_counters[6] && gprec != FSIM_FP64 && p.solver != FSIM_SOLVER_PCG &&
+          !redone) {
+        // the float32 factor of the reduced (or Schur) system lost positive
+        // definiteness (cond ~ 1 / u32 at very stiff pairs): the contact
+        // Hessian at x again with float64 eigen-solves (the trial evaluation
+        // replaced the pair list, so x is evaluated again first), this global
+        // step in float64, its CCD bound and a fresh line search
+        redone = true;
+        gprec = FSIM_FP64;
+        st.fp64_steps++;
+        if (p.solver == FSIM_SOLVER_WOODBURY) {
+          st.reduced_steps[reduced_path(nc, prec, m.one_cta_max)]--;
+          st.reduced_steps[reduced_path(nc, FSIM_FP64, m.one_cta_max)]++;
+        }
+        TRY(eval_at(m.x, m.s, m.tetf));
+        TRY(sync_read(ex, m));
+        {
+          double gn2r;
+          TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2r, kappa,
+                                   gprec));
+        }
+        CK(cudaMemsetAsync(m.counters + 6, 0, sizeof(int) * 2, s));
+        CK(global_step(s, m, m.g, m.dx, FSIM_FP64, m.counters + 6, ex.coop_ctas, ex.alone,
+                       p.solver == FSIM_SOLVER_SCHUR, nc));
+        launch_proxy(s, m, m.dx, m.ds);
+        launch_ccd_reset(s, m);
+        launch_ccd(s, m, m.s, m.ds, p.dhat, p.ccd_s, p.accd_max_iters);
+        CK(cudaGetLastError());
+        scale = 1.0;
+        k = -1;
+        continue;
+      }
       if (k == 0 && ex.h_counters[6]) { rc = FSIM_ENOT_SPD; break; }
       if (k == 0 && ex.h_counters[9]) { rc = FSIM_ECONTACT_OVERFLOW; break; }
       st.ls_trials++;
@@ -481,7 +523,7 @@ int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const doub
     npairs = np_t;
     st.iterations++;
     double gn2;
-    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2, kappa));
+    TRY(gradient_and_hessian(ex, ms, m, m.s, m.tetf, m.g, npairs, prec, &nc, &gn2, kappa, gprec));
     gn = std::sqrt(gn2);
     if (!std::isfinite(gn)) rc = FSIM_ENONFINITE;
   }

@@ -1299,9 +1299,14 @@ __global__ void __launch_bounds__(32 * kPairWarps) k_barrier_pairs_b(const DevMe
                                                                      double dhat) {
   const DevMesh* m = bframe_c(tab, blockIdx.y);
   if (!m) return;
-  k_barrier_pairs_body<float>(m->counters, m->cap_act, m->pairs, m->s, m->tris, m->edges, m->Wptr,
-                              m->Wcol, m->x2of, dhat, m->kappa_f, m->pair_grad, m->pair_hess,
-                              m->x2mark);
+  if (m->bar64)       // a frame switched to float64 contact Hessians
+    k_barrier_pairs_body<double>(m->counters, m->cap_act, m->pairs, m->s, m->tris, m->edges,
+                                 m->Wptr, m->Wcol, m->x2of, dhat, m->kappa_f, m->pair_grad,
+                                 m->pair_hess, m->x2mark);
+  else
+    k_barrier_pairs_body<float>(m->counters, m->cap_act, m->pairs, m->s, m->tris, m->edges,
+                                m->Wptr, m->Wcol, m->x2of, dhat, m->kappa_f, m->pair_grad,
+                                m->pair_hess, m->x2mark);
 }
 
 __global__ void __launch_bounds__(32) k_mollify_ee_b(const DevMesh* __restrict__ tab, double dhat) {

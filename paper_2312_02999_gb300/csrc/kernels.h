@@ -151,6 +151,7 @@ struct DevMesh {
   double ls_scale = 1.0;      // line-search factor of the trial step
   int col = 0;                // frame's column block (3 columns) in multi-RHS buffers
   int one_cta_max = 96;       // mixed reduced system: largest n_c on the one-CTA path
+  int bar64 = 0;              // batched barrier: float64 pair eigen-solves for this frame
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------

@@ -59,7 +59,8 @@ class FrameStats(C.Structure):
                 ("n_c", C.c_int32), ("n_c_max", C.c_int32), ("kappa_doublings", C.c_int32),
                 ("contacts", C.c_int64), ("grad_norm", C.c_double), ("grad_norm0", C.c_double),
                 ("energy", C.c_double), ("alpha_min", C.c_double), ("sum_nc3", C.c_double),
-                ("cg_iterations", C.c_int64), ("reduced_steps", C.c_int32 * 4)]
+                ("cg_iterations", C.c_int64), ("reduced_steps", C.c_int32 * 4),
+                ("fp64_steps", C.c_int32)]
 
     def as_dict(self):
         out = {}

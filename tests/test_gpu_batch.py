@@ -121,3 +121,42 @@ def test_batch_argument_errors(fsim, ctx):
                                         (m, act.fiber, act.stretch, None)], max_frames=2)
     assert rc == fsim.FSIM_ENONFINITE
     assert sts[0]["status"] == fsim.FSIM_ENONFINITE and sts[1]["status"] == 0
+
+
+def test_batch_stiff_requests_switch_to_float64(fsim, ctx):
+    # The 2k-vertex face under requests that press the lips together hard:
+    # a frame whose float32 reduced factor loses positive definiteness
+    # redoes that step with float64 pair eigen-solves and factors on its own
+    # workspace and keeps them for the rest of the frame, inside the batch.
+    # Every frame must converge and agree with its float64 solve.  Some of
+    # these requests have two equilibria a few 1e-5 of the diagonal apart
+    # with energies within 1e-8 (relative) of each other, and rounding
+    # decides which one a solve reaches; at most two frames may end at the
+    # other one, and they must be stationary points of that energy.
+    mesh = I.face_shell(n_target=2000)
+    field = I.bump_field(mesh, n_bumps=64, seed=11)
+    coeffs = I.request_coeffs(48 * 8, n_bumps=64, seed=5)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    reqs, ref = [], []
+    for ci in (16, 188, 189, 195, 235, 270, 303, 344, 359, 0, 3, 40):
+        a = I.bump_actuation(field, coeffs[ci])
+        m.set_actuation(a.fiber, a.stretch)
+        rc, st64 = m.solve_frame(x_init=mesh.rest, precision=fsim.FP64, check=False)
+        assert rc == 0
+        ref.append((m.positions(), st64))
+        reqs.append((m, a.fiber, a.stretch, None))
+    rc, xs, sts = fsim.solve_batch(ctx, reqs, max_frames=8)
+    assert rc == 0
+    diag = _diag(mesh)
+    other = 0
+    for x, (xr, s64), st in zip(xs, ref, sts):
+        assert st["status"] == 0
+        assert st["grad_norm"] <= mesh.tol_rel * st["grad_norm0"] + mesh.tol_abs
+        err = np.abs(x - xr).max() / diag
+        if err > 1e-6:
+            other += 1
+            assert err <= 1e-3
+            assert abs(st["energy"] - s64["energy"]) <= 1e-8 * abs(s64["energy"])
+    assert other <= 2
+    assert sum(st["fp64_steps"] for st in sts) > 0

@@ -644,3 +644,54 @@ def test_mollified_frame_parity(fsim, ctx):
         assert rc == 0 and st["contacts"] > 0
         err = np.abs(m.positions() - xo).max() / _diag(mesh)
         assert err <= tol, (prec, err, st["iterations"], so.iterations)
+
+
+def test_float32_factor_failure_is_redone_in_float64(fsim, ctx):
+    # Requests of the served workload on the 2k-vertex face (64 bumps, all
+    # coefficients of one sign) press the lips so hard that the reduced
+    # matrix N = I + L^T B L reaches cond ~ 1 / u32 and its float32 Cholesky
+    # can meet a non-positive pivot (whether it does depends on the rounding
+    # of the float32 sums, so not every run of one request meets it).  Such a
+    # frame redoes that global step with float64 pair eigen-solves and
+    # factors, and stays in float64 for the rest of its global steps (stats
+    # fp64_steps); every frame must converge and agree with the float64 frame
+    # at the mixed-precision bar.
+    mesh = I.face_shell(n_target=2000)
+    field = I.bump_field(mesh, n_bumps=64, seed=11)
+    coeffs = I.request_coeffs(48 * 8, n_bumps=64, seed=5)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    redone = 0
+    for ci in (16, 188, 189, 195, 235, 270, 303, 344, 359, 0, 3, 40):
+        a = I.bump_actuation(field, coeffs[ci])
+        m.set_actuation(a.fiber, a.stretch)
+        rc64, st64 = m.solve_frame(x_init=mesh.rest, precision=fsim.FP64, check=False)
+        x64 = m.positions()
+        rc, st = m.solve_frame(x_init=mesh.rest, precision=fsim.MIXED, check=False)
+        assert rc64 == 0 and rc == 0, (ci, rc64, rc, st["iterations"], st["fp64_steps"])
+        assert np.abs(m.positions() - x64).max() <= 1e-6 * _diag(mesh), ci
+        redone += st["fp64_steps"]
+    assert redone > 0
+
+
+def test_stiff_request_with_two_equilibria(fsim, ctx):
+    # One request of that workload has two equilibria 6.6e-5 of the diagonal
+    # apart (energies 4e-9 apart, relative; a float64 solve to |g| <= 1e-11
+    # |g_0| lands on one, a mixed solve to the same tolerance on the other,
+    # so both are stationary points); rounding decides which one a solve
+    # reaches.  Both solves must converge to stationary points of nearly
+    # equal energy.
+    mesh = I.face_shell(n_target=2000)
+    field = I.bump_field(mesh, n_bumps=64, seed=11)
+    coeffs = I.request_coeffs(48 * 8, n_bumps=64, seed=5)
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    a = I.bump_actuation(field, coeffs[193])
+    m.set_actuation(a.fiber, a.stretch)
+    rc64, st64 = m.solve_frame(x_init=mesh.rest, precision=fsim.FP64, check=False)
+    x64 = m.positions()
+    rc, st = m.solve_frame(x_init=mesh.rest, precision=fsim.MIXED, check=False)
+    assert rc64 == 0 and rc == 0
+    assert st["grad_norm"] <= 1e-7 * st["grad_norm0"] and st64["grad_norm"] <= 1e-7 * st64["grad_norm0"]
+    assert abs(st["energy"] - st64["energy"]) <= 1e-8 * abs(st64["energy"])
+    assert np.abs(m.positions() - x64).max() <= 1e-3 * _diag(mesh)
