@@ -118,6 +118,11 @@ typedef struct {
                                to a 4-CTA cluster, beyond that to the
                                cooperative kernel.  <= 0 selects 96 (the most
                                one CTA's shared memory holds); a tuning knob */
+  int32_t sigma_product_simt; /* lock-step batches (fsim_solve_batch, server
+                               batch mode): 0 (default) forms u = Sigma^-1 y2
+                               for all frames on the tensor cores (tcgen05,
+                               TF32 head/tail split, about 22 significant
+                               bits); nonzero: float32 SIMT product          */
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1
@@ -278,6 +283,18 @@ fsim_status fsim_eval_contacts(fsim_ctx_t ctx, int mesh_id, const double* x,
 fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x,
                               double* grad_out, int32_t* n_c, int32_t* c_out,
                               double* bcheck_out, int64_t bcheck_cap);
+
+/* The explicit Sigma^-1 of Sec. 3.2 applied to ncols right-hand sides at
+ * once, as the lock-step batches form u = Sigma^-1 y2 (Eq. 9) for all their
+ * frames: y [n2 x ncols] and u_out [n2 x ncols] are row-major host arrays in
+ * x2 order (the free x2 vertices in increasing mesh order), 1 <= ncols <=
+ * 192.  y is rounded to float32 on the device.  tensor_cores nonzero: the
+ * tcgen05 product with TF32 head/tail operands (FSIM_EINVAL where it is not
+ * available); 0: the float32 SIMT product.  Needs a prefactored mesh only;
+ * allocates and frees its own device buffers.  FSIM_ECUDA if a bounded wait
+ * of the tensor-core kernel ran out. */
+fsim_status fsim_eval_sigma_inv_mr(fsim_ctx_t ctx, int mesh_id, const double* y, int32_t ncols,
+                                   int32_t tensor_cores, double* u_out);
 
 /* Global step (Eq. 4 through Eq. 8-11): dx_out [3n] solves
  * (H + PositiveDefinite(B)) dx = -g-hat at x (zero on pinned vertices).

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_local.cu", "k_contact.cu", "k_solve.cu", "k_reduced.cu", "k_pcg.cu",
-           "k_schur.cu", "batch.cu", "prefactor.cpp", "serve.cpp", "region.cpp"]
+           "k_schur.cu", "batch.cu", "k_tc.cu", "prefactor.cpp", "serve.cpp", "region.cpp"]
 NO_FMA = {"k_contact.cu", "region.cpp"}
 
 

@@ -497,6 +497,7 @@ class Batch {
     bs.cols_dev = cols_dev_;
     bs.x1s_dev = x1s_dev_;
     bs.num_sms = ctx_->num_sms;
+    bs.use_tc = ms_.p.sigma_product_simt == 0;
     if (any_b) {
       BCK(global_step_b(bs));
       // CCD step bound of every frame of the batched step
@@ -524,6 +525,7 @@ class Batch {
       if (!any_s) break;
       BTRY(evaluate(srch, 1));
       BTRY(read_back());
+      if (cnt(0)[15]) return FSIM_ECUDA;       // a tensor-core wait ran out
       for (int f = 0; f < cap_; ++f) {
         if (!srch[f]) continue;
         Frame& fr = frames_[f];

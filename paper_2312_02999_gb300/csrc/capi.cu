@@ -862,6 +862,18 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   {
     std::vector<float> sf(f.sigma_inv.begin(), f.sigma_inv.end());
     TRY(upload(ms, s, &m.Sinvf, sf.data(), sf.size()));
+    // TF32 head and tail of Sigma^-1 for the tensor-core product of batches
+    if (m.n2 > 0) {
+      std::vector<float> hi, lo;
+      tc_split_sinv(f.sigma_inv.data(), m.n2, hi, lo, &m.sinv_ld);
+      TRY(upload(ms, s, &m.sinv_hi, hi.data(), hi.size()));
+      TRY(upload(ms, s, &m.sinv_lo, lo.data(), lo.size()));
+      ms.tc_maps.assign((tc_map_bytes() + 7) / 8 + 8, 0);
+      // 64-byte aligned view of the storage for the descriptors
+      uint64_t* base = ms.tc_maps.data();
+      while (((uintptr_t)base & 63) != 0) ++base;
+      m.tc_maps = tc_encode_sinv(m.sinv_hi, m.sinv_lo, m.n2, m.sinv_ld, base) == 0 ? base : nullptr;
+    }
     CK(cudaStreamSynchronize(s));
   }
   m.cap = p->contact_capacity > 0 ? p->contact_capacity
@@ -1141,6 +1153,50 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
     if (nc > 0)
       CK(cudaMemcpy(bcheck_out, m.Bc, sizeof(double) * 9 * (size_t)nc * nc, cudaMemcpyDeviceToHost));
   }
+  return FSIM_OK;
+}
+
+fsim_status fsim_eval_sigma_inv_mr(fsim_ctx_t ctx, int mesh_id, const double* y, int32_t ncols,
+                                   int32_t tensor_cores, double* u_out) {
+  MeshState* ms = get_mesh(ctx, mesh_id);
+  if (!ms) return FSIM_EINVAL;
+  if (!ms->prefactored) return FSIM_ENOT_READY;
+  DevMesh& m = ms->d;
+  if (!y || !u_out || ncols < 1 || ncols > 192 || m.n2 <= 0) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const int n2 = m.n2, nr = (ncols + 31) / 32 * 32;
+  if (tensor_cores && !tc_sinv_supported(m, nr)) return FSIM_EINVAL;
+  std::vector<float> yf((size_t)n2 * nr, 0.f);
+  for (int i = 0; i < n2; ++i)
+    for (int c = 0; c < ncols; ++c) yf[(size_t)i * nr + c] = (float)y[(size_t)i * ncols + c];
+  float *dy = nullptr, *du = nullptr;
+  int* derr = nullptr;
+  auto release = [&]() {
+    if (dy) cudaFree(dy);
+    if (du) cudaFree(du);
+    if (derr) cudaFree(derr);
+  };
+  if (cudaMalloc(&dy, sizeof(float) * yf.size()) != cudaSuccess ||
+      cudaMalloc(&du, sizeof(float) * yf.size()) != cudaSuccess ||
+      cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return FSIM_ENOMEM;
+  }
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(dy, yf.data(), sizeof(float) * yf.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = tensor_cores ? launch_sinv_tc(s, m, dy, nr, du, ctx->num_sms, derr)
+                     : launch_sinv_simt(s, m, dy, nr, du);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(yf.data(), du, sizeof(float) * yf.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess || herr) return FSIM_ECUDA;
+  for (int i = 0; i < n2; ++i)
+    for (int c = 0; c < ncols; ++c) u_out[(size_t)i * ncols + c] = (double)yf[(size_t)i * nr + c];
   return FSIM_OK;
 }
 

@@ -690,10 +690,18 @@ cudaError_t global_step_b(const BatchStep& bs) {
   }
   {
     ProfScope ps(PROF_GEMV, s);
-    k_gemm_mr<<<dim3((n2 + 31) / 32, chunks), 256, 0, s>>>(n2, m.Sinvf, bs.rb + (size_t)n1 * nr,
-                                                           bs.ub, nr);
+    // u = Sigma^-1 y2 on the tensor cores (3xTF32); the SIMT product where
+    // the descriptors could not be made
+    if (bs.use_tc && tc_sinv_supported(m, nr)) {
+      e = launch_sinv_tc(s, m, bs.rb + (size_t)n1 * nr, nr, bs.ub, bs.num_sms, m.counters + 15);
+      if (e != cudaSuccess) return e;
+    } else {
+      k_gemm_mr<<<dim3((n2 + 31) / 32, chunks), 256, 0, s>>>(n2, m.Sinvf, bs.rb + (size_t)n1 * nr,
+                                                             bs.ub, nr);
+      count_launch();
+    }
     k_unpack_mr<<<dim3((n2 + 255) / 256, nb), 256, 0, s>>>(bs.tab, bs.ub, bs.rb, bs.bx, nr);
-    count_launch(2);
+    count_launch();
   }
   // the contact-free backward solve x1 = L1^-T (y1 - L21^T u) on the side
   // stream while the reduced systems are solved
@@ -726,6 +734,12 @@ cudaError_t global_step_b(const BatchStep& bs) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_sinv_simt(cudaStream_t s, const DevMesh& m, const float* Y, int nr, float* U) {
+  k_gemm_mr<<<dim3((m.n2 + 31) / 32, nr / kMrCols), 256, 0, s>>>(m.n2, m.Sinvf, Y, U, nr);
+  count_launch();
+  return cudaGetLastError();
+}
+
 bool batch_supported(const DevMesh& m, int nr) {
   if (!m.Zf || !m.Phi_t || !m.Sinvf || m.n1 <= 0 || m.n2 <= 0 || nr % kMrCols != 0) return false;
   int maxns = 0;
@@ -737,6 +751,7 @@ void set_solver_smem_limits(int max_bytes) {
   // k_fwd_mr: its staged right-hand sides (ns x 32 floats) beside 48 KB of
   // static shared memory; batch_supported keeps ns x 128 B within 160 KB
   cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, 170 * 1024);
+  tc_set_smem_limits();
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
   cudaFuncSetAttribute(k_bwd_chunk<double, 256>, a, max_bytes);

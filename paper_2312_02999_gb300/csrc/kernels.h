@@ -1,6 +1,7 @@
 // Device-side mesh state and the host-callable kernel launchers.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace fsim {
@@ -152,6 +153,13 @@ struct DevMesh {
   int col = 0;                // frame's column block (3 columns) in multi-RHS buffers
   int one_cta_max = 96;       // mixed reduced system: largest n_c on the one-CTA path
   int bar64 = 0;              // batched barrier: float64 pair eigen-solves for this frame
+  // Sigma^-1 split into TF32 head and tail (n2 rows, row stride sinv_ld) and
+  // their TMA descriptors (host memory, owned by the mesh) for the tensor-core
+  // product of the batched global step
+  float* sinv_hi = nullptr;
+  float* sinv_lo = nullptr;
+  int sinv_ld = 0;
+  const void* tc_maps = nullptr;
 };
 
 // ---- local step (k_local.cu) ---------------------------------------------
@@ -292,10 +300,22 @@ struct BatchStep {
   const int* cols_dev = nullptr;            // 3 col per frame (device)
   double* const* x1s_dev = nullptr;         // r of each frame (device array of pointers)
   int num_sms = 1;
+  bool use_tc = true;                       // Sigma^-1 product on the tensor cores
 };
 cudaError_t global_step_b(const BatchStep& bs);
 // whether the batched solves can serve this mesh with nr columns
 bool batch_supported(const DevMesh& m, int nr);
+// tensor-core product u = Sigma^-1 y2 over nr multi-RHS columns (k_tc.cu)
+void tc_split_sinv(const double* sinv, int n2, std::vector<float>& hi, std::vector<float>& lo,
+                   int* ld_out);
+int tc_encode_sinv(const float* d_hi, const float* d_lo, int n2, int ld, void* maps);
+size_t tc_map_bytes();
+void tc_set_smem_limits();
+bool tc_sinv_supported(const DevMesh& m, int nr);
+// the float32 SIMT form of the same product (k_solve.cu)
+cudaError_t launch_sinv_simt(cudaStream_t s, const DevMesh& m, const float* Y, int nr, float* U);
+cudaError_t launch_sinv_tc(cudaStream_t s, const DevMesh& m, const float* Y, int nr, float* U,
+                           int num_sms, int* err);
 size_t reduced_args_bytes();
 void reduced_args_fill(void* dst, const DevMesh& m, int active);
 cudaError_t reduced_prepare_b(cudaStream_t s2, const void* args_dev, int nb, int num_sms);

@@ -37,6 +37,8 @@ struct MeshState {
   double* proj = nullptr;
   double* dxtmp = nullptr;
   bool has_x = false;
+  // TMA descriptors of the tensor-core Sigma^-1 product (DevMesh::tc_maps)
+  std::vector<uint64_t> tc_maps;
 };
 
 // Where a solve runs: its stream, its pinned read-back words, the CTA count

@@ -51,7 +51,8 @@ class Params(C.Structure):
                 ("coop_ctas", C.c_int32), ("contact_capacity", C.c_int64),
                 ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
                 ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double), ("adaptive_kappa", C.c_int32),
-                ("ee_mollifier", C.c_int32), ("reduced_one_cta_max", C.c_int32)]
+                ("ee_mollifier", C.c_int32), ("reduced_one_cta_max", C.c_int32),
+                ("sigma_product_simt", C.c_int32)]
 
 
 class FrameStats(C.Structure):
@@ -128,6 +129,7 @@ _SIGS = {
     "fsim_eval_contacts": [_P, C.c_int, _D, _I32, C.c_int64, _I64, _D],
     "fsim_eval_barrier": [_P, C.c_int, _D, _D, _I32, _I32, _D, C.c_int64],
     "fsim_eval_global_step": [_P, C.c_int, _D, C.c_int, _D, _I32],
+    "fsim_eval_sigma_inv_mr": [_P, C.c_int, _D, C.c_int32, C.c_int32, _D],
     "fsim_eval_ccd": [_P, C.c_int, _D, _D, _D],
     "fsim_eval_energy": [_P, C.c_int, _D, C.c_int, _D, _D],
     "fsim_mesh_info_get": [_P, C.c_int, C.POINTER(MeshInfo)],
@@ -379,6 +381,17 @@ class Mesh:
         _chk(self.lib.fsim_eval_global_step(self.ctx.h, self.id, _d(xx), int(precision), _d(dx),
                                             C.byref(path)), "fsim_eval_global_step")
         return (dx, path.value) if want_path else dx
+
+    def eval_sigma_inv_mr(self, y, tensor_cores=True):
+        """u = Sigma^-1 y for an (n2, ncols) array in x2 order, as the batches form it."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if y.ndim != 2:
+            raise ValueError("y must be (n2, ncols)")
+        u = np.empty_like(y)
+        _chk(self.lib.fsim_eval_sigma_inv_mr(self.ctx.h, self.id, _d(y), int(y.shape[1]),
+                                             1 if tensor_cores else 0, _d(u)),
+             "fsim_eval_sigma_inv_mr")
+        return u
 
     def eval_ccd(self, x, dx):
         xx, dd = self._x(x), self._x(dx)
