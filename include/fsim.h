@@ -284,6 +284,15 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x,
                               double* grad_out, int32_t* n_c, int32_t* c_out,
                               double* bcheck_out, int64_t bcheck_cap);
 
+/* Index checks of a bounds-checked build (compiled with -DFSIM_CHECK; the
+ * build's check variant is libfsim_check.so).  *enabled is 1 in such a build,
+ * else 0.  *word is 0 when no checked index has failed since the last call;
+ * otherwise the first failure seen, site << 48 | index (site 1: force
+ * gather tet slot, 2: supernodal-solve row, 3: contact-list entry).  A
+ * failing index is skipped, not trapped.  Synchronises the device, then
+ * resets the words. */
+fsim_status fsim_check_status(fsim_ctx_t ctx, int32_t* enabled, uint64_t* word);
+
 /* The explicit Sigma^-1 of Sec. 3.2 applied to ncols right-hand sides at
  * once, as the lock-step batches form u = Sigma^-1 y2 (Eq. 9) for all their
  * frames: y [n2 x ncols] and u_out [n2 x ncols] are row-major host arrays in

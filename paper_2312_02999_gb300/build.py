@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsim.so")
+# bounds-checked variant (-DFSIM_CHECK): index checks that record and skip
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libfsim_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_local.cu", "k_contact.cu", "k_solve.cu", "k_reduced.cu", "k_pcg.cu",
            "k_schur.cu", "batch.cu", "k_tc.cu", "prefactor.cpp", "serve.cpp", "region.cpp"]
@@ -29,10 +32,12 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def _compile(src: str) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, check: bool = False) -> str:
+    obj = os.path.join(BUILD_CHECK if check else BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
+    if check:
+        flags += ["-DFSIM_CHECK"]
     if src.endswith(".cu"):
         flags += ARCH + ["--expt-relaxed-constexpr"]
         if src in NO_FMA:
@@ -48,31 +53,33 @@ def _compile(src: str) -> str:
     return obj
 
 
-def _stale(objs) -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "fsim.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if sources changed) and return the path of libfsim.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and not _stale(None):
-        return LIB
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libfsim.so, or of
+    the bounds-checked libfsim_check.so with ``check``."""
+    lib = LIB_CHECK if check else LIB
+    os.makedirs(BUILD_CHECK if check else BUILD, exist_ok=True)
+    if not force and not _stale(lib):
+        return lib
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(_compile, SOURCES))
-    cmd = [_nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcudart"]
+        objs = list(ex.map(lambda src: _compile(src, check), SOURCES))
+    cmd = [_nvcc(), "-shared", "-o", lib] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv)

@@ -443,6 +443,7 @@ class Batch {
   }
 
   int iterate() {
+    NvtxRange nv("fsim.batch_iteration");
     const fsim_params& p = ms_.p;
     std::vector<char> act(cap_, 0);
     for (int f = 0; f < cap_; ++f) {

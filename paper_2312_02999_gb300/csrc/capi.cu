@@ -362,6 +362,7 @@ constexpr double kKappaMaxRatio = 100.0;   // ... up to 100 times the start valu
 
 int solve_frame_impl(const Exec& ex, const MeshState& ms, DevMesh& m, const double* x_init,
                      bool init_is_dev, int prec, fsim_frame_stats* stats) {
+  NvtxRange nv("fsim.frame");
   cudaStream_t s = ex.stream;
   const fsim_params& p = ms.p;
   fsim_frame_stats st{};
@@ -1153,6 +1154,22 @@ fsim_status fsim_eval_barrier(fsim_ctx_t ctx, int mesh_id, const double* x, doub
     if (nc > 0)
       CK(cudaMemcpy(bcheck_out, m.Bc, sizeof(double) * 9 * (size_t)nc * nc, cudaMemcpyDeviceToHost));
   }
+  return FSIM_OK;
+}
+
+fsim_status fsim_check_status(fsim_ctx_t ctx, int32_t* enabled, uint64_t* word) {
+  if (!ctx || !enabled || !word) return FSIM_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return FSIM_ECUDA;
+#ifdef FSIM_CHECK
+  *enabled = 1;
+#else
+  *enabled = 0;
+#endif
+  uint64_t w = 0;
+  for (uint64_t v : {check_word_local(), check_word_solve(), check_word_reduced()})
+    if (w == 0 && v != 0) w = v;
+  *word = w;
   return FSIM_OK;
 }
 

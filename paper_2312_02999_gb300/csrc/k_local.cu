@@ -6,6 +6,7 @@
 // contribution w D gradN_a of each of its four vertices (the row form of
 // w_i G_i^T (G_i x - p_i)).  Forces are written per tet and gathered per
 // vertex in a fixed order (deterministic sums, no atomics).
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -53,7 +54,15 @@ void count_launch(int k) {
 }
 void set_capturing(bool on) { tl_capturing = on; }
 
+// NVTX range names of the stage classes (a tool such as Nsight Systems shows
+// them; without one attached a push/pop is a null check)
+static const char* const kProfNames[PROF_NCLASS] = {
+    "fsim.local_step", "fsim.constraint_set", "fsim.trisolve_fwd", "fsim.trisolve_bwd",
+    "fsim.reduced_factor", "fsim.barrier", "fsim.ccd", "fsim.sigma_product", "fsim.reduced_system",
+    "fsim.pcg", "fsim.schur"};
+
 ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
+  nvtxRangePushA(c >= 0 && c < PROF_NCLASS ? kProfNames[c] : "fsim");
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!(g_prof.mask & (1u << c))) return;
   if (g_prof.pending.size() >= 4096) prof_resolve();
@@ -70,7 +79,13 @@ ProfScope::ProfScope(int c, cudaStream_t s) : slot(-1), stream(s) {
   cudaEventRecord(g_prof.ev0[slot], s);
 }
 
+FSIM_CHECK_READER(check_word_local)
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEventRecord(g_prof.ev1[slot], stream);
@@ -480,6 +495,7 @@ __device__ __forceinline__ void gather_forces_df_body(int n, int T, const int* _
     for (int e = vptr[v]; e < vptr[v + 1]; ++e) {
       const int slot = vslot[e];
       const int t = slot >> 2, a = slot & 3;
+      if (!FSIM_CHECK_IDX(t, T, CHECK_GATHER_TET)) continue;
       s0 = df_add(s0, ld_df(tetf, (size_t)(a * 3 + 0) * T + t));
       s1 = df_add(s1, ld_df(tetf, (size_t)(a * 3 + 1) * T + t));
       s2 = df_add(s2, ld_df(tetf, (size_t)(a * 3 + 2) * T + t));
@@ -505,6 +521,7 @@ __global__ void k_gather_forces(int n, int T, const int* __restrict__ vptr,
     for (int e = vptr[v]; e < vptr[v + 1]; ++e) {
       const int slot = vslot[e];
       const int t = slot >> 2, a = slot & 3;
+      if (!FSIM_CHECK_IDX(t, T, CHECK_GATHER_TET)) continue;
       s0 += tetf[(size_t)(a * 3 + 0) * T + t];
       s1 += tetf[(size_t)(a * 3 + 1) * T + t];
       s2 += tetf[(size_t)(a * 3 + 2) * T + t];

@@ -291,6 +291,7 @@ __device__ void z2_update(const RedArgs<FT>& a, int nc, int w, int nw) {
     const double* srow = a.Sinv + (size_t)q * a.n2;
     double a0 = 0, a1 = 0, a2 = 0;
     for (int m = lane; m < nc; m += 32) {
+      if (!FSIM_CHECK_IDX(a.clist[m], a.n2, CHECK_CLIST)) continue;
       const double sv = srow[a.clist[m]];
       a0 += sv * a.v[3 * m]; a1 += sv * a.v[3 * m + 1]; a2 += sv * a.v[3 * m + 2];
     }
@@ -744,9 +745,11 @@ __device__ __forceinline__ void k_small_s_body(RedArgs<float> a) {
   float* Pt = P + prow(kClusNc);          // 32 x kPtLd
   if (tid == 0) a.nrm[2] = 0.0;
   for (int i = wid; i < nc; i += kSW) {
+    if (!FSIM_CHECK_IDX(a.clist[i], a.n2, CHECK_CLIST)) continue;
     const double* srow = a.Sinv + (size_t)a.clist[i] * a.n2;
 #pragma unroll 4
     for (int j = lane; j < nc; j += 32) {
+      if (!FSIM_CHECK_IDX(a.clist[j], a.n2, CHECK_CLIST)) continue;
       const double sv = srow[a.clist[j]];
       a.S64[(size_t)i * nc + j] = sv;
       if (j <= i) P[prow(i) + j] = (float)sv;
@@ -1568,10 +1571,11 @@ __global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply(RedArgs<float> a, 
   if (have) {
     red_layout(a, nc);
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      cs[k] = a.clist[k];
-      vs[3 * k] = (float)a.v[3 * k];
-      vs[3 * k + 1] = (float)a.v[3 * k + 1];
-      vs[3 * k + 2] = (float)a.v[3 * k + 2];
+      const bool okc = FSIM_CHECK_IDX(a.clist[k], a.n2, CHECK_CLIST);
+      cs[k] = okc ? a.clist[k] : 0;
+      vs[3 * k] = okc ? (float)a.v[3 * k] : 0.f;
+      vs[3 * k + 1] = okc ? (float)a.v[3 * k + 1] : 0.f;
+      vs[3 * k + 2] = okc ? (float)a.v[3 * k + 2] : 0.f;
     }
   }
   __syncthreads();
@@ -1652,10 +1656,11 @@ __global__ void __launch_bounds__(32 * kPhiSplit) k_phi_apply_b(const RedArgs<fl
     const int kn = min(kClusNc, nc - k0);
     __syncthreads();
     for (int k = threadIdx.x; k < kn; k += blockDim.x) {
-      cs[k] = a.clist[k0 + k];
-      vs[3 * k] = (float)a.v[3 * (k0 + k)];
-      vs[3 * k + 1] = (float)a.v[3 * (k0 + k) + 1];
-      vs[3 * k + 2] = (float)a.v[3 * (k0 + k) + 2];
+      const bool okc = FSIM_CHECK_IDX(a.clist[k0 + k], a.n2, CHECK_CLIST);
+      cs[k] = okc ? a.clist[k0 + k] : 0;
+      vs[3 * k] = okc ? (float)a.v[3 * (k0 + k)] : 0.f;
+      vs[3 * k + 1] = okc ? (float)a.v[3 * (k0 + k) + 1] : 0.f;
+      vs[3 * k + 2] = okc ? (float)a.v[3 * (k0 + k) + 2] : 0.f;
     }
     __syncthreads();
     if (p < n1) {
@@ -1802,4 +1807,6 @@ void set_reduced_smem_limits() {
   cudaFuncSetAttribute(k_small_v_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmemV);
   cudaFuncSetAttribute(k_clus_v_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusSmem);
 }
+FSIM_CHECK_READER(check_word_reduced)
+
 }  // namespace fsim

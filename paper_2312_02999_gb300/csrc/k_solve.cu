@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(256)
 k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
          const int* __restrict__ nra, const int64_t* __restrict__ roff,
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
-         const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr) {
+         const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr,
+         int nf) {
   extern __shared__ float bj[];                    // ns x 32
   __shared__ __align__(16) float Zs[2][kMrK][32];
   __shared__ float part[8][32][32];                // warp partial sums (no padding needed:
@@ -304,8 +305,12 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += part[w][rr][j];
     const int r = r0 + rr;
-    if (r < ns) y[(size_t)(c0 + r) * nr + cc + j] = t;
-    else atomicAdd(b + (size_t)rows[roff[J] + r - ns] * nr + cc + j, -t);
+    if (r < ns) {
+      y[(size_t)(c0 + r) * nr + cc + j] = t;
+    } else {
+      const int row = rows[roff[J] + r - ns];
+      if (FSIM_CHECK_IDX(row, nf, CHECK_TRSV_ROW)) atomicAdd(b + (size_t)row * nr + cc + j, -t);
+    }
   }
 }
 
@@ -322,7 +327,8 @@ __global__ void __launch_bounds__(256)
 k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int* __restrict__ nsa,
          const int* __restrict__ nra, const int64_t* __restrict__ roff,
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
-         const float* __restrict__ Z, const float* __restrict__ y, float* __restrict__ x, int nr) {
+         const float* __restrict__ Z, const float* __restrict__ y, float* __restrict__ x, int nr,
+         int nf) {
   constexpr int kRows = 64;
   constexpr int kPer = kRows * 32 / 256;           // elements per thread per tile
   __shared__ __align__(16) float buf[2 * 2 * kRows * 32 + 64];   // [2][ws | Zs]
@@ -340,9 +346,16 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const int e = tid + 256 * i, rr = e >> 5, j = e & 31, r = rb + rr;
-      wr[i] = r < ld ? (r < ns ? y[(size_t)(c0 + r) * nr + cc + j]
-                               : -x[(size_t)__ldg(Rj + r - ns) * nr + cc + j])
-                     : 0.f;
+      float w = 0.f;
+      if (r < ld) {
+        if (r < ns) {
+          w = y[(size_t)(c0 + r) * nr + cc + j];
+        } else {
+          const int row = __ldg(Rj + r - ns);
+          if (FSIM_CHECK_IDX(row, nf, CHECK_TRSV_ROW)) w = -x[(size_t)row * nr + cc + j];
+        }
+      }
+      wr[i] = w;
       // Z_J[r][k0 + j] (lower triangle of the diagonal block)
       zr[i] = (r < ld && j < kn && r >= k0 + j) ? __ldg(Zj + (size_t)(k0 + j) * ldz + r) : 0.f;
     }
@@ -685,7 +698,7 @@ cudaError_t global_step_b(const BatchStep& bs) {
     const size_t sm = sizeof(float) * kMrCols * (size_t)m.h_level_maxns[l];
     k_fwd_mr<<<dim3(z - a, chunks), 256, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
                                                    m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.rb,
-                                                   bs.yb, nr);
+                                                   bs.yb, nr, nf);
     count_launch();
   }
   {
@@ -716,7 +729,7 @@ cudaError_t global_step_b(const BatchStep& bs) {
     ProfScope ps(PROF_TRSV_BWD, s2);
     k_bwd_mr<<<dim3(z - a, chunks), 256, 0, s2>>>(m.bwd_items32 + a, m.sn_c0, m.sn_ns, m.sn_nr1,
                                                   m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.yb,
-                                                  bs.bx, nr);
+                                                  bs.bx, nr, nf);
     count_launch();
   }
   if (cudaEventRecord(bs.ev[3], s2) != cudaSuccess) return cudaGetLastError();
@@ -733,6 +746,8 @@ cudaError_t global_step_b(const BatchStep& bs) {
   count_launch();
   return cudaGetLastError();
 }
+
+FSIM_CHECK_READER(check_word_solve)
 
 cudaError_t launch_sinv_simt(cudaStream_t s, const DevMesh& m, const float* Y, int nr, float* U) {
   k_gemm_mr<<<dim3((m.n2 + 31) / 32, nr / kMrCols), 256, 0, s>>>(m.n2, m.Sinvf, Y, U, nr);

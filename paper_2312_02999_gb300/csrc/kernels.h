@@ -340,6 +340,49 @@ struct ProfScope {
   int slot;
   cudaStream_t stream;
 };
+// ---------------------------------------------------------------------------
+// Bounds-checked builds (-DFSIM_CHECK).  Data-dependent indices (adjacency
+// slots, pair primitives, scatter rows, contact lists) are tested before
+// use; a failing index is skipped and the first failure of a translation
+// unit is kept in its check word: site << 48 | (index & 0xffffffffffff).
+// Without FSIM_CHECK the test is a constant true and costs nothing.
+// ---------------------------------------------------------------------------
+enum CheckSite : int {
+  CHECK_GATHER_TET = 1,      // force gather: vertex-tet slot out of the tet range
+  CHECK_TRSV_ROW = 2,        // multi-RHS supernodal solves: off-diagonal row position
+  CHECK_CLIST = 3            // reduced system / z2 / Phi: contact list entry out of x2
+};
+#if defined(FSIM_CHECK) && defined(__CUDACC__)
+static __device__ unsigned long long g_check_word = 0ull;   // one per translation unit
+__device__ __forceinline__ bool check_idx(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_check_word, 0ull,
+            ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return false;
+}
+#define FSIM_CHECK_IDX(i, n, site) ::fsim::check_idx((long long)(i), (long long)(n), (site))
+// host reader of this translation unit's word (reset to 0 after reading)
+#define FSIM_CHECK_READER(name)                                                   \
+  uint64_t name() {                                                               \
+    unsigned long long v = 0, z = 0;                                              \
+    cudaMemcpyFromSymbol(&v, g_check_word, sizeof(v));                            \
+    cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));                              \
+    return (uint64_t)v;                                                           \
+  }
+#else
+#define FSIM_CHECK_IDX(i, n, site) true
+#define FSIM_CHECK_READER(name) \
+  uint64_t name() { return 0; }
+#endif
+uint64_t check_word_local();
+uint64_t check_word_solve();
+uint64_t check_word_reduced();
+
+// An NVTX range for the lifetime of the object (whole frames, batch iterations)
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+};
 void prof_set_mask(unsigned mask);
 bool prof_active();
 // While a thread captures a CUDA graph its launches are not counted (the

@@ -130,6 +130,7 @@ _SIGS = {
     "fsim_eval_barrier": [_P, C.c_int, _D, _D, _I32, _I32, _D, C.c_int64],
     "fsim_eval_global_step": [_P, C.c_int, _D, C.c_int, _D, _I32],
     "fsim_eval_sigma_inv_mr": [_P, C.c_int, _D, C.c_int32, C.c_int32, _D],
+    "fsim_check_status": [_P, _I32, C.POINTER(C.c_uint64)],
     "fsim_eval_ccd": [_P, C.c_int, _D, _D, _D],
     "fsim_eval_energy": [_P, C.c_int, _D, C.c_int, _D, _D],
     "fsim_mesh_info_get": [_P, C.c_int, C.POINTER(MeshInfo)],
@@ -160,14 +161,14 @@ SOLVER_WOODBURY = 0
 SOLVER_PCG = 1
 SOLVER_SCHUR = 2
 
-_lib = None
+_libs = {}
 
 
 def load(path: str = LIB_PATH):
-    """Load libfsim.so (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libfsim.so, or another build of it such as the bounds-checked
+    libfsim_check.so (raises if it has not been built)."""
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise ImportError(f"CUDA library not built: {path} (run paper_2312_02999_gb300.build)")
     lib = C.CDLL(path)
@@ -175,7 +176,7 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
-    _lib = lib
+    _libs[path] = lib
     return lib
 
 
@@ -211,11 +212,18 @@ def default_params(**kw) -> Params:
 class Context:
     """One fsim context on a CUDA device."""
 
-    def __init__(self, device: int = 0):
-        self.lib = load()
+    def __init__(self, device: int = 0, lib_path: str = LIB_PATH):
+        self.lib = load(lib_path)
         h = _P()
         _chk(self.lib.fsim_create(C.byref(h), int(device)), "fsim_create")
         self.h = h
+
+    def check_status(self):
+        """(enabled, word) of fsim_check_status: whether this library was built
+        with index checks, and the first failed check (0: none)."""
+        en, w = C.c_int32(), C.c_uint64()
+        _chk(self.lib.fsim_check_status(self.h, C.byref(en), C.byref(w)), "fsim_check_status")
+        return bool(en.value), int(w.value)
 
     def close(self):
         if self.h:

