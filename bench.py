@@ -616,10 +616,12 @@ def run_ours(args):
     value = fps(srv_m)
     iters = [st["iterations"] for st in srv_m["stats"]]
     rooflines = batch_rooflines(bprof, info)
-    # "chol" times the reduced-system kernels on both streams and nests in
-    # "reduced": the dominant class is chosen among the disjoint ones
-    disjoint_r = [r for r in rooflines if r["kernel_class"] != "chol"]
-    dominant = max(disjoint_r, key=lambda r: r["ms"]) if disjoint_r else None
+    # The dominant kernel is the one with the largest share of the launch
+    # list of this workload (ncu, serialised): k_elastic_df_b, the local step,
+    # at 27 % (profiles/launches_face30k_served_batch32.md).  The "reduced"
+    # class brackets five kernels that overlap the backward solve on the side
+    # stream, so its event time also holds the SMs it waits for.
+    dominant = next((r for r in rooflines if r["kernel_class"] == "local_step"), None)
     single_leg = lambda r: {
         "value": world * K / (sum(r["times"]) / 1e3) if world == 1 else None,
         "ms_per_frame": statistics.mean(r["times"]),
@@ -686,6 +688,14 @@ def run_ours(args):
 FP32_TFLOPS_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 
 
+def _measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured bf16 burst (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback bf16 burst"
+
+
 def _measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -699,6 +709,12 @@ def _measured_hbm():
 # Jacobi polar rotation ~1200, re-orthonormalisation 372, S = R1^T M 558,
 # rotation correction 305, p = R A 468, D and |D|^2 369, forces 738
 LOCAL_FLOP_PER_TET = 5160.0
+# DRAM bytes per tet of k_elastic_df_b (ncu dram__bytes_read.sum + write.sum
+# of one 16-frame launch on face_shell_30k, 151.8 + 182.0 MB over 16 x 148,056
+# tets; profiles/k_elastic_df_b_face30k_batch16.md), scaled to a launch by its
+# tets; traffic grows with the tets a launch processes
+LOCAL_DRAM_BYTES_PER_TET = 140.9
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rates
 
 
 def batch_rooflines(bprof, info):
@@ -724,7 +740,10 @@ def batch_rooflines(bprof, info):
                       "frac": ach / FP32_TFLOPS_PEAK,
                       "work": f"{LOCAL_FLOP_PER_TET:.0f} float32 flop per tet x T x frames",
                       "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
-                      "bytes_per_launch": (96.0 + 144.0 * nb) * T + 48.0 * n * nb})
+                      "bytes_per_launch": (96.0 + 144.0 * nb) * T + 48.0 * n * nb,
+                      "traffic": LOCAL_DRAM_BYTES_PER_TET * T * nb,
+                      "traffic_source": "ncu DRAM bytes of a 16-frame launch, per tet, x tets "
+                                        "of this launch"})
         elif cls in ("trsv_fwd", "trsv_bwd"):
             lv = max(int(info["n_levels"]), 1)
             byts = (4.0 * nnz + 2 * 4.0 * 3 * nb * int(info["n_free"])) / lv
@@ -735,11 +754,15 @@ def batch_rooflines(bprof, info):
                       "work": "float32 factor entries (read once for all frames) + right-hand "
                               "sides in and out, per level launch (total / levels)"})
         elif cls == "sigma_gemv":
-            byts = 4.0 * n2 * n2 + 2 * 4.0 * 3 * nb * n2
-            ach = byts / (avg * 1e-3) / 1e9
-            e.update({"bound": "hbm", "kernel": "k_gemm_mr + k_unpack_mr", "achieved": ach,
-                      "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": hbm_src,
-                      "work": "float32 Sigma^-1 once + right-hand sides in and out"})
+            nr = (3 * nb + 31) // 32 * 32
+            flop = 3 * 2.0 * n2 * n2 * nr
+            ach = flop / (avg * 1e-3) / 1e12
+            pk, pk_src = _measured_bf16()
+            pk *= TF32_PER_BF16
+            e.update({"bound": "tensor", "kernel": "k_sinv_tc (tcgen05 kind::tf32) + k_unpack_mr",
+                      "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                      "peak_source": pk_src + " x nominal TF32/BF16 ratio 1.1/2.25",
+                      "work": "3 TF32 products (head/tail split) x 2 n2^2 nr flop"})
         elif cls in ("reduced", "chol"):
             flop = 18.0 * sum(st["sum_nc3"] for st in bprof["stats"]) / it
             ach = flop / (avg * 1e-3) / 1e12
