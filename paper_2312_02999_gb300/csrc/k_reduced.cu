@@ -283,7 +283,8 @@ __device__ void cta_lt_apply(const FT* L, int nc, const VT* p, FT* q) {
   }
 }
 
-// z2 = u - (Sigma^-1[:, c] (x) I_3) v, one warp per row (warp w of nw)
+// z2 = u - (Sigma^-1[:, c] (x) I_3) v, one warp per row (warp w of nw): the
+// form for a single frame, which has few rows to spread over the GPU
 template <typename FT>
 __device__ void z2_update(const RedArgs<FT>& a, int nc, int w, int nw) {
   const int lane = threadIdx.x & 31;
@@ -309,9 +310,35 @@ __device__ void z2_update(const RedArgs<FT>& a, int nc, int w, int nw) {
   }
 }
 
+// The same with one row per lane (warp w of nw takes rows 32 w .. 32 w + 31,
+// then strides by 32 nw): the form for batches, whose frames together give
+// enough warps.  Sigma^-1 is stored exactly symmetric (both triangles from
+// one product), so row q's entries at the contact columns are read as
+// Sigma^-1[c_m][q]: consecutive lanes read consecutive addresses and no
+// cross-lane reduction is needed (each float64 warp instruction costs about
+// 64 cycles of its SM sub-partition on GB300, so this halves the cost)
+template <typename FT>
+__device__ void z2_update_rows(const RedArgs<FT>& a, int nc, int w, int nw) {
+  const int lane = threadIdx.x & 31;
+  for (int q0 = 32 * w; q0 < a.n2; q0 += 32 * nw) {
+    const int q = q0 + lane;
+    if (q >= a.n2) continue;
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int m = 0; m < nc; ++m) {
+      const int c = a.clist[m];
+      if (!FSIM_CHECK_IDX(c, a.n2, CHECK_CLIST)) continue;
+      const double sv = a.Sinv[(size_t)c * a.n2 + q];
+      a0 += sv * a.v[3 * m]; a1 += sv * a.v[3 * m + 1]; a2 += sv * a.v[3 * m + 2];
+    }
+    a.z2[3 * q] = a.u[3 * q] - a0;
+    a.z2[3 * q + 1] = a.u[3 * q + 1] - a1;
+    a.z2[3 * q + 2] = a.u[3 * q + 2] - a2;
+  }
+}
+
 // The z2 update alone (plain launch) after the one-CTA or cluster path; with
 // n_c = 0 it copies z2 = u.
-__device__ __forceinline__ void k_z2_update_body(RedArgs<float> a) {
+__device__ __forceinline__ void k_z2_update_body(RedArgs<float> a, bool rows) {
   const int nc = *a.nc_dev;
   if (nc == 0) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * a.n2; e += gridDim.x * blockDim.x)
@@ -320,10 +347,12 @@ __device__ __forceinline__ void k_z2_update_body(RedArgs<float> a) {
   }
   if (nc > a.small_lim) return;         // the cooperative kernel owns larger n_c
   red_layout(a, nc);
-  z2_update(a, nc, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  if (rows) z2_update_rows(a, nc, w, nw);
+  else z2_update(a, nc, w, nw);
 }
 __global__ void __launch_bounds__(256) k_z2_update(RedArgs<float> a) {
-  k_z2_update_body(a);
+  k_z2_update_body(a, false);
 }
 
 template <typename FT>
@@ -1629,7 +1658,7 @@ __global__ void __maxnreg__(128) k_clus_v_b(const RedArgs<float>* __restrict__ A
 }
 __global__ void __launch_bounds__(256) k_z2_update_b(const RedArgs<float>* __restrict__ A) {
   const RedArgs<float> a = A[blockIdx.y];
-  if (a.active) k_z2_update_body(a);
+  if (a.active) k_z2_update_body(a, true);
 }
 
 // x1 = bx1 + Phi[:, c] v for every frame and any n_c (v from whichever path
@@ -1751,8 +1780,10 @@ cudaError_t reduced_solve_b(cudaStream_t s, const void* args_dev, const void* ar
     count_launch();
     if (e != cudaSuccess) return e;
   }
-  // float64 row products: enough warps per frame to keep the float64 pipes busy
-  const int zgrid = std::max(2, std::min(8 * std::max(1, num_sms) / nb, 64));
+  // float64 row products, one row per lane: 256 rows per CTA of 8 warps,
+  // enough CTAs to cover the rows of every frame (at least 2 per frame, also
+  // for the n_c = 0 copy)
+  const int zgrid = std::max(2, (H[0].n2 + 255) / 256);
   k_z2_update_b<<<dim3(zgrid, nb), 256, 0, s>>>(A);
   count_launch();
   return cudaGetLastError();

@@ -483,14 +483,13 @@ __global__ void k_gather_rhs_mr(const DevMesh* __restrict__ tab, float* __restri
 }
 
 // per frame: u (float64) and y2 (float) in the frame's own buffers for the
-// reduced system; x2 rows of the contact-free backward solve = u (all columns)
+// reduced system (the x2 rows of the contact-free backward solve get u by one
+// contiguous copy)
 __global__ void k_unpack_mr(const DevMesh* __restrict__ tab, const float* __restrict__ ub,
-                            const float* __restrict__ rb, float* __restrict__ bx, int nr) {
+                            const float* __restrict__ rb, int nr) {
   const DevMesh& m = tab[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n2) return;
-  if (blockIdx.y == 0)
-    for (int j = 0; j < nr; ++j) bx[(size_t)(m.n1 + i) * nr + j] = ub[(size_t)i * nr + j];
   if (!m.active) return;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -713,8 +712,12 @@ cudaError_t global_step_b(const BatchStep& bs) {
                                                              bs.ub, nr);
       count_launch();
     }
-    k_unpack_mr<<<dim3((n2 + 255) / 256, nb), 256, 0, s>>>(bs.tab, bs.ub, bs.rb, bs.bx, nr);
+    k_unpack_mr<<<dim3((n2 + 255) / 256, nb), 256, 0, s>>>(bs.tab, bs.ub, bs.rb, nr);
     count_launch();
+    // x2 rows of the contact-free backward solve = u, all columns (same row stride)
+    e = cudaMemcpyAsync(bs.bx + (size_t)n1 * nr, bs.ub, sizeof(float) * (size_t)n2 * nr,
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
   }
   // the contact-free backward solve x1 = L1^-T (y1 - L21^T u) on the side
   // stream while the reduced systems are solved
