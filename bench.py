@@ -51,10 +51,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-target", type=int, default=30000)
-    ap.add_argument("--streams", type=int, default=64,
+    # 96 sequences in three concurrent 32-frame batches: 149 frames/s at p50 / p99
+    # 0.58 / 0.62 s on one GB300 (64 in two batches: 135 at 0.41 / 0.46 s; 128 in
+    # four: 155 at 0.76 / 0.82 s)
+    ap.add_argument("--streams", type=int, default=96,
                     help="concurrent frame sequences of the headline (batch-mode) leg")
     ap.add_argument("--batch-frames", type=int, default=32, help="frames per lock-step batch")
-    ap.add_argument("--batch-workers", type=int, default=2, help="concurrent batches")
+    ap.add_argument("--batch-workers", type=int, default=3, help="concurrent batches")
     ap.add_argument("--lowlat-streams", type=int, default=8,
                     help="sequences (and per-request workers) of the low-latency leg")
     ap.add_argument("--fp64-steps", type=int, default=2,
