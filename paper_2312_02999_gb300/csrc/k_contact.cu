@@ -214,6 +214,135 @@ k_cand_ee(int Ns, int Ne, const double* __restrict__ s, const double* __restrict
   }
 }
 
+// Pass A, one warp per pair (single frames: few pairs, so the latency of
+// a pair's chain sets the time and the lanes share its Jacobi rotations and
+// lift).  Per-pair gradient and PSD Hessian blocks (PositiveDefinite of
+// Algorithm 1); marks the touched x2 vertices.  One warp per pair: the
+// reduced (n <= 5) Hessian is built redundantly by every lane, each cyclic
+// Jacobi rotation updates its rows, columns and eigenvectors lane-parallel,
+// and the 144 block entries of the lift are spread over the lanes.  ET is the
+// type of the small eigen-solve (float64, or float32 in the mixed form).
+// One pair-warp per CTA: the float64 geometry of a pair is a long chain of
+// float64 instructions, and an SM's float64 pipe is narrow on this part, so
+// the pairs are spread over as many SMs as possible.
+constexpr int kPairWarps = 1;
+
+template <typename ET>
+__device__ __forceinline__ void k_barrier_pairs_warp_body(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+                const double* __restrict__ s, const int* __restrict__ tris,
+                const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
+                const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
+                double kappa, double* __restrict__ pgrad, double* __restrict__ phess,
+                int* __restrict__ x2mark) {
+  __shared__ ET As[kPairWarps][5][5];
+  __shared__ ET Qs[kPairWarps][5][5];
+  __shared__ double Hp[kPairWarps][5][5];
+  __shared__ double hv[kPairWarps][4][3];
+  __shared__ double sq[kPairWarps][4][4];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t np = *count;
+  np = np < cap ? np : cap;
+  for (int64_t p = blockIdx.x * (int64_t)kPairWarps + w; p < np;
+       p += (int64_t)gridDim.x * kPairWarps) {
+    int type, i, j;
+    unpack_key(pairs[p], type, i, j);
+    int V[4];
+    load_pair(type, i, j, tris, edges, V);
+    double X[4][3];
+    gather_X(s, V, X);
+    PairReduced r;
+    pair_reduced(type, X, dhat, kappa, r);
+    const int n = r.n;
+    if (lane < 25) {
+      const int a = lane / 5, b = lane % 5;
+      As[w][a][b] = (ET)r.A[a][b];
+      Qs[w][a][b] = a == b ? ET(1) : ET(0);
+    }
+    __syncwarp();
+    const ET tiny = sizeof(ET) == 8 ? ET(1e-300) : ET(1e-30);
+    const ET tol = sizeof(ET) == 8 ? ET(1e-30) : ET(1e-13);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      ET off = 0, dia = 0;
+      for (int a = 0; a < n; ++a) {
+        dia += As[w][a][a] * As[w][a][a];
+        for (int b = a + 1; b < n; ++b) off += As[w][a][b] * As[w][a][b];
+      }
+      if (!(off > tol * dia)) break;
+      for (int pp = 0; pp < n - 1; ++pp)
+        for (int qq = pp + 1; qq < n; ++qq) {
+          const ET apq = As[w][pp][qq];
+          if (!(fabs(apq) > tiny)) continue;
+          const ET app = As[w][pp][pp], aqq = As[w][qq][qq];
+          const ET th = (aqq - app) / (ET(2) * apq);
+          const ET t = (th >= ET(0) ? ET(1) : ET(-1)) / (fabs(th) + sqrt(th * th + ET(1)));
+          const ET c = ET(1) / sqrt(t * t + ET(1)), sn = t * c;
+          ET x0 = 0, x1 = 0;
+          const bool rowl = lane < n && lane != pp && lane != qq;
+          const bool qlan = lane >= 8 && lane < 8 + n;
+          if (rowl) { x0 = As[w][lane][pp]; x1 = As[w][lane][qq]; }
+          if (qlan) { x0 = Qs[w][lane - 8][pp]; x1 = Qs[w][lane - 8][qq]; }
+          __syncwarp();
+          if (rowl) {
+            const ET np_ = c * x0 - sn * x1, nq = sn * x0 + c * x1;
+            As[w][lane][pp] = np_; As[w][pp][lane] = np_;
+            As[w][lane][qq] = nq; As[w][qq][lane] = nq;
+          }
+          if (qlan) {
+            Qs[w][lane - 8][pp] = c * x0 - sn * x1;
+            Qs[w][lane - 8][qq] = sn * x0 + c * x1;
+          }
+          if (lane == 16) As[w][pp][pp] = app - t * apq;
+          if (lane == 17) As[w][qq][qq] = aqq + t * apq;
+          if (lane == 18) { As[w][pp][qq] = ET(0); As[w][qq][pp] = ET(0); }
+          __syncwarp();
+        }
+    }
+    // projection: keep eigenvalues above a relative floor (zero in float64;
+    // float32 rounding noise of the largest one in the mixed form)
+    ET lmax = 0;
+    for (int a = 0; a < n; ++a) lmax = fmax(lmax, As[w][a][a]);
+    const ET floor_ = sizeof(ET) == 8 ? ET(0) : ET(1e-6) * lmax;
+    if (lane < 25) {
+      const int a = lane / 5, b = lane % 5;
+      double acc = 0.0;
+      if (a < n && b < n)
+        for (int l = 0; l < n; ++l) {
+          const ET lam = As[w][l][l];
+          if (lam > floor_) acc += (double)Qs[w][a][l] * (double)lam * (double)Qs[w][b][l];
+        }
+      Hp[w][a][b] = acc;
+    }
+    __syncwarp();
+    const int k = r.k;
+    if (lane < 12) {                  // hv[i][a] = sum_m q_m[i] Hp[a][3+m]
+      const int ii = lane / 3, a = lane % 3;
+      double acc = 0.0;
+      for (int m = 0; m < k; ++m) acc += r.q[m][ii] * Hp[w][a][3 + m];
+      hv[w][ii][a] = acc;
+    } else if (lane < 28) {           // sq[i][j] = sum q_m[i] q_l[j] Hp[3+m][3+l]
+      const int ii = (lane - 12) / 4, jj = (lane - 12) % 4;
+      double acc = 0.0;
+      for (int m = 0; m < k; ++m)
+        for (int l = 0; l < k; ++l) acc += r.q[m][ii] * r.q[l][jj] * Hp[w][3 + m][3 + l];
+      sq[w][ii][jj] = acc;
+    }
+    __syncwarp();
+    if (lane < 12) pgrad[p * 12 + lane] = r.gfac * r.c[lane / 3] * r.vh[lane % 3];
+    for (int e = lane; e < 144; e += 32) {
+      const int ab = e / 9, rc = e % 9;
+      const int ii = ab / 4, jj = ab % 4, a = rc / 3, b = rc % 3;
+      phess[p * 144 + e] = r.ch[ii] * r.ch[jj] * Hp[w][a][b] + r.ch[ii] * hv[w][jj][a] * r.vh[b] +
+                           r.ch[jj] * r.vh[a] * hv[w][ii][b] + sq[w][ii][jj] * r.vh[a] * r.vh[b];
+    }
+    if (lane < 4)
+      for (int64_t e = Wptr[V[lane]]; e < Wptr[V[lane] + 1]; ++e) {
+        const int q = x2of[Wcol[e]];
+        if (q >= 0) x2mark[q] = 1;
+      }
+    __syncwarp();
+  }
+}
+
 // Pass A: per-pair gradient and PSD Hessian blocks (PositiveDefinite of
 // Algorithm 1); marks the touched x2 vertices.  One lane per pair: the
 // distance, barrier and pair Hessian in a reduced basis of <= 5 coordinates
@@ -222,9 +351,11 @@ k_cand_ee(int Ns, int Ne, const double* __restrict__ s, const double* __restrict
 // the lift to the 12 gradient entries and 144 Hessian entries.  GB300 issues
 // a warp-wide float64 instruction about every 64 cycles per SM
 // sub-partition, so the float64 geometry costs per warp instruction: with a
-// pair per lane one instruction serves 32 pairs (a warp per pair, as before,
-// spent the same instruction on one).  One warp per CTA spreads the pairs
-// over as many SMs as possible.
+// pair per lane one instruction serves 32 pairs (the warp-per-pair form
+// spends it on one).  This is the form for batches, whose frames together
+// have thousands of pairs; a single frame's hundred or so pairs finish sooner
+// with a warp per pair, whose lanes share a pair's rotations and lift.  One
+// warp per CTA spreads the pairs over as many SMs as possible.
 constexpr int kPairLanes = 32;
 
 template <typename ET>
@@ -375,13 +506,13 @@ __device__ __forceinline__ void k_barrier_pairs_body(const int* __restrict__ cou
                           x2mark);
 }
 template <typename ET>
-__global__ void __launch_bounds__(kPairLanes) k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+__global__ void __launch_bounds__(32 * kPairWarps) k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
                 const double* __restrict__ s, const int* __restrict__ tris,
                 const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
                 const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
                 double kappa, double* __restrict__ pgrad, double* __restrict__ phess,
                 int* __restrict__ x2mark) {
-  k_barrier_pairs_body<ET>(count, cap, pairs, s, tris, edges, Wptr, Wcol, x2of, dhat, kappa, pgrad, phess, x2mark);
+  k_barrier_pairs_warp_body<ET>(count, cap, pairs, s, tris, edges, Wptr, Wcol, x2of, dhat, kappa, pgrad, phess, x2mark);
 }
 
 // Edge-edge mollifier (optional): for EE pairs with c = |e_a x e_b|^2 below
@@ -1185,15 +1316,15 @@ void launch_barrier_pairs(cudaStream_t st, const DevMesh& m, int64_t np, const d
   np = np < m.cap_act ? np : m.cap_act;
   if (np <= 0) return;
   ProfScope ps(PROF_BARRIER, st);
-  const int64_t want = (np + kPairLanes - 1) / kPairLanes;      // one lane per pair
+  const int64_t want = (np + kPairWarps - 1) / kPairWarps;      // one warp per pair
   const unsigned grid = (unsigned)(want < 8 * 152 ? want : 8 * 152);
-  const unsigned mgrid = (unsigned)(np < 8 * 152 ? np : 8 * 152);  // mollifier: a warp per pair
+  const unsigned mgrid = grid;
   if (precision == 0)
-    k_barrier_pairs<double><<<grid, kPairLanes, 0, st>>>(
+    k_barrier_pairs<double><<<grid, 32 * kPairWarps, 0, st>>>(
         m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);
   else
-    k_barrier_pairs<float><<<grid, kPairLanes, 0, st>>>(
+    k_barrier_pairs<float><<<grid, 32 * kPairWarps, 0, st>>>(
         m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);
   count_launch();
