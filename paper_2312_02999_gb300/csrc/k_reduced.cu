@@ -865,24 +865,60 @@ __global__ void __launch_bounds__(256) k_small_x(RedArgs<float> a) {
 }
 
 // k_small_n (grid): N = I + (L_s (x) I_3)^T X, lower part, packed.
-__device__ __forceinline__ void k_small_n_body(RedArgs<float> a) {
+// N = I + (L_s (x) I_3)^T X, lower triangle, by 32 x 32 tiles: CTA `tile`
+// takes row tile ti and column tile tj <= ti of the lower triangle (tiles
+// beyond 3 n_c exit).  Entry (row = 3 i + ax, col) is 1[row == col] plus the
+// sum over j >= i of L_s[j][i] X[3 j + ax][col], accumulated in increasing j.
+// X rows 3 j + ax and the tile's L_s entries are staged in shared memory
+// kNJ values of j at a time; a thread keeps 4 rows of one column.
+constexpr int kNJ = 16;
+constexpr int kNTiles = (3 * kClusNc + 31) / 32 * ((3 * kClusNc + 31) / 32 + 1) / 2;
+__device__ __forceinline__ void k_small_n_body(RedArgs<float> a, int tile) {
+  __shared__ float Xs[3 * kNJ][32];
+  __shared__ float Ls[kNJ][12];
   const int nc = *a.nc_dev;
   if (nc == 0 || nc > a.small_lim) return;
+  const int n3 = 3 * nc, nt = (n3 + 31) / 32;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+  const int tj = tile - ti * (ti + 1) / 2;
   red_layout(a, nc);
-  const int n3 = 3 * nc;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
-  for (int e = gtid; e < n3 * n3; e += gsz) {
-    const int row = e / n3, col = e % n3;
-    if (col > row) continue;
-    const int i = row / 3, ax = row % 3;
-    float acc = (row == col) ? 1.f : 0.f;
-#pragma unroll 8
-    for (int j = i; j < nc; ++j) acc += a.S[(size_t)j * nc + i] * a.X[(size_t)(3 * j + ax) * n3 + col];
-    a.N[prow(row) + col] = acc;        // packed lower, the layout k_small_v factors in
+  const int R0 = 32 * ti, C0 = 32 * tj, i0 = R0 / 3;
+  const int tid = threadIdx.x, col = tid & 31, rw = tid >> 5;
+  int iv[4], ax[4];
+  float acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int row = R0 + rw + 8 * q;
+    iv[q] = row / 3 - i0;            // 0 .. 11
+    ax[q] = row % 3;
+    acc[q] = (row == C0 + col) ? 1.f : 0.f;
+  }
+  for (int j0 = i0; j0 < nc; j0 += kNJ) {
+    __syncthreads();
+    for (int e = tid; e < 3 * kNJ * 32; e += blockDim.x) {
+      const int rr = e >> 5, c = e & 31, xr = 3 * j0 + rr;
+      Xs[rr][c] = (xr < n3 && C0 + c < n3) ? a.X[(size_t)xr * n3 + C0 + c] : 0.f;
+    }
+    for (int e = tid; e < kNJ * 12; e += blockDim.x) {
+      const int jj = e / 12, ii = e % 12, j = j0 + jj, i = i0 + ii;
+      Ls[jj][ii] = (j < nc && i < nc && j >= i) ? a.S[(size_t)j * nc + i] : 0.f;
+    }
+    __syncthreads();
+    const int jn = min(kNJ, nc - j0);
+    for (int jj = 0; jj < jn; ++jj)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += Ls[jj][iv[q]] * Xs[3 * jj + ax[q]][col];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int row = R0 + rw + 8 * q, c = C0 + col;
+    if (row < n3 && c <= row) a.N[prow(row) + c] = acc[q];   // packed lower (k_small_v's layout)
   }
 }
 __global__ void __launch_bounds__(256) k_small_n(RedArgs<float> a) {
-  k_small_n_body(a);
+  k_small_n_body(a, blockIdx.x);
 }
 
 // q = (L_s (x) I_3)^T p (float; L_s packed plain, in shared memory)
@@ -1528,7 +1564,7 @@ cudaError_t launch_reduced_t(cudaStream_t s, const DevMesh& m, const double* u, 
     } else {
       k_small_s<<<1, kST, kSmallSmemS, s>>>(a);
       k_small_x<3><<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
-      k_small_n<<<2 * std::max(1, num_sms), 256, 0, s>>>(a);
+      k_small_n<<<kNTiles, 256, 0, s>>>(a);
       count_launch(3);
     }
     if (want_small) {
@@ -1644,7 +1680,7 @@ __global__ void __launch_bounds__(kST) k_small_s_b(const RedArgs<float>* __restr
 }
 __global__ void __launch_bounds__(256) k_small_n_b(const RedArgs<float>* __restrict__ A) {
   const RedArgs<float> a = A[blockIdx.y];
-  if (a.active) k_small_n_body(a);
+  if (a.active) k_small_n_body(a, blockIdx.x);
 }
 __global__ void __launch_bounds__(kST) k_small_v_b(const RedArgs<float>* __restrict__ A) {
   const RedArgs<float> a = A[blockIdx.y];
@@ -1730,7 +1766,7 @@ cudaError_t reduced_prepare_b(cudaStream_t s2, const void* args_dev, int nb, int
   ProfScope ps(PROF_CHOL, s2);
   k_small_s_b<<<dim3(1, nb), kST, kSmallSmemS, s2>>>(A);
   k_small_x_b<2><<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s2>>>(A);
-  k_small_n_b<<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s2>>>(A);
+  k_small_n_b<<<dim3(kNTiles, nb), 256, 0, s2>>>(A);
   count_launch(3);
   return cudaGetLastError();
 }
@@ -1819,7 +1855,7 @@ bool reduced_prepare(cudaStream_t s, const DevMesh& m, const double* u, const vo
     ProfScope ps(PROF_CHOL, s2);
     k_small_s<<<1, kST, kSmallSmemS, s2>>>(a);
     k_small_x<2><<<2 * std::max(1, num_sms), 256, 0, s2>>>(a);
-    k_small_n<<<2 * std::max(1, num_sms), 256, 0, s2>>>(a);
+    k_small_n<<<kNTiles, 256, 0, s2>>>(a);
     count_launch(3);
   }
   // the join is recorded even if a launch failed, so the fork always closes
