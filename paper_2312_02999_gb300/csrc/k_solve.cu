@@ -224,10 +224,15 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
          const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr,
          int nf) {
-  extern __shared__ float bj[];                    // kFwdColSplit x 32
-  __shared__ __align__(16) float Zs[2][kMrK][32];
-  __shared__ float part[8][32][32];                // warp partial sums (no padding needed:
-                                                   // lanes always index the last dimension)
+  // the two factor tiles and the staged right-hand sides (16 KB each) during
+  // the k loop; the warps' partial sums (8 x 32 x 32 floats, lanes indexing
+  // the last dimension) in the same 32 KB after it, so that 7 CTAs fit an SM
+  __shared__ __align__(16) float sh[2 * kMrK * 32 + kFwdColSplit * kMrCols];
+  static_assert(8 * 32 * 32 == 2 * kMrK * 32 + kFwdColSplit * kMrCols,
+                "partial sums must fill the tile and right-hand-side buffer");
+  float (*Zs)[kMrK][32] = reinterpret_cast<float (*)[kMrK][32]>(sh);
+  float* bj = sh + 2 * kMrK * 32;                  // (columns of the item) x 32
+  float (*part)[32][32] = reinterpret_cast<float (*)[32][32]>(sh);
   const int4 it = items[blockIdx.x];
   const int J = it.x, r0 = it.y, rn = it.z, kb = it.w;   // columns [kb, kb + kFwdColSplit)
   const int cc = blockIdx.y * kMrCols;
@@ -697,8 +702,7 @@ cudaError_t global_step_b(const BatchStep& bs) {
     const int a = m.h_fwd_mr_ptr[l], z = m.h_fwd_mr_ptr[l + 1];
     if (z <= a) continue;
     ProfScope ps(PROF_TRSV_FWD, s);
-    const size_t sm = sizeof(float) * kMrCols * (size_t)std::min(m.h_level_maxns[l], kFwdColSplit);
-    k_fwd_mr<<<dim3(z - a, chunks), 256, sm, s>>>(m.fwd_items_mr + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+    k_fwd_mr<<<dim3(z - a, chunks), 256, 0, s>>>(m.fwd_items_mr + a, m.sn_c0, m.sn_ns, m.sn_nr1,
                                                    m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.rb,
                                                    bs.yb, nr, nf);
     count_launch();
@@ -768,10 +772,6 @@ bool batch_supported(const DevMesh& m, int nr) {
 }
 
 void set_solver_smem_limits(int max_bytes) {
-  // k_fwd_mr: its staged right-hand sides (up to kFwdColSplit x 32 floats,
-  // 16 KB) beside 48 KB of static shared memory
-  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(float) * kMrCols * kFwdColSplit));
   tc_set_smem_limits();
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);
