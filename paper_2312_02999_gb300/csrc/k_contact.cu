@@ -903,6 +903,40 @@ __device__ __forceinline__ void gather_Xf(const float* sf, const int V[4], float
     for (int d = 0; d < 3; ++d) X[k][d] = sf[3 * (size_t)V[k] + d];
 }
 
+// Tile-pair culling for the all-pairs sweeps: every thread of a kTile block
+// contributes its i-side box (inflated, `a`; empty if out of range) and the
+// j-tile box it staged (plain, `b`; empty if out of range); the block's
+// unions are compared, and a tile pair whose unions do not overlap holds no
+// overlapping pair (ov32 per axis), so the block may skip it.  Every thread
+// of the block must call this.
+__device__ __forceinline__ bool tile_pair_overlaps(const float* a, const float* b) {
+  __shared__ float red[kTile / 32][12];
+  float u[12];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    u[q] = a[q]; u[3 + q] = a[3 + q]; u[6 + q] = b[q]; u[9 + q] = b[3 + q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const float w = __shfl_xor_sync(0xffffffffu, u[q], o);
+      u[q] = (q % 6) < 3 ? fminf(u[q], w) : fmaxf(u[q], w);
+    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) red[wid][q] = u[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    float r = red[0][q];
+    for (int w = 1; w < kTile / 32; ++w) r = (q % 6) < 3 ? fminf(r, red[w][q]) : fmaxf(r, red[w][q]);
+    u[q] = r;
+  }
+  return ov32(u, u + 6);
+}
+
 struct SweepArgs {
   int Ns, Nt, Ne;
   const float* box;
@@ -945,10 +979,15 @@ __device__ __forceinline__ void k_sweep_pt_body(SweepArgs a) {
   }
   __syncthreads();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= a.Ns) return;
-  float vb[6];
+  float vb[6], tbk[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) vb[q] = a.box[12 * (size_t)v + q];
+  for (int q = 0; q < 6; ++q) {
+    const float e = q < 3 ? INFINITY : -INFINITY;     // empty box
+    vb[q] = v < a.Ns ? a.box[12 * (size_t)v + q] : e;
+    tbk[q] = t0 + (int)threadIdx.x < a.Nt ? tb[threadIdx.x][q] : e;
+  }
+  if (!tile_pair_overlaps(vb, tbk)) return;
+  if (v >= a.Ns) return;
   unsigned long long vk[6];
   if (MODE == 1) {
 #pragma unroll
@@ -999,11 +1038,16 @@ __device__ __forceinline__ void k_sweep_ee_body(SweepArgs a) {
   }
   __syncthreads();
   const int i = blockIdx.x * kTile + threadIdx.x;
+  float ib[6], ebk[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float e = q < 3 ? INFINITY : -INFINITY;     // empty box
+    ib[q] = i < a.Ne ? a.box[12 * (size_t)(eoff + i) + q] : e;
+    ebk[q] = j0 + (int)threadIdx.x < a.Ne ? eb[threadIdx.x][q] : e;
+  }
+  if (!tile_pair_overlaps(ib, ebk)) return;
   if (i >= a.Ne) return;
   const int i0 = a.edges[2 * i], i1 = a.edges[2 * i + 1];
-  float ib[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) ib[q] = a.box[12 * (size_t)(eoff + i) + q];
   unsigned long long ikk[6];
   if (MODE == 1) {
 #pragma unroll
