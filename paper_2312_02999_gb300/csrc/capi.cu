@@ -80,9 +80,7 @@ void free_mesh(MeshState& ms) {
   delete[] ms.d.h_fwd_ptr;
   delete[] ms.d.h_bwd_ptr;
   delete[] ms.d.h_bwd32_ptr;
-  delete[] ms.d.h_fwd_mr_ptr;
   ms.d.h_bwd32_ptr = nullptr;
-  ms.d.h_fwd_mr_ptr = nullptr;
   ms.d.h_level_ptr = nullptr;
   ms.d.h_level_maxns = nullptr;
   ms.d.h_level_maxld = nullptr;
@@ -828,14 +826,12 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   m.h_fwd_ptr = new int[f.n_levels + 1];
   m.h_bwd_ptr = new int[f.n_levels + 1];
   m.h_bwd32_ptr = new int[f.n_levels + 1];
-  m.h_fwd_mr_ptr = new int[f.n_levels + 1];
   // work items: forward = 32-row chunks of Z_J, backward = 8-column chunks
   // (32-column chunks for the multi-right-hand-side backward solve)
-  std::vector<int4> fwd, bwd, bwd32, fwd_mr;
+  std::vector<int4> fwd, bwd, bwd32;
   m.h_fwd_ptr[0] = 0;
   m.h_bwd_ptr[0] = 0;
   m.h_bwd32_ptr[0] = 0;
-  m.h_fwd_mr_ptr[0] = 0;
   for (int l = 0; l <= f.n_levels; ++l) m.h_level_ptr[l] = f.level_ptr[l];
   for (int l = 0; l < f.n_levels; ++l) {
     int mx = 1, mxld = 1;
@@ -844,13 +840,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
       const int ldj = ns[J] + nr1[J];
       mx = std::max(mx, ns[J]);
       mxld = std::max(mxld, ldj);
-      for (int r0 = 0; r0 < ldj; r0 += 32) {
-        fwd.push_back(make_int4(J, r0, std::min(32, ldj - r0), 0));
-        // rows of the diagonal block only need columns k <= row
-        const int kend = r0 < ns[J] ? std::min(ns[J], r0 + 32) : ns[J];
-        for (int k0 = 0; k0 < kend; k0 += kFwdColSplit)
-          fwd_mr.push_back(make_int4(J, r0, std::min(32, ldj - r0), k0));
-      }
+      for (int r0 = 0; r0 < ldj; r0 += 32) fwd.push_back(make_int4(J, r0, std::min(32, ldj - r0), 0));
       for (int k0 = 0; k0 < ns[J]; k0 += 8) bwd.push_back(make_int4(J, k0, std::min(8, ns[J] - k0), 0));
       // 32 columns and up to kBwdRowSplit rows each: the long row ranges of
       // the top supernodes spread over many CTAs (partial sums added atomically)
@@ -863,12 +853,10 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
     m.h_fwd_ptr[l + 1] = (int)fwd.size();
     m.h_bwd_ptr[l + 1] = (int)bwd.size();
     m.h_bwd32_ptr[l + 1] = (int)bwd32.size();
-    m.h_fwd_mr_ptr[l + 1] = (int)fwd_mr.size();
   }
   TRY(upload(ms, s, &m.fwd_items, fwd.data(), fwd.size()));
   TRY(upload(ms, s, &m.bwd_items, bwd.data(), bwd.size()));
   TRY(upload(ms, s, &m.bwd_items32, bwd32.data(), bwd32.size()));
-  TRY(upload(ms, s, &m.fwd_items_mr, fwd_mr.data(), fwd_mr.size()));
   TRY(upload(ms, s, &m.Sinv, f.sigma_inv.data(), f.sigma_inv.size()));
   if (p->solver == FSIM_SOLVER_SCHUR && !f.sigma.empty())
     TRY(upload(ms, s, &m.Sig, f.sigma.data(), f.sigma.size()));

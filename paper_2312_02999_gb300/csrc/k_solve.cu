@@ -224,23 +224,18 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
          const int64_t* __restrict__ zoff, const int* __restrict__ rows,
          const float* __restrict__ Z, float* __restrict__ b, float* __restrict__ y, int nr,
          int nf) {
-  // the two factor tiles and the staged right-hand sides (16 KB each) during
-  // the k loop; the warps' partial sums (8 x 32 x 32 floats, lanes indexing
-  // the last dimension) in the same 32 KB after it, so that 7 CTAs fit an SM
-  __shared__ __align__(16) float sh[2 * kMrK * 32 + kFwdColSplit * kMrCols];
-  static_assert(8 * 32 * 32 == 2 * kMrK * 32 + kFwdColSplit * kMrCols,
-                "partial sums must fill the tile and right-hand-side buffer");
-  float (*Zs)[kMrK][32] = reinterpret_cast<float (*)[kMrK][32]>(sh);
-  float* bj = sh + 2 * kMrK * 32;                  // (columns of the item) x 32
-  float (*part)[32][32] = reinterpret_cast<float (*)[32][32]>(sh);
+  extern __shared__ float bj[];                    // ns x 32
+  __shared__ __align__(16) float Zs[2][kMrK][32];
+  __shared__ float part[8][32][32];                // warp partial sums (no padding needed:
+                                                   // lanes always index the last dimension)
   const int4 it = items[blockIdx.x];
-  const int J = it.x, r0 = it.y, rn = it.z, kb = it.w;   // columns [kb, kb + kFwdColSplit)
+  const int J = it.x, r0 = it.y, rn = it.z;
   const int cc = blockIdx.y * kMrCols;
   const int c0 = c0a[J], ns = nsa[J], ld = ns + nra[J];
   const float* Zj = Z + zoff[J];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // rows of the diagonal block only need k <= row (L_JJ^-1 is lower triangular)
-  const int kend = min(r0 < ns ? min(ns, r0 + rn) : ns, kb + kFwdColSplit);
+  const int kend = r0 < ns ? min(ns, r0 + rn) : ns;
   constexpr int kPer = kMrK * 32 / 256;            // Z elements per thread per tile
   float zr[kPer];
   auto load_z = [&](int k0) {
@@ -257,15 +252,15 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
       Zs[buf][e >> 5][e & 31] = zr[i];
     }
   };
-  load_z(kb);
-  {   // right-hand sides of the item's columns, 8 loads in flight per thread
-    const int tot = (kend - kb) * kMrCols;
+  load_z(0);
+  {   // right-hand sides of the supernode's columns, 8 loads in flight per thread
+    const int tot = ns * kMrCols;
     for (int e0 = 0; e0 < tot; e0 += 8 * 256) {
       float v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int e = e0 + tid + 256 * i;
-        v[i] = e < tot ? b[(size_t)(c0 + kb + e / kMrCols) * nr + cc + (e % kMrCols)] : 0.f;
+        v[i] = e < tot ? b[(size_t)(c0 + e / kMrCols) * nr + cc + (e % kMrCols)] : 0.f;
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -282,12 +277,12 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
 #pragma unroll
   for (int q = 0; q < 32; ++q) acc[q] = 0.f;
   int buf = 0;
-  for (int k0 = kb; k0 < kend; k0 += kMrK) {
+  for (int k0 = 0; k0 < kend; k0 += kMrK) {
     const bool more = k0 + kMrK < kend;
     if (more) load_z(k0 + kMrK);                   // next tile in flight
     const int kn = min(kMrK, kend - k0);
     for (int kk = wid; kk < kn; kk += 8) {
-      const float bk = bj[(k0 - kb + kk) * kMrCols + lane];
+      const float bk = bj[(k0 + kk) * kMrCols + lane];
       const float4* zp = reinterpret_cast<const float4*>(&Zs[buf][kk][0]);
 #pragma unroll
       for (int q4 = 0; q4 < 8; ++q4) {
@@ -311,7 +306,7 @@ k_fwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
     for (int w = 0; w < 8; ++w) t += part[w][rr][j];
     const int r = r0 + rr;
     if (r < ns) {
-      atomicAdd(y + (size_t)(c0 + r) * nr + cc + j, t);      // y zeroed before the pass
+      y[(size_t)(c0 + r) * nr + cc + j] = t;
     } else {
       const int row = rows[roff[J] + r - ns];
       if (FSIM_CHECK_IDX(row, nf, CHECK_TRSV_ROW)) atomicAdd(b + (size_t)row * nr + cc + j, -t);
@@ -695,14 +690,12 @@ cudaError_t global_step_b(const BatchStep& bs) {
   cudaError_t e = reduced_prepare_b(s2, bs.args_dev, nb, bs.num_sms);
   if (e != cudaSuccess) return e;
   if (cudaEventRecord(bs.ev[1], s2) != cudaSuccess) return cudaGetLastError();
-  // the forward result accumulates over column-split items: zeroed first
-  if (n1 > 0 && cudaMemsetAsync(bs.yb, 0, sizeof(float) * (size_t)n1 * nr, s) != cudaSuccess)
-    return cudaGetLastError();
   for (int l = 0; l < m.n_levels && n1 > 0; ++l) {
-    const int a = m.h_fwd_mr_ptr[l], z = m.h_fwd_mr_ptr[l + 1];
+    const int a = m.h_fwd_ptr[l], z = m.h_fwd_ptr[l + 1];
     if (z <= a) continue;
     ProfScope ps(PROF_TRSV_FWD, s);
-    k_fwd_mr<<<dim3(z - a, chunks), 256, 0, s>>>(m.fwd_items_mr + a, m.sn_c0, m.sn_ns, m.sn_nr1,
+    const size_t sm = sizeof(float) * kMrCols * (size_t)m.h_level_maxns[l];
+    k_fwd_mr<<<dim3(z - a, chunks), 256, sm, s>>>(m.fwd_items + a, m.sn_c0, m.sn_ns, m.sn_nr1,
                                                    m.sn_roff, m.sn_zoff, m.sn_rows, m.Zf, bs.rb,
                                                    bs.yb, nr, nf);
     count_launch();
@@ -766,12 +759,16 @@ cudaError_t launch_sinv_simt(cudaStream_t s, const DevMesh& m, const float* Y, i
 }
 
 bool batch_supported(const DevMesh& m, int nr) {
-  // (the forward items stage at most kFwdColSplit x 32 right-hand-side values)
-  return m.Zf && m.Phi_t && m.Sinvf && m.n1 > 0 && m.n2 > 0 && nr % kMrCols == 0 &&
-         m.fwd_items_mr && m.h_fwd_mr_ptr;
+  if (!m.Zf || !m.Phi_t || !m.Sinvf || m.n1 <= 0 || m.n2 <= 0 || nr % kMrCols != 0) return false;
+  int maxns = 0;
+  for (int l = 0; l < m.n_levels; ++l) maxns = std::max(maxns, m.h_level_maxns[l]);
+  return sizeof(float) * kMrCols * (size_t)maxns <= 160 * 1024;
 }
 
 void set_solver_smem_limits(int max_bytes) {
+  // k_fwd_mr: its staged right-hand sides (ns x 32 floats) beside 48 KB of
+  // static shared memory; batch_supported keeps ns x 128 B within 160 KB
+  cudaFuncSetAttribute(k_fwd_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, 170 * 1024);
   tc_set_smem_limits();
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(k_fwd_chunk<double, 256>, a, max_bytes);

@@ -79,9 +79,6 @@ struct DevMesh {
   int4* bwd_items32 = nullptr;  // (J, first column, columns <= 32, first row) for the batched
                                 // solve: rows [first row, + kBwdRowSplit) of Z_J
   int* h_bwd32_ptr = nullptr; // HOST (n_levels + 1)
-  int4* fwd_items_mr = nullptr; // (J, first row, rows <= 32, first column) for the batched
-                                // forward solve: columns [first column, + kFwdColSplit) of Z_J
-  int* h_fwd_mr_ptr = nullptr; // HOST (n_levels + 1)
   double* y1 = nullptr;       // n1*3 forward-solve scratch
   float* y1f = nullptr;
   double* Sinv = nullptr;     // n2 x n2 Schur-complement inverse (Sec. 3.2)
@@ -261,9 +258,6 @@ void launch_check_finite(cudaStream_t s, int n, const double* v, int* flag);
 
 // rows of Z_J one batched backward work item covers
 constexpr int kBwdRowSplit = 256;
-// columns of Z_J per batched forward item: the long inner products of the top
-// supernodes spread over several CTAs (partial sums added atomically)
-constexpr int kFwdColSplit = 128;
 
 // ---- lock-step batches -------------------------------------------------------
 // `tab` is a device array of nb DevMesh copies (frames of one mesh); m0 is a
