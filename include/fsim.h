@@ -123,6 +123,11 @@ typedef struct {
                                for all frames on the tensor cores (tcgen05,
                                TF32 head/tail split, about 22 significant
                                bits); nonzero: float32 SIMT product          */
+  int32_t barrier_lane_per_pair; /* single-frame solves: nonzero forms the pair
+                               gradients and PSD Hessians with one lane per pair,
+                               the form batches always use; 0 (default): one
+                               warp per pair, faster for a single frame's few
+                               hundred pairs                                  */
 } fsim_params;
 #define FSIM_SOLVER_WOODBURY 0
 #define FSIM_SOLVER_PCG 1

@@ -901,6 +901,7 @@ fsim_status fsim_prefactor(fsim_ctx_t ctx, int mesh_id, const fsim_params* p) {
   }
   m.skin = p->skin > 0.0 ? p->skin : std::max(10.0 * p->dhat, 0.25 * ms.mean_edge);
   m.one_cta_max = p->reduced_one_cta_max > 0 ? std::min(p->reduced_one_cta_max, 96) : 96;
+  m.barrier_lanes = p->barrier_lane_per_pair != 0 ? 1 : 0;
   m.ee_moll = p->ee_mollifier ? 1 : 0;
   m.cap_act = p->active_capacity > 0 ? p->active_capacity
                                      : std::max<int64_t>(1 << 16, 16 * (int64_t)std::max(m.Nt, 1));

@@ -519,6 +519,15 @@ __device__ __forceinline__ void k_barrier_pairs_body(const int* __restrict__ cou
                           x2mark);
 }
 template <typename ET>
+__global__ void __launch_bounds__(kPairLanes) k_barrier_pairs_lanes(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
+                const double* __restrict__ s, const int* __restrict__ tris,
+                const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
+                const int* __restrict__ Wcol, const int* __restrict__ x2of, double dhat,
+                double kappa, double* __restrict__ pgrad, double* __restrict__ phess,
+                int* __restrict__ x2mark) {
+  k_barrier_pairs_body<ET>(count, cap, pairs, s, tris, edges, Wptr, Wcol, x2of, dhat, kappa, pgrad, phess, x2mark);
+}
+template <typename ET>
 __global__ void __launch_bounds__(32 * kPairWarps) k_barrier_pairs(const int* __restrict__ count, int64_t cap, const unsigned long long* __restrict__ pairs,
                 const double* __restrict__ s, const int* __restrict__ tris,
                 const int* __restrict__ edges, const int64_t* __restrict__ Wptr,
@@ -1376,7 +1385,18 @@ void launch_barrier_pairs(cudaStream_t st, const DevMesh& m, int64_t np, const d
   const int64_t want = (np + kPairWarps - 1) / kPairWarps;      // one warp per pair
   const unsigned grid = (unsigned)(want < 8 * 152 ? want : 8 * 152);
   const unsigned mgrid = grid;
-  if (precision == 0)
+  if (m.barrier_lanes) {                                          // one lane per pair
+    const int64_t lw = (np + kPairLanes - 1) / kPairLanes;
+    const unsigned lgrid = (unsigned)(lw < 8 * 152 ? lw : 8 * 152);
+    if (precision == 0)
+      k_barrier_pairs_lanes<double><<<lgrid, kPairLanes, 0, st>>>(
+          m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+          m.pair_grad, m.pair_hess, m.x2mark);
+    else
+      k_barrier_pairs_lanes<float><<<lgrid, kPairLanes, 0, st>>>(
+          m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
+          m.pair_grad, m.pair_hess, m.x2mark);
+  } else if (precision == 0)
     k_barrier_pairs<double><<<grid, 32 * kPairWarps, 0, st>>>(
         m.counters, m.cap_act, m.pairs, sp, m.tris, m.edges, m.Wptr, m.Wcol, m.x2of, dhat, kappa,
         m.pair_grad, m.pair_hess, m.x2mark);

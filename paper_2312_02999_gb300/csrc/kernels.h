@@ -153,6 +153,7 @@ struct DevMesh {
   int col = 0;                // frame's column block (3 columns) in multi-RHS buffers
   int one_cta_max = 96;       // mixed reduced system: largest n_c on the one-CTA path
   int bar64 = 0;              // batched barrier: float64 pair eigen-solves for this frame
+  int barrier_lanes = 0;      // single-frame barrier: one lane per pair (else a warp)
   // Sigma^-1 split into TF32 head and tail (n2 rows, row stride sinv_ld) and
   // their TMA descriptors (host memory, owned by the mesh) for the tensor-core
   // product of the batched global step

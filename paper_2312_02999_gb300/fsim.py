@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("active_capacity", C.c_int64), ("skin", C.c_double), ("solver", C.c_int32),
                 ("cg_max_iters", C.c_int32), ("cg_tol", C.c_double), ("adaptive_kappa", C.c_int32),
                 ("ee_mollifier", C.c_int32), ("reduced_one_cta_max", C.c_int32),
-                ("sigma_product_simt", C.c_int32)]
+                ("sigma_product_simt", C.c_int32), ("barrier_lane_per_pair", C.c_int32)]
 
 
 class FrameStats(C.Structure):

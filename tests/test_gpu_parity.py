@@ -162,6 +162,29 @@ def test_barrier_gradient_and_reduced_block(fsim, slab_small):
     assert np.allclose(Bc, Bc.T, atol=1e-9 * np.abs(Bc).max())
 
 
+def test_barrier_lane_per_pair_form(fsim, ctx, slab_small):
+    # the one-lane-per-pair form of the pair terms (what batches run; here
+    # selected for a single frame) against the oracle, and against the
+    # one-warp-per-pair form on the same state (same arithmetic; the lift is
+    # associated differently, so rounding-level differences only)
+    mesh, act, mw, pr = slab_small
+    ml, _ = _pair(fsim, ctx, mesh, act, barrier_lane_per_pair=1)
+    x = _contact_x(mesh, 3e-4, seed=7, gap_shift=0.0035)
+    g, clist, Bc = ml.eval_barrier(x)
+    gw, clist_w, Bw = mw.eval_barrier(x)
+    ev = pr.evaluate(x)
+    V, gp, _ = pr._pair_terms(ev, project=False)
+    gs = np.zeros((pr.W.shape[0], 3))
+    np.add.at(gs, V.ravel(), gp.reshape(-1, 3))
+    assert _rel(g, pr.W.T @ gs) <= 1e-9
+    Bfull = pr.barrier_hessian(ev, project=True).toarray()
+    cv = np.nonzero(pr.x2_mask)[0][clist]
+    idx = (3 * cv[:, None] + np.arange(3)).ravel()
+    assert _rel(Bc, Bfull[np.ix_(idx, idx)]) <= 1e-8
+    assert np.array_equal(clist, clist_w)
+    assert _rel(g, gw) <= 1e-13 and _rel(Bc, Bw) <= 1e-12
+
+
 U32 = 2.0 ** -24     # float32 unit roundoff
 # Forward-error constant of the mixed global step (see _mixed_step_bound)
 MIXED_STEP_C = 32.0
