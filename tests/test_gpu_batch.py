@@ -112,6 +112,35 @@ def test_batch_face_frames_match_the_oracle(fsim, ctx):
         assert abs(st["iterations"] - int(gold[f"iterations{k}"])) <= 2
 
 
+def test_headline_batch_frames_match_the_oracle(fsim, ctx):
+    # the launch configuration of the headline: one 32-frame lock-step batch
+    # (96 multi-RHS columns, tensor-core Sigma^-1 product, lane-per-pair
+    # barrier) on the full 30k face; two of its frames are the stored oracle
+    # frames (frame 20 from rest, frame 21 from the oracle's frame 20), the
+    # other 30 are further frames of the sequence from rest, which must
+    # converge.  The oracle frames are placed in the middle of the batch.
+    gold = dict(np.load(GOLD))
+    mesh = I.face_shell()
+    field = I.bump_field(mesh, seed=int(gold["field_seed"]))
+    coeffs = I.keyframe_coeffs(seed=int(gold["seq_seed"]))
+    m = ctx.upload(mesh)
+    m.prefactor(fsim.params_for(mesh))
+    f20, f21 = gold["frames"].tolist()
+    reqs = []
+    for k in range(32):
+        fr = 22 + k if k not in (13, 14) else (f20 if k == 13 else f21)
+        a = I.bump_actuation(field, coeffs[fr])
+        reqs.append((m, a.fiber, a.stretch, gold["x0"] if k == 14 else None))
+    rc, xs, sts = fsim.solve_batch(ctx, reqs, max_frames=32)
+    assert rc == 0
+    assert all(st["status"] == 0 for st in sts)
+    diag = _diag(mesh)
+    for k, slot in ((0, 13), (1, 14)):
+        err = np.abs(xs[slot] - gold[f"x{k}"]).max() / diag
+        assert err <= 1e-6, (k, err)
+        assert abs(sts[slot]["iterations"] - int(gold[f"iterations{k}"])) <= 4
+
+
 def test_batch_argument_errors(fsim, ctx):
     mesh = I.two_slabs(3, 3, 2)
     m = ctx.upload(mesh)
