@@ -17,6 +17,23 @@ __device__ __forceinline__ double sqrt_t<double>(double v) { return sqrt(v); }
 template <>
 __device__ __forceinline__ float sqrt_t<float>(float v) { return sqrtf(v); }
 
+// a / b and 1 / sqrt(v): exact float64 operations; in float32 the fast
+// hardware forms (a few ulp), which the float32 polar rotation can use
+// because the mixed local step refines its rotation in double-float
+// arithmetic afterwards
+template <typename T>
+__device__ __forceinline__ T fdiv_t(T a, T b);
+template <>
+__device__ __forceinline__ double fdiv_t<double>(double a, double b) { return a / b; }
+template <>
+__device__ __forceinline__ float fdiv_t<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T v);
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+
 template <typename T>
 __device__ __forceinline__ void matmul(const T A[3][3], const T B[3][3], T C[3][3]) {
 #pragma unroll
@@ -80,9 +97,9 @@ __device__ void polar_rotation(const T M[3][3], T R[3][3]) {
       T ag = fabs(g);
       if (ag > eps * sqrt_t(a * b) && ag > tiny) {
         off += ag;
-        T zeta = (b - a) / (T(2) * g);
-        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt_t(T(1) + zeta * zeta));
-        T c = T(1) / sqrt_t(T(1) + t * t);
+        T zeta = fdiv_t(b - a, T(2) * g);
+        T t = fdiv_t(zeta >= T(0) ? T(1) : T(-1), fabs(zeta) + sqrt_t(T(1) + zeta * zeta));
+        T c = rsqrt_t(T(1) + t * t);
         T s = c * t;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -112,8 +129,8 @@ __device__ void polar_rotation(const T M[3][3], T R[3][3]) {
   for (int i = 0; i < 3; ++i) {
     const T ba = kmin == 0 ? B[i][1] : B[i][0];
     const T bb = kmin == 2 ? B[i][1] : B[i][2];
-    a[i] = sa > tiny ? ba / sa : T(0);
-    b[i] = sb > tiny ? bb / sb : T(0);
+    a[i] = sa > tiny ? fdiv_t(ba, sa) : T(0);
+    b[i] = sb > tiny ? fdiv_t(bb, sb) : T(0);
   }
   if (!(sa > tiny)) { a[0] = 1; a[1] = 0; a[2] = 0; }
   if (!(sb > tiny)) {  // any unit vector orthogonal to a
