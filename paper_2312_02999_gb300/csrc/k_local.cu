@@ -335,16 +335,14 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        F[i][j] = df_add_fast(df_add_fast(df_mul(Du[i][0], Di[0][j]), df_mul(Du[i][1], Di[1][j])),
-                         df_mul(Du[i][2], Di[2][j]));
+        F[i][j] = df_dot3(Du[i][0], Di[0][j], Du[i][1], Di[1][j], Du[i][2], Di[2][j]);
         if (i == j) F[i][j] = df_add_fast(F[i][j], df_from_float(1.f));
       }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        M[i][j] = df_add_fast(df_add_fast(df_mul(F[i][0], A[0][j]), df_mul(F[i][1], A[1][j])),
-                         df_mul(F[i][2], A[2][j]));
+        M[i][j] = df_dot3(F[i][0], A[0][j], F[i][1], A[1][j], F[i][2], A[2][j]);
     float R0[3][3];
     {
       float Mf[3][3];
@@ -373,8 +371,7 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        df acc = df_add_fast(df_add_fast(df_mul_f(M[0][j], R0[0][i]), df_mul_f(M[1][j], R0[1][i])),
-                        df_mul_f(M[2][j], R0[2][i]));
+        df acc = df_dot3_f(M[0][j], R0[0][i], M[1][j], R0[1][i], M[2][j], R0[2][i]);
         const float c = R1c[0][i] * M[0][j].hi + R1c[1][i] * M[1][j].hi + R1c[2][i] * M[2][j].hi;
         S[i][j] = df_add_fast(acc, df_from_float(c));
       }
@@ -426,8 +423,7 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        P[i][j] = df_add_fast(df_add_fast(df_mul(R[i][0], A[0][j]), df_mul(R[i][1], A[1][j])),
-                         df_mul(R[i][2], A[2][j]));
+        P[i][j] = df_dot3(R[i][0], A[0][j], R[i][1], A[1][j], R[i][2], A[2][j]);
     const df wt = ld_df(w_df, t);
     df Dd[3][3];
     df ssum = {0.f, 0.f};
@@ -447,8 +443,7 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int a = 1; a < 4; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const df q = df_add_fast(df_add_fast(df_mul(Dd[d][0], Di[a - 1][0]), df_mul(Dd[d][1], Di[a - 1][1])),
-                            df_mul(Dd[d][2], Di[a - 1][2]));
+        const df q = df_dot3(Dd[d][0], Di[a - 1][0], Dd[d][1], Di[a - 1][1], Dd[d][2], Di[a - 1][2]);
         const df fa = df_mul(wt, q);
         tetf[(size_t)(a * 3 + d) * T + t] = make_float2(fa.hi, fa.lo);
         f0[d] = df_sub(f0[d], fa);
