@@ -104,6 +104,29 @@ __device__ __forceinline__ df df_dot3_f(df a0, float b0, df a1, float b1, df a2,
   return df_fast_two_sum(s2.hi, e);
 }
 
+// a + b + c for double-float terms: the high parts summed with two-sums,
+// the low parts and the sums' rounding errors in float32, normalised once
+// (exact-cancellation safe in the high parts)
+__device__ __forceinline__ df df_sum3(df a, df b, df c) {
+  const df s = df_two_sum(a.hi, b.hi);
+  const df s2 = df_two_sum(s.hi, c.hi);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), c.lo), __fadd_rn(s.lo, s2.lo));
+  return df_two_sum(s2.hi, e);
+}
+
+// a0 b0 + a1 b1 + a2 b2 for float32 factors, as a double-float (the exact
+// products' high and low parts summed as in df_dot3)
+__device__ __forceinline__ df df_dot3_ff(float a0, float b0, float a1, float b1, float a2, float b2) {
+  const float p0 = __fmul_rn(a0, b0), p1 = __fmul_rn(a1, b1), p2 = __fmul_rn(a2, b2);
+  float e = __fmaf_rn(a0, b0, -p0);
+  e = __fadd_rn(e, __fmaf_rn(a1, b1, -p1));
+  e = __fadd_rn(e, __fmaf_rn(a2, b2, -p2));
+  const df s = df_two_sum(p0, p1);
+  const df s2 = df_two_sum(s.hi, p2);
+  e = __fadd_rn(e, __fadd_rn(s.lo, s2.lo));
+  return df_two_sum(s2.hi, e);
+}
+
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 

@@ -358,10 +358,9 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j) {
-        df g = df_add_fast(df_add_fast(df_two_prod(R0[0][i], R0[0][j]), df_two_prod(R0[1][i], R0[1][j])),
-                      df_two_prod(R0[2][i], R0[2][j]));
-        const df r = df_sub(df_from_float(i == j ? 1.f : 0.f), g);
-        Dm[i][j] = Dm[j][i] = 0.5f * (r.hi + r.lo);
+        const df g = df_dot3_ff(R0[0][i], R0[0][j], R0[1][i], R0[1][j], R0[2][i], R0[2][j]);
+        // (1 - g.hi) is exact for g.hi near 1 (and 0 - g.hi always)
+        Dm[i][j] = Dm[j][i] = 0.5f * ((i == j ? 1.f - g.hi : -g.hi) - g.lo);
       }
     float R1c[3][3];
     matmul(R0, Dm, R1c);
@@ -373,7 +372,8 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
       for (int j = 0; j < 3; ++j) {
         df acc = df_dot3_f(M[0][j], R0[0][i], M[1][j], R0[1][i], M[2][j], R0[2][i]);
         const float c = R1c[0][i] * M[0][j].hi + R1c[1][i] * M[1][j].hi + R1c[2][i] * M[2][j].hi;
-        S[i][j] = df_add_fast(acc, df_from_float(c));
+        // c is a correction of relative size ~1e-7: it joins the low part
+        S[i][j] = df_fast_two_sum(acc.hi, __fadd_rn(acc.lo, c));
       }
     float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
     {
@@ -426,30 +426,32 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
         P[i][j] = df_dot3(R[i][0], A[0][j], R[i][1], A[1][j], R[i][2], A[2][j]);
     const df wt = ld_df(w_df, t);
     df Dd[3][3];
-    df ssum = {0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        Dd[i][j] = df_sub(F[i][j], P[i][j]);
-        ssum = df_add_fast(ssum, df_mul(Dd[i][j], Dd[i][j]));
-      }
+      for (int j = 0; j < 3; ++j) Dd[i][j] = df_sub(F[i][j], P[i][j]);
+    // |D|^2 by rows (terms of one sign)
+    const df ssum = df_sum3(df_dot3(Dd[0][0], Dd[0][0], Dd[0][1], Dd[0][1], Dd[0][2], Dd[0][2]),
+                            df_dot3(Dd[1][0], Dd[1][0], Dd[1][1], Dd[1][1], Dd[1][2], Dd[1][2]),
+                            df_dot3(Dd[2][0], Dd[2][0], Dd[2][1], Dd[2][1], Dd[2][2], Dd[2][2]));
     e = df_mul(wt, ssum);
     e.hi *= 0.5f;
     e.lo *= 0.5f;
     // f_a = w D gradN_a, gradN_a = row a-1 of Dm^-1 (a = 1..3), f_0 = -sum
-    df f0[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    df fa[3][3];
 #pragma unroll
     for (int a = 1; a < 4; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const df q = df_dot3(Dd[d][0], Di[a - 1][0], Dd[d][1], Di[a - 1][1], Dd[d][2], Di[a - 1][2]);
-        const df fa = df_mul(wt, q);
-        tetf[(size_t)(a * 3 + d) * T + t] = make_float2(fa.hi, fa.lo);
-        f0[d] = df_sub(f0[d], fa);
+        fa[a - 1][d] = df_mul(wt, q);
+        tetf[(size_t)(a * 3 + d) * T + t] = make_float2(fa[a - 1][d].hi, fa[a - 1][d].lo);
       }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) tetf[(size_t)d * T + t] = make_float2(f0[d].hi, f0[d].lo);
+    for (int d = 0; d < 3; ++d) {
+      const df f0 = df_neg(df_sum3(fa[0][d], fa[1][d], fa[2][d]));
+      tetf[(size_t)d * T + t] = make_float2(f0.hi, f0.lo);
+    }
     if (proj != nullptr) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) proj[(size_t)9 * t + k] = df_to_double(P[k / 3][k % 3]);
