@@ -127,6 +127,14 @@ __device__ __forceinline__ df df_dot3_ff(float a0, float b0, float a1, float b1,
   return df_two_sum(s2.hi, e);
 }
 
+// a - b with the high parts' difference exact (two-sum) and the low parts'
+// difference rounded once in float32: an absolute error within a few units
+// of 2^-48 (|a| + |b|), also when a and b nearly cancel
+__device__ __forceinline__ df df_sub_fast(df a, df b) {
+  const df s = df_two_sum(a.hi, -b.hi);
+  return df_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 

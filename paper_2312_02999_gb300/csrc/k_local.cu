@@ -316,9 +316,9 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
     for (int d = 0; d < 3; ++d) u0[d] = ld_df(udf, 3 * (size_t)tv.x + d);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      Du[d][0] = df_sub(ld_df(udf, 3 * (size_t)tv.y + d), u0[d]);
-      Du[d][1] = df_sub(ld_df(udf, 3 * (size_t)tv.z + d), u0[d]);
-      Du[d][2] = df_sub(ld_df(udf, 3 * (size_t)tv.w + d), u0[d]);
+      Du[d][0] = df_sub_fast(ld_df(udf, 3 * (size_t)tv.y + d), u0[d]);
+      Du[d][1] = df_sub_fast(ld_df(udf, 3 * (size_t)tv.z + d), u0[d]);
+      Du[d][2] = df_sub_fast(ld_df(udf, 3 * (size_t)tv.w + d), u0[d]);
     }
     df Di[3][3];
 #pragma unroll
@@ -429,7 +429,7 @@ __device__ __forceinline__ void elastic_df_body(int T, const int4* __restrict__ 
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Dd[i][j] = df_sub(F[i][j], P[i][j]);
+      for (int j = 0; j < 3; ++j) Dd[i][j] = df_sub_fast(F[i][j], P[i][j]);
     // |D|^2 by rows (terms of one sign)
     const df ssum = df_sum3(df_dot3(Dd[0][0], Dd[0][0], Dd[0][1], Dd[0][1], Dd[0][2], Dd[0][2]),
                             df_dot3(Dd[1][0], Dd[1][0], Dd[1][1], Dd[1][1], Dd[1][2], Dd[1][2]),
