@@ -707,16 +707,19 @@ def _measured_hbm():
         return 6800.0, "fallback"
 
 
-# double-float and float32 operations of the mixed local step per tet,
-# counted from k_elastic_df (FMA = 2 flop): Du 180, F 501, M 468, float32
-# Jacobi polar rotation ~1200, re-orthonormalisation 372, S = R1^T M 558,
-# rotation correction 305, p = R A 468, D and |D|^2 369, forces 738
+# The unit of work of the mixed local step per tet: the double-float and
+# float32 operations of its first double-float formulation, with separate
+# products and additions (FMA = 2 flop): Du 180, F 501, M 468, float32 Jacobi
+# polar rotation ~1200, re-orthonormalisation 372, S = R1^T M 558, rotation
+# correction 305, p = R A 468, D and |D|^2 369, forces 738.  It is kept fixed
+# so that a faster form of the same arithmetic (fused dot products and sums)
+# shows as a higher rate.
 LOCAL_FLOP_PER_TET = 5160.0
 # DRAM bytes per tet of k_elastic_df_b (ncu dram__bytes_read.sum + write.sum
-# of one 16-frame launch on face_shell_30k, 151.8 + 182.0 MB over 16 x 148,056
+# of one 16-frame launch on face_shell_30k, 152.8 + 182.0 MB over 16 x 148,056
 # tets; profiles/k_elastic_df_b_face30k_batch16.md), scaled to a launch by its
 # tets; traffic grows with the tets a launch processes
-LOCAL_DRAM_BYTES_PER_TET = 140.9
+LOCAL_DRAM_BYTES_PER_TET = 141.3
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rates
 
 
