@@ -341,6 +341,15 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
   const float* Zj = Z + zoff[J];
   const int* Rj = rows + roff[J];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // the item's off-diagonal row positions (at most kBwdRowSplit), fetched
+  // once, so that each staged tile needs one dependent global load, not two
+  __shared__ int ridx[kBwdRowSplit];
+  const int r_first = max(k0, it.w);
+  for (int q = tid; q < ld - r_first; q += blockDim.x) {
+    const int r = r_first + q;
+    ridx[q] = r >= ns ? __ldg(Rj + r - ns) : -1;
+  }
+  __syncthreads();
   float wr[kPer], zr[kPer];
   auto load = [&](int rb) {
 #pragma unroll
@@ -351,7 +360,7 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
         if (r < ns) {
           w = y[(size_t)(c0 + r) * nr + cc + j];
         } else {
-          const int row = __ldg(Rj + r - ns);
+          const int row = ridx[r - r_first];
           if (FSIM_CHECK_IDX(row, nf, CHECK_TRSV_ROW)) w = -x[(size_t)row * nr + cc + j];
         }
       }
@@ -373,7 +382,6 @@ k_bwd_mr(const int4* __restrict__ items, const int* __restrict__ c0a, const int*
   float acc[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-  const int r_first = max(k0, it.w);
   load(r_first);
   store(0);
   __syncthreads();
