@@ -489,13 +489,29 @@ __device__ __forceinline__ void gather_forces_df_body(int n, int T, const int* _
   if (v >= n) return;
   df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
   if (!pinned[v]) {
-    for (int e = vptr[v]; e < vptr[v + 1]; ++e) {
-      const int slot = vslot[e];
-      const int t = slot >> 2, a = slot & 3;
-      if (!FSIM_CHECK_IDX(t, T, CHECK_GATHER_TET)) continue;
-      s0 = df_add(s0, ld_df(tetf, (size_t)(a * 3 + 0) * T + t));
-      s1 = df_add(s1, ld_df(tetf, (size_t)(a * 3 + 1) * T + t));
-      s2 = df_add(s2, ld_df(tetf, (size_t)(a * 3 + 2) * T + t));
+    // four slots per step: their index and force loads are all in flight
+    // before the (exact-cancellation safe) double-float sums use them
+    const int e0 = vptr[v], e1 = vptr[v + 1];
+    for (int e = e0; e < e1; e += 4) {
+      int slot[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) slot[q] = e + q < e1 ? vslot[e + q] : -1;
+      df f[4][3];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = slot[q] >> 2, a = slot[q] & 3;
+        const bool ok = slot[q] >= 0 && FSIM_CHECK_IDX(t, T, CHECK_GATHER_TET);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          f[q][d] = ok ? ld_df(tetf, (size_t)(a * 3 + d) * T + t) : df{0.f, 0.f};
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (slot[q] < 0) break;
+        s0 = df_add(s0, f[q][0]);
+        s1 = df_add(s1, f[q][1]);
+        s2 = df_add(s2, f[q][2]);
+      }
     }
   }
   g[3 * (size_t)v + 0] = df_to_double(s0);
