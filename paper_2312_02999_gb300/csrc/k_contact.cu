@@ -840,6 +840,20 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
 }
 
+// The same key from the bits alone (-0.0 mapped to +0.0 by comparison, not
+// by a float64 addition), and its inverse.  GB300 runs float64 compares,
+// min / max and additions on its narrow float64 pipe, so the boxes take their
+// min / max on the keys (integer pipe) and convert back once.
+__device__ __forceinline__ unsigned long long order_key_bits(double v) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  if (u == 0x8000000000000000ULL) u = 0;
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+  const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
 __device__ __forceinline__ void k_prim_prep_body(int Ns, int Nt, int Ne, const double* __restrict__ s,
                             const double* __restrict__ ds, const int* __restrict__ tris,
                             const int* __restrict__ edges, double pad, float* __restrict__ box,
@@ -852,30 +866,32 @@ __device__ __forceinline__ void k_prim_prep_body(int Ns, int Nt, int Ne, const d
   if (p < Ns) { ids[0] = p; nv = 1; }
   else if (p < Ns + Nt) { const int t = p - Ns; ids[0] = tris[3 * t]; ids[1] = tris[3 * t + 1]; ids[2] = tris[3 * t + 2]; nv = 3; }
   else { const int e = p - Ns - Nt; ids[0] = edges[2 * e]; ids[1] = edges[2 * e + 1]; nv = 2; }
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  unsigned long long klo[3] = {~0ULL, ~0ULL, ~0ULL}, khi[3] = {0ULL, 0ULL, 0ULL};
   for (int k = 0; k < nv; ++k)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double x = s[3 * (size_t)ids[k] + d];
-      lo[d] = fmin(lo[d], x); hi[d] = fmax(hi[d], x);
+      const unsigned long long kx = order_key_bits(x);
+      klo[d] = min(klo[d], kx); khi[d] = max(khi[d], kx);
       if (ds != nullptr) {
-        const double e = x + ds[3 * (size_t)ids[k] + d];
-        lo[d] = fmin(lo[d], e); hi[d] = fmax(hi[d], e);
+        const unsigned long long ke = order_key_bits(x + ds[3 * (size_t)ids[k] + d]);
+        klo[d] = min(klo[d], ke); khi[d] = max(khi[d], ke);
       }
     }
   float* b = box + 12 * (size_t)p;
   unsigned long long* kk = key + 12 * (size_t)p;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double la = lo[d] - pad, ha = hi[d] + pad;    // same rounding as the oracle's test
+    const double lo = key_value(klo[d]), hi = key_value(khi[d]);
+    const double la = lo - pad, ha = hi + pad;          // same rounding as the oracle's test
     b[d] = __double2float_rd(la);
     b[3 + d] = __double2float_ru(ha);
-    b[6 + d] = __double2float_rd(lo[d]);
-    b[9 + d] = __double2float_ru(hi[d]);
-    kk[d] = order_key(la);
-    kk[3 + d] = order_key(ha);
-    kk[6 + d] = order_key(lo[d]);
-    kk[9 + d] = order_key(hi[d]);
+    b[6 + d] = __double2float_rd(lo);
+    b[9 + d] = __double2float_ru(hi);
+    kk[d] = order_key_bits(la);
+    kk[3 + d] = order_key_bits(ha);
+    kk[6 + d] = klo[d];
+    kk[9 + d] = khi[d];
   }
   if (p < Ns) {
 #pragma unroll
