@@ -816,6 +816,7 @@ __global__ void __launch_bounds__(kST) k_small_s(RedArgs<float> a) {
 
 // k_small_x (grid): y = B u_c in float64, |y2|^2 (PARTS & 1: these need the
 // right-hand side), X = B (L_s (x) I_3) (PARTS & 2: needs only B and L_s).
+constexpr int kXRows = 4;                  // rows of X per staged block
 template <int PARTS>
 __device__ __forceinline__ void k_small_x_body(RedArgs<float> a) {
   const int nc = *a.nc_dev;
@@ -844,19 +845,35 @@ __device__ __forceinline__ void k_small_x_body(RedArgs<float> a) {
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0 && q != 0.0) atomicAdd(&a.nrm[2], q);
   }
-  if (PARTS & 2)
-  for (int e = gtid; e < n3 * n3; e += gsz) {
-    const int row = e / n3, colx = e % n3;
-    const int i = row / 3, k = colx / 3, b = colx % 3;
-    const double* brow = a.Bc + (size_t)row * n3;
-    float acc = 0.f;
-    const int ci = a.cnt[i];
+  if (PARTS & 2) {
+    // X by blocks of kXRows rows: the block's rows of B-check are converted
+    // to float32 once into shared memory (a float64 conversion costs a
+    // float64-pipe issue on GB300), then every thread forms entries of the
+    // block from them
+    __shared__ float bs[kXRows][3 * kClusNc];
+    const int nblk = (n3 + kXRows - 1) / kXRows;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+      const int r0 = rb * kXRows;
+      __syncthreads();
+      for (int e = threadIdx.x; e < kXRows * n3; e += blockDim.x) {
+        const int rr = e / n3, c = e - rr * n3, row = r0 + rr;
+        bs[rr][c] = row < n3 ? (float)a.Bc[(size_t)row * n3 + c] : 0.f;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kXRows * n3; e += blockDim.x) {
+        const int rr = e / n3, colx = e - rr * n3, row = r0 + rr;
+        if (row >= n3) continue;
+        const int i = row / 3, k = colx / 3, b = colx % 3;
+        float acc = 0.f;
+        const int ci = a.cnt[i];
 #pragma unroll 4
-    for (int q = 0; q < ci; ++q) {
-      const int j = a.list[(size_t)i * nc + q];
-      if (j >= k) acc += (float)brow[3 * j + b] * a.S[(size_t)j * nc + k];
+        for (int q = 0; q < ci; ++q) {
+          const int j = a.list[(size_t)i * nc + q];
+          if (j >= k) acc += bs[rr][3 * j + b] * a.S[(size_t)j * nc + k];
+        }
+        a.X[(size_t)row * n3 + colx] = acc;
+      }
     }
-    a.X[e] = acc;
   }
 }
 template <int PARTS>
@@ -1765,7 +1782,7 @@ cudaError_t reduced_prepare_b(cudaStream_t s2, const void* args_dev, int nb, int
   const auto* A = static_cast<const RedArgs<float>*>(args_dev);
   ProfScope ps(PROF_CHOL, s2);
   k_small_s_b<<<dim3(1, nb), kST, kSmallSmemS, s2>>>(A);
-  k_small_x_b<2><<<dim3(std::max(1, 2 * num_sms / nb), nb), 256, 0, s2>>>(A);
+  k_small_x_b<2><<<dim3((3 * kClusNc + kXRows - 1) / kXRows, nb), 256, 0, s2>>>(A);
   k_small_n_b<<<dim3(kNTiles, nb), 256, 0, s2>>>(A);
   count_launch(3);
   return cudaGetLastError();
