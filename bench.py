@@ -619,12 +619,7 @@ def run_ours(args):
     value = fps(srv_m)
     iters = [st["iterations"] for st in srv_m["stats"]]
     rooflines = batch_rooflines(bprof, info)
-    # The dominant kernel is the one with the largest share of the launch
-    # list of this workload (ncu, serialised): k_elastic_df_b, the local step,
-    # at 27 % (profiles/launches_face30k_served_batch32.md).  The "reduced"
-    # class brackets five kernels that overlap the backward solve on the side
-    # stream, so its event time also holds the SMs it waits for.
-    dominant = next((r for r in rooflines if r["kernel_class"] == "local_step"), None)
+    dominant = dominant_roofline(rooflines)
     single_leg = lambda r: {
         "value": world * K / (sum(r["times"]) / 1e3) if world == 1 else None,
         "ms_per_frame": statistics.mean(r["times"]),
@@ -721,6 +716,16 @@ LOCAL_FLOP_PER_TET = 5160.0
 # tets; traffic grows with the tets a launch processes
 LOCAL_DRAM_BYTES_PER_TET = 141.3
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rates
+
+
+def dominant_roofline(rooflines):
+    """The roofline of the dominant kernel: the one with the largest share of
+    this workload's launch list (ncu, serialised), k_elastic_df_b, the local
+    step, at about a quarter (profiles/launches_face30k_served_96streams.md).
+    The "reduced" class brackets several kernels that overlap the backward
+    solve on the side stream, so its event time also holds the SMs it waits
+    for."""
+    return next((r for r in rooflines if r["kernel_class"] == "local_step"), None)
 
 
 def batch_rooflines(bprof, info):

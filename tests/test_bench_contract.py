@@ -38,3 +38,30 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_batch_rooflines_arithmetic():
+    # the roofline entries bench.py reports, from synthetic per-class event
+    # times: achieved = work / average launch time, frac = achieved / peak
+    sys.path.insert(0, ROOT)
+    import bench
+    T, n, n2, nb = 1000, 300, 40, 4
+    info = {"T": T, "n": n, "n2": n2, "factor_nnz": 5000, "n_levels": 5, "n_free": 280}
+    bprof = {"frames": nb, "stats": [{"iterations": 10, "sum_nc3": 8000.0}] * nb,
+             "classes": {"local_step": (2, 4.0), "sigma_gemv": (2, 0.2), "reduced": (10, 5.0),
+                         "detect": (0, 0.0)}}
+    rl = {r["kernel_class"]: r for r in bench.batch_rooflines(bprof, info)}
+    assert "detect" not in rl                       # classes without launches are left out
+    loc = rl["local_step"]
+    assert loc["bound"] == "alu" and loc["unit"] == "TFLOP/s"
+    ach = bench.LOCAL_FLOP_PER_TET * T * nb / (2.0e-3) / 1e12
+    assert abs(loc["achieved"] - ach) <= 1e-12 * ach
+    assert abs(loc["frac"] - ach / bench.FP32_TFLOPS_PEAK) <= 1e-12
+    assert abs(loc["traffic"] - bench.LOCAL_DRAM_BYTES_PER_TET * T * nb) <= 1e-6
+    tc = rl["sigma_gemv"]
+    nr = (3 * nb + 31) // 32 * 32
+    assert tc["bound"] == "tensor"
+    assert abs(tc["achieved"] - 3 * 2.0 * n2 * n2 * nr / 0.1e-3 / 1e12) <= 1e-9
+    red = rl["reduced"]
+    assert abs(red["achieved"] - 18.0 * 8000.0 * nb / 10 / 0.5e-3 / 1e12) <= 1e-12
+    assert bench.dominant_roofline(list(rl.values()))["kernel_class"] == "local_step"
